@@ -1,0 +1,166 @@
+"""Ozaki error-free splitting product, float64 CPU oracle (Sec. "Ozaki Scheme").
+
+TEST INFRASTRUCTURE ONLY (see the package header).
+
+What the paper states (Sec. "Ozaki Scheme" and the caption of Fig. 2): each
+operand is scaled to keep its exponent range (row-wise for A, column-wise for
+B), split into S slice matrices of the input's size that multiply without
+rounding error, the slice products A_i B_j with i + j <= S + 1 are formed, and
+the products are summed in the original (FP64) precision. S splits cost 2S
+times the memory and S(S+1)/2 products.
+
+The paper does not print the split formula (it points to the improved
+extraction of Minamihata et al.). The reading implemented here, used by the GPU
+path as well:
+
+* scaling: e_r = ilogb(max_j |A_rj|) + 1 for a nonzero row (0 for a zero row),
+  so every scaled entry x = A_rj 2^-e_r lies in (-1, 1). B is scaled per column
+  the same way (f_c), i.e. B^T is scaled per row.
+* digits: for i = 1..S, y = x 2^beta, d_i = trunc(y), x = y - d_i. Every step is
+  exact in FP64 and |d_i| <= 2^beta - 1. beta = 7 gives digits in int8 range
+  (the INT8 mode); beta = 8 gives integers exactly representable in bfloat16.
+  There is no remainder slice: the truncation of the last digit is the error
+  that the diagonal i + j = S + 1 carries.
+* level sums: S_L = sum over i + j = L of D_i^A (D_j^B)^T, exact integers,
+  for L = 2 .. S + 1 (these are exactly the kept pairs).
+* recombination: C = 2^(e_r + f_c) * (S_{S+1} 2^-beta(S+1) + ... + S_2 2^-2beta),
+  summed in FP64 from the smallest level (L = S + 1) to the largest, rounding at
+  each addition; each S_L 2^-beta L is exact.
+
+Parity: pinned. The tests check digit reconstruction with exact rationals,
+level sums against Python exact-integer products, the truncation bound against
+the exact rational product, agreement with the correctly rounded product when
+beta*S covers FP64, and the paper's printed product counts.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+# digit width per precision mode (bits of magnitude per slice)
+BETA = {"int8": 7, "bf16": 8}
+
+
+def kept_pairs(s: int):
+    """Slice pairs (i, j), 1-based, with i + j <= s + 1 (Sec. "Ozaki Scheme")."""
+    if s < 1:
+        raise ValueError("need at least one slice")
+    return [(i, j) for i in range(1, s + 1) for j in range(1, s + 1) if i + j <= s + 1]
+
+
+def product_count(s: int) -> int:
+    """Number of slice products; the paper states S(S+1)/2."""
+    return len(kept_pairs(s))
+
+
+def symmetric_square_product_count(s: int) -> int:
+    """Products for a symmetric square A*A with the transpose trick (Sec. "Comparison
+    with the Markidis Method").
+
+    Reading: the error-free terms (i + j <= s) need one product per unordered
+    pair because A_j A_i = (A_i A_j)^T, while the s terms on the diagonal
+    i + j = s + 1 that carry the truncation error are all formed. This gives the
+    paper's 8 (four splits) and 11 (five splits).
+    """
+    exact_unordered = len([(i, j) for (i, j) in kept_pairs(s) if i <= j and i + j <= s])
+    diagonal = len([(i, j) for (i, j) in kept_pairs(s) if i + j == s + 1])
+    return exact_unordered + diagonal
+
+
+def row_exponents(A: np.ndarray) -> np.ndarray:
+    """e_r with max_j |A_rj| < 2^e_r <= 2 max_j |A_rj| (0 for an all-zero row)."""
+    A = np.asarray(A, dtype=np.float64)
+    if not np.all(np.isfinite(A)):
+        raise ValueError("non-finite input")
+    m = np.max(np.abs(A), axis=1) if A.shape[1] > 0 else np.zeros(A.shape[0])
+    _, e = np.frexp(m)  # m = f 2^e with 1/2 <= f < 1
+    e = e.astype(np.int64)
+    e[m == 0] = 0
+    return e
+
+
+def split_rows(A: np.ndarray, s: int, beta: int):
+    """Row-scaled digit planes of A.
+
+    Returns (e, D, residual): e[r] the row exponents, D an (s, m, k) int64 array
+    of digits, residual the (m, k) float64 remainder in (-1, 1) after s digits,
+    so that A = 2^e (sum_i D_i 2^-beta i + residual 2^-beta s) exactly.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    e = row_exponents(A)
+    x = np.ldexp(A, -e[:, None])
+    D = np.zeros((s,) + A.shape, dtype=np.int64)
+    radix = 2.0 ** beta
+    for i in range(s):
+        y = x * radix
+        d = np.trunc(y)
+        x = y - d
+        D[i] = d.astype(np.int64)
+    return e, D, x
+
+
+def split_cols(B: np.ndarray, s: int, beta: int):
+    """Column-scaled digit planes of B, stored as the row split of B^T."""
+    return split_rows(np.asarray(B, dtype=np.float64).T, s, beta)
+
+
+def level_sums(DA: np.ndarray, DBt: np.ndarray, beta: int):
+    """Exact level sums S_L = sum_{i+j=L} D_i^A (D_j^B)^T for L = 2 .. s+1.
+
+    DA is (s, m, k), DBt is (s, n, k) (digits of B^T). The products are taken
+    with float64 matrix multiplication on integer-valued operands; every partial
+    sum is an integer of magnitude below (L-1) k (2^beta - 1)^2 < 2^53 (asserted),
+    so each is exact whatever order the library adds in.
+    """
+    s, m, k = DA.shape
+    n = DBt.shape[1]
+    bound = s * max(k, 1) * (2 ** beta - 1) ** 2
+    if bound >= 2 ** 53:
+        raise ValueError("level sums could exceed 2^53; not exact in float64")
+    out = {}
+    for L in range(2, s + 2):
+        acc = np.zeros((m, n), dtype=np.float64)
+        for i in range(1, L):
+            j = L - i
+            if i > s or j > s:
+                continue
+            acc = acc + DA[i - 1].astype(np.float64) @ DBt[j - 1].astype(np.float64).T
+        out[L] = acc.astype(np.int64)
+    return out
+
+
+def recombine(S: dict, e_row: np.ndarray, f_col: np.ndarray, s: int, beta: int) -> np.ndarray:
+    """FP64 sum of the levels, smallest first, then the power-of-two unscaling."""
+    m = e_row.shape[0]
+    n = f_col.shape[0]
+    C = np.zeros((m, n), dtype=np.float64)
+    for L in range(s + 1, 1, -1):
+        C = C + S[L].astype(np.float64) * (2.0 ** (-beta * L))
+    return np.ldexp(C, e_row[:, None] + f_col[None, :])
+
+
+def ozaki_gemm(A: np.ndarray, B: np.ndarray, s: int, beta: int = 7, return_parts: bool = False):
+    """C ~= A B through the Ozaki scheme with s slices of beta bits."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    if A.ndim != 2 or B.ndim != 2 or A.shape[1] != B.shape[0]:
+        raise ValueError("shape mismatch")
+    e, DA, _ = split_rows(A, s, beta)
+    f, DBt, _ = split_cols(B, s, beta)
+    S = level_sums(DA, DBt, beta)
+    C = recombine(S, e, f, s, beta)
+    if return_parts:
+        return C, dict(e=e, f=f, DA=DA, DBt=DBt, S=S)
+    return C
+
+
+def truncation_bound(e_row: np.ndarray, f_col: np.ndarray, k: int, s: int, beta: int) -> np.ndarray:
+    """Elementwise bound on |C - A B| for the scheme above.
+
+    Per scaled product the dropped pairs (i + j >= s + 2) and the residuals
+    contribute less than (s + 2) 2^-beta s; the FP64 recombination adds at most
+    s roundings of a sum below k in magnitude. Both scale by k and 2^(e_r+f_c).
+    """
+    scale = np.ldexp(np.ones((e_row.shape[0], f_col.shape[0])), e_row[:, None] + f_col[None, :])
+    per = (s + 2) * 2.0 ** (-beta * s) + s * 2.0 ** (-53)
+    return scale * max(k, 1) * per

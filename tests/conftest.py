@@ -1,0 +1,26 @@
+"""Shared test configuration.
+
+Tests marked `gpu` need a CUDA device and the compiled library; everything else
+runs on the CPU (`pytest -m "not gpu"`).
+"""
+
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled libdmp")
+    config.addinivalue_line("markers", "slow: long-running (minutes)")
+
+
+@pytest.fixture(scope="session")
+def golden_dir():
+    return GOLDEN

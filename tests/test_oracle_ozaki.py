@@ -1,0 +1,278 @@
+"""Pins for the Ozaki-product oracle (Sec. "Ozaki Scheme").
+
+Every check here compares the oracle with something other than itself: the
+paper's printed counts, exact rational arithmetic, Python exact-integer
+products, the exact product of integer matrices, or the correctly rounded exact
+product. The planted-mistake tests show that a plausible slip in the oracle
+(a dropped level, a transposed operand, a wrong digit sign) fails these pins.
+"""
+
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import ozaki as oz
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _mixed_matrix(m, k, seed):
+    """Entries of both signs spanning many binades, plus a zero row and exact zeros."""
+    rng = _rng(seed)
+    A = rng.standard_normal((m, k)) * np.exp2(rng.integers(-30, 10, size=(m, k)))
+    A[1, :] = 0.0
+    A[2, 3] = 0.0
+    A[3, :] *= 2.0 ** -400
+    return A
+
+
+# ----------------------------------------------------------------- paper's counts
+
+def test_paper_product_counts(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "paper_counts.json")))
+    for row in g["products_per_split_count"]:
+        assert oz.product_count(row["splits"]) == row["products"], row["where"]
+    for row in g["symmetric_square_products"]:
+        assert oz.symmetric_square_product_count(row["splits"]) == row["products"], row["where"]
+    be = g["break_even"]
+    assert be["calls"] * oz.product_count(be["splits_low"]) == be["products_low"]
+    assert be["calls"] * oz.product_count(be["splits_high"]) == be["products_high"]
+
+
+def test_memory_factor_two_s():
+    """S digit planes per operand, each the size of the operand: 2S for A and B."""
+    A = _rng(0).standard_normal((6, 5))
+    B = _rng(1).standard_normal((5, 4))
+    for s in (1, 3, 6):
+        _, DA, _ = oz.split_rows(A, s, 7)
+        _, DBt, _ = oz.split_cols(B, s, 7)
+        assert DA.size + DBt.size == s * (A.size + B.size)
+
+
+def test_kept_pairs_are_the_levels():
+    for s in range(1, 10):
+        pairs = oz.kept_pairs(s)
+        assert all(i + j <= s + 1 for i, j in pairs)
+        assert len(set(pairs)) == len(pairs)
+        assert sorted({i + j for i, j in pairs}) == list(range(2, s + 2))
+
+
+# ----------------------------------------------------------------- split
+
+def _check_split(split_rows, A, s, beta):
+    e, D, res = split_rows(A, s, beta)
+    m, k = A.shape
+    for r in range(m):
+        rowmax = max(abs(Fraction(float(v))) for v in A[r])
+        if rowmax == 0:
+            assert e[r] == 0
+        else:
+            assert rowmax < Fraction(2) ** int(e[r]) <= 2 * rowmax
+        for c in range(k):
+            x = Fraction(float(A[r, c])) / Fraction(2) ** int(e[r])
+            # digits are the beta-bit expansion of |x| carrying the sign of x
+            sign = -1 if x < 0 else 1
+            ax = abs(x)
+            prev = 0
+            for i in range(1, s + 1):
+                whole = int(ax * 2 ** (beta * i))  # floor of a nonnegative rational
+                digit = whole - prev * 2 ** beta
+                prev = whole
+                assert D[i - 1, r, c] == sign * digit
+                assert abs(D[i - 1, r, c]) <= 2 ** beta - 1
+            # exact reconstruction with the residual
+            recon = sum(Fraction(int(D[i, r, c])) / Fraction(2) ** (beta * (i + 1)) for i in range(s))
+            recon += Fraction(float(res[r, c])) / Fraction(2) ** (beta * s)
+            assert recon * Fraction(2) ** int(e[r]) == Fraction(float(A[r, c]))
+            assert abs(res[r, c]) < 1.0
+
+
+@pytest.mark.parametrize("beta", [7, 8])
+@pytest.mark.parametrize("s", [1, 3, 7])
+def test_split_matches_exact_expansion(beta, s):
+    A = _mixed_matrix(5, 9, seed=11 + s + beta)
+    _check_split(oz.split_rows, A, s, beta)
+
+
+def test_split_cols_is_split_of_transpose():
+    B = _mixed_matrix(7, 6, seed=3)
+    f, DBt, _ = oz.split_cols(B, 4, 7)
+    e, DT, _ = oz.split_rows(B.T.copy(), 4, 7)
+    assert np.array_equal(f, e) and np.array_equal(DBt, DT)
+
+
+def test_split_rejects_nonfinite():
+    A = np.ones((3, 3))
+    A[1, 1] = np.nan
+    with pytest.raises(ValueError):
+        oz.split_rows(A, 3, 7)
+
+
+# ----------------------------------------------------------------- level sums
+
+def _brute_levels(DA, DBt):
+    s, m, k = DA.shape
+    n = DBt.shape[1]
+    out = {}
+    for L in range(2, s + 2):
+        S = [[0] * n for _ in range(m)]
+        for i in range(1, s + 1):
+            j = L - i
+            if not (1 <= j <= s):
+                continue
+            for r in range(m):
+                for c in range(n):
+                    S[r][c] += sum(int(DA[i - 1, r, t]) * int(DBt[j - 1, c, t]) for t in range(k))
+        out[L] = S
+    return out
+
+
+def _check_levels(level_sums, A, B, s, beta):
+    _, DA, _ = oz.split_rows(A, s, beta)
+    _, DBt, _ = oz.split_cols(B, s, beta)
+    got = level_sums(DA, DBt, beta)
+    want = _brute_levels(DA, DBt)
+    assert sorted(got) == sorted(want)
+    for L in want:
+        assert np.array_equal(got[L], np.array(want[L], dtype=np.int64)), L
+
+
+@pytest.mark.parametrize("s,beta", [(3, 7), (5, 8), (6, 7)])
+def test_level_sums_equal_exact_integer_products(s, beta):
+    A = _mixed_matrix(5, 7, seed=21)
+    B = _mixed_matrix(7, 4, seed=22)
+    _check_levels(oz.level_sums, A, B, s, beta)
+
+
+# ----------------------------------------------------------------- full product
+
+def _exact_product(A, B):
+    m, k = A.shape
+    n = B.shape[1]
+    return [[sum(Fraction(float(A[r, t])) * Fraction(float(B[t, c])) for t in range(k)) for c in range(n)]
+            for r in range(m)]
+
+
+def _check_bound(gemm, A, B, s, beta):
+    C, parts = gemm(A, B, s, beta, return_parts=True)
+    exact = _exact_product(A, B)
+    bound = oz.truncation_bound(parts["e"], parts["f"], A.shape[1], s, beta)
+    for r in range(A.shape[0]):
+        for c in range(B.shape[1]):
+            err = abs(Fraction(float(C[r, c])) - exact[r][c])
+            assert err <= Fraction(float(bound[r, c])), (r, c, float(err), bound[r, c])
+
+
+@pytest.mark.parametrize("s,beta", [(2, 7), (4, 7), (3, 8), (6, 7)])
+def test_error_within_truncation_bound(s, beta):
+    A = _mixed_matrix(6, 8, seed=31)
+    B = _mixed_matrix(8, 5, seed=32)
+    _check_bound(oz.ozaki_gemm, A, B, s, beta)
+
+
+def test_integer_matrices_are_exact():
+    """Entries that are integers below 2^beta need one slice: the product is exact."""
+    rng = _rng(5)
+    A = rng.integers(-127, 128, size=(9, 11)).astype(np.float64)
+    B = rng.integers(-127, 128, size=(11, 6)).astype(np.float64)
+    A[:, 0] = 127.0
+    B[0, :] = -100.0
+    want = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    for s in (1, 2, 5):
+        assert np.array_equal(oz.ozaki_gemm(A, B, s, 7), want)
+
+
+def test_full_coverage_is_correctly_rounded():
+    """With beta*s >= 70 on nonnegative inputs (the random [0, 1] matrices of
+    Fig. 3), the result is within 2 ulp of the correctly rounded exact product."""
+    rng = _rng(6)
+    A = rng.random((6, 10))
+    B = rng.random((10, 5))
+    C = oz.ozaki_gemm(A, B, 10, 7)
+    exact = _exact_product(A, B)
+    for r in range(6):
+        for c in range(5):
+            ref = float(exact[r][c])
+            assert abs(C[r, c] - ref) <= 2 * np.spacing(ref), (r, c)
+
+
+def test_error_falls_with_splits():
+    """Fig. 3: the error of the product of random [0, 1] matrices falls with the
+    number of splits until it reaches the FP64 floor."""
+    rng = _rng(7)
+    A = rng.random((40, 64))
+    B = rng.random((64, 30))
+    ref = np.array(_exact_product_float(A, B))
+    errs = [np.linalg.norm(oz.ozaki_gemm(A, B, s, 7) - ref) for s in range(1, 10)]
+    for a, b in zip(errs, errs[1:]):
+        assert b <= a or b < 1e-12
+    assert errs[0] > 1e-3 and errs[-1] < 1e-12
+
+
+def _exact_product_float(A, B):
+    return [[float(v) for v in row] for row in _exact_product(A, B)]
+
+
+def test_recombination_order_smallest_level_first():
+    """The FP64 sum adds levels from L = s+1 down to 2. With a big leading level
+    and two small ones worth 0.375 and 0.25 of its ulp, adding the small ones
+    first rounds up while adding them last leaves the big level unchanged."""
+    s, beta = 3, 7
+    big = 2 ** 53 - 1  # S_2; S_2 2^-14 has ulp 2^-14
+    S = {2: np.array([[big]], dtype=np.int64),
+         3: np.array([[48]], dtype=np.int64),     # 48 2^-21 = 0.375 ulp
+         4: np.array([[4096]], dtype=np.int64)}   # 4096 2^-28 = 0.25 ulp
+    C = oz.recombine(S, np.array([0]), np.array([0]), s, beta)
+    assert C[0, 0] == 2.0 ** 39
+    assert C[0, 0] != float(Fraction(big, 2 ** 14))
+
+
+# ----------------------------------------------------------------- planted mistakes
+
+def test_planted_dropped_level_fails_the_bound():
+    def gemm_drop_level(A, B, s, beta, return_parts=False):
+        C, parts = oz.ozaki_gemm(A, B, s, beta, return_parts=True)
+        S = dict(parts["S"])
+        S[s + 1] = np.zeros_like(S[s + 1])
+        S[2] = S[2] * 0  # a dropped leading level
+        C = oz.recombine(S, parts["e"], parts["f"], s, beta)
+        return (C, parts) if return_parts else C
+
+    A = _mixed_matrix(6, 8, seed=41)
+    B = _mixed_matrix(8, 5, seed=42)
+    with pytest.raises(AssertionError):
+        _check_bound(gemm_drop_level, A, B, 4, 7)
+
+
+def test_planted_transposed_operand_fails_brute_force():
+    def levels_transposed(DA, DBt, beta):
+        s = DA.shape[0]
+        out = {}
+        for L in range(2, s + 2):
+            acc = np.zeros((DA.shape[1], DBt.shape[1]))
+            for i in range(1, L):
+                j = L - i
+                if i <= s and j <= s:
+                    acc = acc + DA[i - 1].astype(np.float64) @ DBt[j - 1].astype(np.float64)  # missing .T
+            out[L] = acc.astype(np.int64)
+        return out
+
+    A = _mixed_matrix(5, 5, seed=51)
+    B = _mixed_matrix(5, 5, seed=52)
+    with pytest.raises(AssertionError):
+        _check_levels(levels_transposed, A, B, 3, 7)
+
+
+def test_planted_wrong_digit_sign_fails_reconstruction():
+    def split_abs(A, s, beta):
+        e, D, res = oz.split_rows(A, s, beta)
+        return e, np.abs(D), res
+
+    A = _mixed_matrix(4, 6, seed=61)
+    with pytest.raises(AssertionError):
+        _check_split(split_abs, A, 3, 7)

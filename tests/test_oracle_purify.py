@@ -1,0 +1,189 @@
+"""Pins for the purification oracle.
+
+Checks against closed forms and mathematical properties: the spectral projector
+of H = Q diag(e) Q^T, a dense eigensolver, a hand-worked n = 3 case, McWeeny's
+printed step (Sec. "Density Matrix Purification"), trace conservation of the
+canonical update, Gershgorin's theorem, and the stopping rules.
+"""
+
+import json
+import os
+from functools import partial
+
+import numpy as np
+import pytest
+
+from oracle import ozaki as oz
+from oracle import purify as pu
+from synth import config_hamiltonian, make_hamiltonian
+
+
+def _projector(Q, n_occ):
+    V = Q[:, :n_occ]
+    return V @ V.T
+
+
+def _random_spd_spectrum_matrix(n, vals, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (Q * vals) @ Q.T
+
+
+@pytest.fixture(scope="module")
+def c0():
+    h = config_hamiltonian(0)
+    return h, pu.purify(h.H, h.n_occ, tol=1e-10)
+
+
+def test_config0_closed_form(c0):
+    h, r = c0
+    P_star = _projector(h.Q, h.n_occ)
+    assert r["status"] == pu.CONVERGED
+    assert np.max(np.abs(r["P"] - P_star)) <= 1e-10
+    assert abs(np.trace(r["P"]) - h.n_occ) <= 1e-10 * h.n
+    assert r["idem"] < 1e-10
+    E_star = float(np.sum(h.e[: h.n_occ]))
+    assert abs(r["energy"] - E_star) <= 1e-12 * abs(E_star)
+    assert all(0.0 <= c <= 1.0 for c in r["c_history"])
+
+
+def test_trace_conserved_along_iterations(c0):
+    h, r = c0
+    assert max(abs(t - h.n_occ) for t in r["trace_history"]) <= 1e-11 * h.n
+
+
+def test_energy_non_increasing(c0):
+    _, r = c0
+    b = r["band_history"]
+    assert all(b[i + 1] <= b[i] + 1e-12 * abs(b[i]) for i in range(len(b) - 1))
+
+
+def test_tiny_against_eigensolver():
+    rng = np.random.default_rng(8)
+    for n, n_occ in [(5, 2), (16, 5), (48, 20)]:
+        G = rng.standard_normal((n, n))
+        H = 0.5 * (G + G.T)
+        w, V = np.linalg.eigh(H)
+        if w[n_occ] - w[n_occ - 1] < 0.05:
+            continue
+        r = pu.purify(H, n_occ, tol=1e-12)
+        assert r["status"] == pu.CONVERGED
+        assert np.max(np.abs(r["P"] - V[:, :n_occ] @ V[:, :n_occ].T)) < 1e-10
+
+
+def test_hand_worked_n3(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "pm_n3_hand.json")))
+    H = np.diag(g["H_diag"])
+    P0, info = pu.initial_guess(H, g["n_occ"])
+    assert info["lam"] == pytest.approx(g["lambda"], rel=1e-15)
+    assert info["mu"] == pytest.approx(g["mu"], rel=1e-15)
+    assert np.allclose(np.diag(P0), g["P0_diag"], rtol=0, atol=1e-15)
+    t1, t2, t3 = np.trace(P0), np.trace(P0 @ P0), np.trace(P0 @ P0 @ P0)
+    c = pu.pm_coefficient(t1, t2, t3)
+    assert c == pytest.approx(g["c0"], abs=1e-14)
+    P1 = pu.pm_update(P0, P0 @ P0, P0 @ P0 @ P0, c)
+    assert np.allclose(np.diag(P1), g["P1_diag"], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("branch", ["low", "high"])
+def test_update_conserves_trace(branch):
+    """tr(P') = tr(P) for any spectrum in (0, 1): the defining property of the
+    canonical coefficient. A dropped term in c or in a branch breaks it."""
+    rng = np.random.default_rng(9 if branch == "low" else 10)
+    n = 30
+    for _ in range(20):
+        if branch == "low":
+            vals = rng.uniform(0.05, 0.45, size=n)  # mostly below 1/2: c < 1/2
+        else:
+            vals = rng.uniform(0.55, 0.95, size=n)  # mostly above 1/2: c > 1/2
+        P = _random_spd_spectrum_matrix(n, vals, rng.integers(1 << 30))
+        X2, X3 = P @ P, P @ P @ P
+        c = pu.pm_coefficient(np.trace(P), np.trace(X2), np.trace(X3))
+        assert (c < 0.5) == (branch == "low")
+        P1 = pu.pm_update(P, X2, X3, c)
+        assert abs(np.trace(P1) - np.trace(P)) < 1e-12 * n
+        # the update maps [0, 1] into [0, 1] with fixed points 0 and 1
+        w = np.linalg.eigvalsh(0.5 * (P1 + P1.T))
+        assert w.min() > -1e-12 and w.max() < 1 + 1e-12
+
+
+def test_c_half_is_mcweeny():
+    """With c = 1/2 both branches equal McWeeny's printed step 3P^2 - 2P^3."""
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0.05, 0.45, size=10)
+    vals = np.concatenate([x, 1.0 - x])  # symmetric about 1/2 -> c = 1/2 exactly
+    P = _random_spd_spectrum_matrix(20, vals, 12)
+    X2, X3 = P @ P, P @ P @ P
+    c = pu.pm_coefficient(np.trace(P), np.trace(X2), np.trace(X3))
+    assert c == pytest.approx(0.5, abs=1e-12)
+    mcweeny = 3 * X2 - 2 * X3
+    for cc in (0.5, np.nextafter(0.5, 0)):
+        assert np.allclose(pu.pm_update(P, X2, X3, cc), mcweeny, atol=1e-12)
+
+
+def test_gershgorin_encloses_spectrum_and_p0_in_unit_interval():
+    for seed in range(4):
+        h = make_hamiltonian(64, 16, seed=100 + seed)
+        h_min, h_max, _, _ = pu.gershgorin(h.H)
+        w = np.linalg.eigvalsh(h.H)
+        assert h_min <= w.min() and w.max() <= h_max
+        P0, _ = pu.initial_guess(h.H, 16)
+        w0 = np.linalg.eigvalsh(P0)
+        assert w0.min() >= -1e-14 and w0.max() <= 1 + 1e-14
+        assert abs(np.trace(P0) - 16) < 1e-12
+
+
+def test_diagonal_hamiltonian_gives_occupation_diagonal():
+    e = np.array([0.3, -1.0, 0.7, -0.2, 1.5, -0.6])
+    r = pu.purify(np.diag(e), 3, tol=1e-12)
+    occ = np.argsort(e)[:3]
+    want = np.zeros(6)
+    want[occ] = 1.0
+    assert np.allclose(r["P"], np.diag(want), atol=1e-12)
+
+
+def test_stopping_rules_and_errors():
+    h = make_hamiltonian(32, 8, seed=5)
+    r = pu.purify(h.H, 8, max_iter=1)
+    assert r["status"] == pu.NOT_CONVERGED and r["iters"] == 1
+    r = pu.purify(h.H, 8, tol=0.0, max_iter=100)  # tol 0 can never be met
+    assert r["status"] in (pu.C_OUT_OF_RANGE, pu.STALLED, pu.NOT_CONVERGED)
+    assert np.max(np.abs(r["P"] - _projector(h.Q, 8))) < 1e-10
+    for bad in (0, 32, -1):
+        with pytest.raises(ValueError):
+            pu.purify(h.H, bad)
+    H = h.H.copy()
+    H[2, 3] = np.nan
+    with pytest.raises(ValueError):
+        pu.purify(H, 8)
+    with pytest.raises(ValueError):
+        pu.purify(2.0 * np.eye(8), 3)
+
+
+def test_energy_tolerance_rule():
+    h = make_hamiltonian(64, 16, seed=6)
+    r = pu.purify(h.H, 16, tol=0.0, energy_tol=1e-8)
+    assert r["status"] == pu.CONVERGED
+    assert abs(r["band_history"][-1] - r["band_history"][-2]) < 1e-8
+
+
+def test_ozaki_mode_converges_towards_projector():
+    """An Ozaki-mode run reaches the projector to within an error that falls
+    with the slice count (the behaviour Fig. 6 reports)."""
+    h = make_hamiltonian(96, 24, seed=7)
+    P_star = _projector(h.Q, 24)
+    errs = []
+    for s in (3, 5, 7):
+        r = pu.purify(h.H, 24, tol=1e-10, product=partial(oz.ozaki_gemm, s=s, beta=7))
+        errs.append(np.max(np.abs(r["P"] - P_star)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-9
+
+
+def test_error_metrics_paper_conventions():
+    h = make_hamiltonian(40, 10, seed=8)
+    P = _projector(h.Q, 10)
+    m = pu.error_metrics(P, h.H, P_ref=P, E_ref=float(np.sum(h.e[:10])))
+    assert m["rmsd"] == 0.0 and m["max_abs"] == 0.0
+    assert m["band_energy"] == pytest.approx(2 * np.sum(h.e[:10]), rel=1e-12)
+    assert m["commutator"] < 1e-12 and m["rel_energy"] < 1e-13
