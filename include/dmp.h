@@ -1,0 +1,216 @@
+/*
+ * dmp.h -- density-matrix purification with Ozaki-scheme products on GB300.
+ *
+ * The problem (arXiv 2407.13299, Sec. "Density Matrix Purification"): given an
+ * orthogonalised Hamiltonian H (n x n, symmetric; the Loewdin transform of Sec.
+ * "Implementation Details" is done by the caller) and the number of occupied
+ * orbitals n_occ, compute the density matrix P, the projector onto the n_occ
+ * lowest eigenvectors of H (the spin-restricted K of the paper is 2P). P is
+ * built by canonical purification (the Palser-Manolopoulos method the paper
+ * cites), whose only heavy step is the dense product, and every product can be
+ * emulated with the Ozaki error-free splitting scheme (Sec. "Ozaki Scheme",
+ * Fig. 2): power-of-two row/column scaling, s digit slices per operand, exact
+ * slice-pair products, FP64 recombination of the pairs with i + j <= s + 1.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major float64 in DEVICE memory owned by the caller,
+ *     element (i, j) at ptr[i * ld + j], ld >= number of columns.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). All work is
+ *     enqueued on it.
+ *   - Workspace: every call that needs scratch takes a caller-allocated device
+ *     buffer `ws` of `ws_bytes`, sized by the matching *_workspace_size call;
+ *     the library allocates no device memory of its own.
+ *   - Return value: 0 (DMP_OK) or a positive numerical status for purification
+ *     (see below), or a negative error. No C++ exception crosses this ABI.
+ *   - Thread safety: calls on different streams with different workspaces may
+ *     run concurrently; a workspace must not be shared by calls in flight.
+ */
+#ifndef DMP_H
+#define DMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- precision modes ------------------------------------------------------
+ * DMP_FP64        every product in float64 (FP64 mma on the GPU).
+ * DMP_OZAKI_INT8  Ozaki products with beta = 7 digit slices (|d| <= 127, the
+ *                 int8 range): exact s32 accumulation of the level sums.
+ * DMP_OZAKI_BF16  Ozaki products with beta = 8 digit slices (|d| <= 255, the
+ *                 integers bfloat16 holds exactly), bf16 tensor cores only.
+ */
+enum { DMP_FP64 = 0, DMP_OZAKI_INT8 = 1, DMP_OZAKI_BF16 = 2 };
+
+/* ---- executors for the slice-pair products ---------------------------------
+ * DMP_EXEC_IMMA  int8 x int8 -> int32 warp-level tensor-core MMA.
+ * DMP_EXEC_TC    digits carried in bfloat16 on the 5th-generation tensor cores
+ *                (tcgen05), fp32 accumulation in tensor memory, drained to
+ *                exact integers every K chunk that keeps partial sums < 2^24.
+ * Both give bit-identical level sums; DMP_EXEC_AUTO picks the faster.
+ */
+enum { DMP_EXEC_AUTO = 0, DMP_EXEC_IMMA = 1, DMP_EXEC_TC = 2 };
+
+/* ---- return codes ------------------------------------------------------- */
+enum {
+  DMP_OK = 0,               /* converged: ||P^2 - P||_F < tol (or energy_tol met) */
+  DMP_NOT_CONVERGED = 1,    /* max_iter reached                                    */
+  DMP_STALLED = 2,          /* band energy rose on two steps by < 1e-2 (paper's halt rule) */
+  DMP_C_OUT_OF_RANGE = 3,   /* tr(P - P^2) <= 0 or c outside [0, 1]: noise floor  */
+  DMP_ERR_INVALID_ARG = -1, /* bad size, null pointer, ld < n, n_occ not in (0, n), s out of range */
+  DMP_ERR_NONFINITE = -2,   /* NaN or Inf in an input or an iterate               */
+  DMP_ERR_CUDA = -3,        /* a CUDA runtime call failed                          */
+  DMP_ERR_TIMEOUT = -4,     /* a bounded device wait gave up                       */
+  DMP_ERR_UNSUPPORTED = -5, /* mode/executor/size combination not available       */
+  DMP_ERR_WORKSPACE = -6    /* ws_bytes (or tape_bytes) smaller than required      */
+};
+
+/* Options. Zero-initialise and set what you need; zeros select defaults. */
+typedef struct {
+  int32_t mode;             /* DMP_FP64 / DMP_OZAKI_INT8 / DMP_OZAKI_BF16           */
+  int32_t slices;           /* s in [1, 10] (beta 7) or [1, 9] (beta 8); 0 -> 7      */
+  int32_t executor;         /* DMP_EXEC_*                                            */
+  int32_t max_iter;         /* 0 -> 100 (the paper's cap)                            */
+  int32_t checkpoint_every; /* forward iterates kept every k steps for the adjoint; 0 -> 8 */
+  int32_t reserved;
+  double tol;               /* ||P^2 - P||_F threshold; 0 -> 1e-10                   */
+  double energy_tol;        /* optional |change of Tr(HK)| threshold; 0 = off        */
+} dmp_opts;
+
+/* Per-run report, filled when the host pointer is non-NULL (the call then
+ * synchronises the stream before returning). */
+typedef struct {
+  int32_t status;      /* DMP_OK .. DMP_C_OUT_OF_RANGE, or a negative error     */
+  int32_t iters;       /* purification updates applied                         */
+  int32_t slices_used; /* s (0 in FP64 mode)                                     */
+  int32_t executor_used;
+  double energy;       /* tr(P H)                                                */
+  double band_energy;  /* Tr(H K) = 2 tr(P H), the paper's energy                */
+  double idem;         /* ||P^2 - P||_F of the returned P                        */
+  double trace;        /* tr(P)                                                  */
+  double c_last;       /* last purification coefficient                          */
+  double h_min, h_max; /* Gershgorin bounds used for the initial guess          */
+} dmp_info;
+
+/* Bytes of workspace dm_purify needs for this n and these options. */
+int dmp_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
+
+/* Bytes of the adjoint tape dm_purify writes when given one (checkpoints every
+ * opts->checkpoint_every iterates plus per-step scalars). */
+int dmp_tape_size(int64_t n, const dmp_opts* opts, size_t* bytes);
+
+/*
+ * dm_purify: canonical purification of H (Sec. "Density Matrix Purification";
+ * initial guess from the Gershgorin bounds, coefficient
+ * c = tr(P^2 - P^3) / tr(P - P^2), update
+ *   c >= 1/2: P' = ((1 + c) P^2 - P^3) / c,
+ *   c <  1/2: P' = ((1 - 2c) P + (1 + c) P^2 - P^3) / (1 - c)),
+ * every product in opts->mode. Stopping rules, tested in this order on each
+ * iterate P_k: ||P_k^2 - P_k||_F < tol (DMP_OK); the paper's energy halt rule
+ * (DMP_STALLED); |change of band energy| < energy_tol if set (DMP_OK);
+ * k == max_iter (DMP_NOT_CONVERGED); tr(P - P^2) <= 0 or c outside [0, 1]
+ * (DMP_C_OUT_OF_RANGE). The returned P is that P_k.
+ *   H      n x n, leading dimension ldh. Only the upper triangle is read; the
+ *          lower triangle is taken as its mirror.
+ *   P      n x n output, leading dimension ldp (may not alias H).
+ *   info   host pointer or NULL (then nothing is reported).
+ *          The call synchronises `stream` once per iteration to read the
+ *          device-side stopping decision, and before it returns.
+ *   tape   NULL, or a device buffer of dmp_tape_size bytes that receives what
+ *          dm_purify_backward needs.
+ * Returns the status (>= 0) or a negative error.
+ */
+int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_opts* opts,
+              double* P, int64_t ldp, dmp_info* info, void* ws, size_t ws_bytes,
+              void* tape, size_t tape_bytes, void* stream);
+
+/* Bytes of workspace ozaki_gemm needs. */
+int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int32_t slices,
+                              int32_t executor, size_t* bytes);
+
+/*
+ * ozaki_gemm: C = A B, m x k times k x n, through the Ozaki scheme
+ * (Sec. "Ozaki Scheme"): A scaled per row and B per column by powers of two,
+ * split into `slices` digit planes of beta bits (mode DMP_OZAKI_INT8: beta 7;
+ * DMP_OZAKI_BF16: beta 8), level sums S_L = sum_{i+j=L} A_i B_j formed exactly
+ * for L = 2..s+1, and C = 2^(e_r+f_c) * sum_L S_L 2^(-beta L) added in float64
+ * from L = s+1 down to 2. The result is bit-for-bit the same for every
+ * executor. mode DMP_FP64 computes a plain float64 product instead.
+ * A row of A or column of B holding NaN/Inf gives a NaN row/column of C.
+ * Limits: s * k * (2^beta - 1)^2 < 2^31 (exact s32 level sums).
+ */
+int ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+               int64_t ldb, double* C, int64_t ldc, int32_t mode, int32_t slices, int32_t executor,
+               void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ozaki_level_sums: the exact integer slice-pair products of ozaki_gemm,
+ * S[L-2][i][j] = (sum_{a+b=L} A_a B_b)[i][j] as int32, L = 2..s+1, written to
+ * S (s x m x n, row-major, leading dimension n). Exposed so that the integer
+ * part of the scheme can be compared bit for bit. Same workspace as ozaki_gemm.
+ */
+int ozaki_level_sums(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                     const double* B, int64_t ldb, int32_t* S, int32_t mode, int32_t slices,
+                     int32_t executor, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * ozaki_split: the row scaling and digit planes of A (m x k), the first step
+ * of the scheme, exactly as the product kernels consume them. exps[m] receives
+ * e_r (max_j |A_rj| < 2^e_r; 0 for a zero row; INT32_MAX for a row holding NaN
+ * or Inf, whose products are then NaN). digits receives s planes of m x k
+ * (plane-major, leading dimension k) of the beta-bit truncated digits,
+ * |d| <= 2^beta - 1: int8 for executor DMP_EXEC_IMMA, bfloat16 bit patterns
+ * for DMP_EXEC_TC. Workspace as for ozaki_gemm(m, 1, k, ...).
+ */
+int ozaki_split(int64_t m, int64_t k, const double* A, int64_t lda, int32_t mode, int32_t slices,
+                int32_t executor, int32_t* exps, void* digits, void* ws, size_t ws_bytes,
+                void* stream);
+
+/* Workspace for the batched call below. */
+int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* opts, size_t* bytes);
+
+/*
+ * dm_purify_batched: purify `batch` independent Hamiltonians of possibly
+ * different sizes with the same options. H, P, n and n_occ are HOST arrays of
+ * length `batch`; H[b] and P[b] are device pointers (n[b] x n[b], leading
+ * dimension n[b]). infos (host, length batch, nullable) receives one report per
+ * matrix. Each matrix stops on its own rule; the call returns DMP_OK when all
+ * converged, else the largest status seen.
+ */
+int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n,
+                      const int64_t* n_occ, double* const* P, const dmp_opts* opts,
+                      dmp_info* infos, void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace for the backward call below. */
+int dmp_backward_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
+
+/*
+ * dm_purify_backward: reverse mode through the purification dm_purify ran with
+ * `tape`, giving dL/dH for a loss L(P) from G = dL/dP (n x n, leading dimension
+ * n). Each step k is differentiated with its branch and iteration count frozen
+ * and with the dependence of c_k on P_k kept; the iterates are recomputed from
+ * the checkpoints of the tape. dLdH (n x n, leading dimension n) is the
+ * gradient with respect to H as a general matrix (the Gershgorin bounds enter
+ * through their extreme rows); for a symmetric perturbation of H_ij and H_ji
+ * the change of L is dLdH[i][j] + dLdH[j][i]. Products use the forward's mode.
+ */
+int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts* opts,
+                       const void* tape, size_t tape_bytes, const double* dLdP, double* dLdH,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Name of a return code. */
+const char* dmp_status_str(int code);
+
+/* Number of kernels this library has launched since load (all threads). */
+long long dmp_launch_count(void);
+
+/* Library version string. */
+const char* dmp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMP_H */

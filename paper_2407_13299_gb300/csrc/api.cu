@@ -1,0 +1,472 @@
+// C-ABI entry points of libdmp (declared in include/dmp.h).
+//
+// Host orchestration only: argument checks, workspace carving and kernel
+// launches. Every arithmetic step of the path runs in the kernels of this
+// library.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "dmp_internal.cuh"
+
+namespace dmp {
+
+std::atomic<long long> g_launches{0};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+// Sequential carving of a workspace into aligned regions.
+struct Carver {
+  size_t cur = 0;
+  size_t take(size_t bytes) {
+    const size_t off = cur;
+    cur = (cur + bytes + kAlign - 1) / kAlign * kAlign;
+    return off;
+  }
+};
+
+struct Opts {
+  int mode, s, beta, executor, max_iter, every;
+  double tol, energy_tol;
+};
+
+int normalize(const dmp_opts* o, Opts& out) {
+  if (o == nullptr) return DMP_ERR_INVALID_ARG;
+  out.mode = o->mode;
+  if (out.mode != DMP_FP64 && out.mode != DMP_OZAKI_INT8 && out.mode != DMP_OZAKI_BF16)
+    return DMP_ERR_INVALID_ARG;
+  out.beta = beta_of(out.mode);
+  out.s = o->slices == 0 ? 7 : o->slices;
+  if (out.mode != DMP_FP64) {
+    const int smax = out.beta == 7 ? 10 : 9;
+    if (out.s < 1 || out.s > smax) return DMP_ERR_INVALID_ARG;
+  } else {
+    out.s = 0;
+  }
+  out.executor = o->executor;
+  if (out.executor < DMP_EXEC_AUTO || out.executor > DMP_EXEC_TC) return DMP_ERR_INVALID_ARG;
+  if (out.mode == DMP_OZAKI_INT8 && out.executor == DMP_EXEC_AUTO) out.executor = DMP_EXEC_IMMA;
+  if (out.mode == DMP_OZAKI_BF16 && out.executor == DMP_EXEC_AUTO) out.executor = DMP_EXEC_TC;
+  if (out.mode == DMP_OZAKI_BF16 && out.executor == DMP_EXEC_IMMA) return DMP_ERR_UNSUPPORTED;
+  if (out.mode != DMP_FP64 && out.executor == DMP_EXEC_TC) return DMP_ERR_UNSUPPORTED;
+  if (out.mode == DMP_FP64) out.executor = 0;
+  out.max_iter = o->max_iter == 0 ? 100 : o->max_iter;
+  if (out.max_iter < 0) return DMP_ERR_INVALID_ARG;
+  out.every = o->checkpoint_every == 0 ? 8 : o->checkpoint_every;
+  if (out.every < 1) return DMP_ERR_INVALID_ARG;
+  out.tol = o->tol == 0.0 ? 1e-10 : o->tol;
+  out.energy_tol = o->energy_tol;
+  if (!(out.tol >= 0.0) || !(out.energy_tol >= 0.0)) return DMP_ERR_INVALID_ARG;
+  return DMP_OK;
+}
+
+// Level sums stay exact in int32 while s k (2^beta - 1)^2 < 2^31.
+bool levels_fit_int32(int64_t k, int s, int beta) {
+  const double bound = static_cast<double>(s) * static_cast<double>(k) *
+                       std::pow(2.0, beta) * std::pow(2.0, beta);
+  return bound < 2147483648.0;
+}
+
+int elem_bytes(int executor) { return executor == DMP_EXEC_TC ? 2 : 1; }
+int elem_kind(int executor) { return executor == DMP_EXEC_TC ? 3 : 1; }
+
+#define DMP_CUDA(call)                       \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return DMP_ERR_CUDA; \
+  } while (0)
+
+// ---------------------------------------------------------------- dm_purify layout
+struct PurifyLayout {
+  size_t state, partials, rowbuf, expsP, expsX, Palt, X2, planesP, planesX, total;
+  int64_t n_pad, k_pad;
+};
+
+PurifyLayout purify_layout(int64_t n, const Opts& o) {
+  PurifyLayout L;
+  Carver c;
+  L.n_pad = round_up(n, kTileM);
+  L.k_pad = round_up(n, kPadK);
+  L.state = c.take(sizeof(PurifyState));
+  L.partials = c.take(static_cast<size_t>(kMeasureBlocks) * 8 * sizeof(double));
+  L.rowbuf = c.take(gershgorin_rowbuf_bytes(n));
+  L.expsP = c.take(static_cast<size_t>(L.n_pad) * sizeof(int32_t));
+  L.expsX = c.take(static_cast<size_t>(L.n_pad) * sizeof(int32_t));
+  L.Palt = c.take(static_cast<size_t>(n) * n * sizeof(double));
+  L.X2 = c.take(static_cast<size_t>(n) * n * sizeof(double));
+  if (o.mode != DMP_FP64) {
+    const size_t plane = static_cast<size_t>(o.s) * L.n_pad * L.k_pad * elem_bytes(o.executor);
+    L.planesP = c.take(plane);
+    L.planesX = c.take(plane);
+  } else {
+    L.planesP = L.planesX = 0;
+  }
+  L.total = c.cur;
+  return L;
+}
+
+// Tape: header, per-step coefficients, then checkpoints P_0, P_k, P_2k, ...
+struct TapeHeader {
+  int32_t magic, n, iters, every, n_ckpt, mode, s, executor;
+  int32_t status, row_min, row_max, lam_branch;
+  double lam, mu, h_min, h_max;
+};
+constexpr int32_t kTapeMagic = 0x444d5054;  // "DMPT"
+
+struct TapeLayout {
+  size_t header, coeffs, ckpt, total;
+  int n_ckpt;
+};
+
+TapeLayout tape_layout(int64_t n, const Opts& o) {
+  TapeLayout T;
+  Carver c;
+  T.header = c.take(sizeof(TapeHeader));
+  T.coeffs = c.take(static_cast<size_t>(o.max_iter + 1) * sizeof(double));
+  T.n_ckpt = o.max_iter / o.every + 1;
+  T.ckpt = c.take(static_cast<size_t>(T.n_ckpt) * n * n * sizeof(double));
+  T.total = c.cur;
+  return T;
+}
+
+inline char* at(void* base, size_t off) { return static_cast<char*>(base) + off; }
+
+}  // namespace
+}  // namespace dmp
+
+using namespace dmp;
+
+extern "C" {
+
+const char* dmp_version(void) { return "dmp 0.1 (sm_103a)"; }
+
+long long dmp_launch_count(void) { return g_launches.load(); }
+
+const char* dmp_status_str(int code) {
+  switch (code) {
+    case DMP_OK: return "DMP_OK";
+    case DMP_NOT_CONVERGED: return "DMP_NOT_CONVERGED";
+    case DMP_STALLED: return "DMP_STALLED";
+    case DMP_C_OUT_OF_RANGE: return "DMP_C_OUT_OF_RANGE";
+    case DMP_ERR_INVALID_ARG: return "DMP_ERR_INVALID_ARG";
+    case DMP_ERR_NONFINITE: return "DMP_ERR_NONFINITE";
+    case DMP_ERR_CUDA: return "DMP_ERR_CUDA";
+    case DMP_ERR_TIMEOUT: return "DMP_ERR_TIMEOUT";
+    case DMP_ERR_UNSUPPORTED: return "DMP_ERR_UNSUPPORTED";
+    case DMP_ERR_WORKSPACE: return "DMP_ERR_WORKSPACE";
+    default: return "DMP_UNKNOWN";
+  }
+}
+
+int dmp_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes) {
+  Opts o;
+  const int rc = normalize(opts, o);
+  if (rc != DMP_OK) return rc;
+  if (n < 2 || bytes == nullptr) return DMP_ERR_INVALID_ARG;
+  *bytes = purify_layout(n, o).total;
+  return DMP_OK;
+}
+
+int dmp_tape_size(int64_t n, const dmp_opts* opts, size_t* bytes) {
+  Opts o;
+  const int rc = normalize(opts, o);
+  if (rc != DMP_OK) return rc;
+  if (n < 2 || bytes == nullptr) return DMP_ERR_INVALID_ARG;
+  *bytes = tape_layout(n, o).total;
+  return DMP_OK;
+}
+
+int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_opts* opts,
+              double* P, int64_t ldp, dmp_info* info, void* ws, size_t ws_bytes, void* tape,
+              size_t tape_bytes, void* stream) {
+  Opts o;
+  int rc = normalize(opts, o);
+  if (rc != DMP_OK) return rc;
+  if (H == nullptr || P == nullptr || ws == nullptr) return DMP_ERR_INVALID_ARG;
+  if (n < 2 || ldh < n || ldp < n || n_occ <= 0 || n_occ >= n) return DMP_ERR_INVALID_ARG;
+  if (o.mode != DMP_FP64 && !levels_fit_int32(n, o.s, o.beta)) return DMP_ERR_UNSUPPORTED;
+  const PurifyLayout L = purify_layout(n, o);
+  if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
+  TapeLayout TL{};
+  if (tape != nullptr) {
+    TL = tape_layout(n, o);
+    if (tape_bytes < TL.total) return DMP_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  PurifyState* state = reinterpret_cast<PurifyState*>(at(ws, L.state));
+  double* partials = reinterpret_cast<double*>(at(ws, L.partials));
+  double* rowbuf = reinterpret_cast<double*>(at(ws, L.rowbuf));
+  int32_t* expsP = reinterpret_cast<int32_t*>(at(ws, L.expsP));
+  int32_t* expsX = reinterpret_cast<int32_t*>(at(ws, L.expsX));
+  double* Palt = reinterpret_cast<double*>(at(ws, L.Palt));
+  double* X2 = reinterpret_cast<double*>(at(ws, L.X2));
+  void* planesP = o.mode != DMP_FP64 ? at(ws, L.planesP) : nullptr;
+  void* planesX = o.mode != DMP_FP64 ? at(ws, L.planesX) : nullptr;
+
+  PurifyState init;
+  std::memset(&init, 0, sizeof(init));
+  init.tol = o.tol;
+  init.energy_tol = o.energy_tol;
+  init.max_iter = o.max_iter;
+  init.status = DMP_NOT_CONVERGED;
+  DMP_CUDA(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  DMP_CUDA(launch_gershgorin_init(H, n, ldh, n_occ, rowbuf, state, P, ldp, st));
+
+  double* tape_c = tape ? reinterpret_cast<double*>(at(tape, TL.coeffs)) : nullptr;
+  double* tape_ck = tape ? reinterpret_cast<double*>(at(tape, TL.ckpt)) : nullptr;
+
+  double* cur = P;
+  int64_t ldcur = ldp;
+  double* alt = Palt;
+  int64_t ldalt = n;
+  const int* done = &state->done;
+  for (int k = 0; k <= o.max_iter; ++k) {
+    if (tape != nullptr && k % o.every == 0) {
+      DMP_CUDA(cudaMemcpy2DAsync(tape_ck + static_cast<size_t>(k / o.every) * n * n, n * sizeof(double),
+                                 cur, ldcur * sizeof(double), n * sizeof(double), n,
+                                 cudaMemcpyDeviceToDevice, st));
+    }
+    EpiArgs e2{};
+    e2.kind = EPI_SYM_STORE;
+    e2.C = X2;
+    e2.ldc = n;
+    if (o.mode == DMP_FP64) {
+      DMP_CUDA(launch_gemm_f64(cur, ldcur, cur, ldcur, n, n, n, 1, e2, done, st));
+    } else {
+      DMP_CUDA(launch_split_rows(cur, n, n, ldcur, o.s, o.beta, expsP, planesP, L.n_pad, L.k_pad,
+                                 elem_kind(o.executor), nullptr, done, st));
+      DMP_CUDA(launch_ozaki_imma(static_cast<const int8_t*>(planesP), static_cast<const int8_t*>(planesP),
+                                 expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, o.s, o.beta, 1, e2, done, st));
+    }
+    DMP_CUDA(launch_measure(cur, ldcur, X2, n, H, ldh, n, partials, state, st));
+    int32_t flag_done = 0;
+    DMP_CUDA(cudaMemcpyAsync(&flag_done, &state->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DMP_CUDA(cudaStreamSynchronize(st));
+    if (flag_done) break;
+    if (tape != nullptr) {
+      DMP_CUDA(cudaMemcpyAsync(tape_c + k, &state->c, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    EpiArgs e3{};
+    e3.kind = EPI_PM_UPDATE;
+    e3.C = alt;
+    e3.ldc = ldalt;
+    e3.P = cur;
+    e3.ldp = ldcur;
+    e3.X2 = X2;
+    e3.ldx = n;
+    e3.state = state;
+    if (o.mode == DMP_FP64) {
+      DMP_CUDA(launch_gemm_f64(cur, ldcur, X2, n, n, n, n, 1, e3, done, st));
+    } else {
+      DMP_CUDA(launch_split_rows(X2, n, n, n, o.s, o.beta, expsX, planesX, L.n_pad, L.k_pad,
+                                 elem_kind(o.executor), nullptr, done, st));
+      DMP_CUDA(launch_ozaki_imma(static_cast<const int8_t*>(planesP), static_cast<const int8_t*>(planesX),
+                                 expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, o.s, o.beta, 1, e3, done, st));
+    }
+    std::swap(cur, alt);
+    std::swap(ldcur, ldalt);
+  }
+  if (cur != P) {
+    DMP_CUDA(cudaMemcpy2DAsync(P, ldp * sizeof(double), cur, ldcur * sizeof(double), n * sizeof(double), n,
+                               cudaMemcpyDeviceToDevice, st));
+  }
+  PurifyState fin;
+  DMP_CUDA(cudaMemcpyAsync(&fin, state, sizeof(fin), cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaStreamSynchronize(st));
+  if (tape != nullptr) {
+    TapeHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kTapeMagic;
+    h.n = static_cast<int32_t>(n);
+    h.iters = fin.iter;
+    h.every = o.every;
+    h.n_ckpt = TL.n_ckpt;
+    h.mode = o.mode;
+    h.s = o.s;
+    h.executor = o.executor;
+    h.status = fin.status;
+    h.row_min = fin.row_min;
+    h.row_max = fin.row_max;
+    h.lam_branch = fin.lam_branch;
+    h.lam = fin.lam;
+    h.mu = fin.mu;
+    h.h_min = fin.h_min;
+    h.h_max = fin.h_max;
+    DMP_CUDA(cudaMemcpyAsync(at(tape, TL.header), &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    DMP_CUDA(cudaStreamSynchronize(st));
+  }
+  if (info != nullptr) {
+    info->status = fin.status;
+    info->iters = fin.iter;
+    info->slices_used = o.s;
+    info->executor_used = o.executor;
+    info->energy = fin.energy;
+    info->band_energy = 2.0 * fin.energy;
+    info->idem = std::sqrt(fin.idem2);
+    info->trace = fin.t1;
+    info->c_last = fin.c;
+    info->h_min = fin.h_min;
+    info->h_max = fin.h_max;
+  }
+  return fin.status;
+}
+
+int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int32_t slices,
+                              int32_t executor, size_t* bytes) {
+  dmp_opts d{};
+  d.mode = mode;
+  d.slices = slices;
+  d.executor = executor;
+  Opts o;
+  const int rc = normalize(&d, o);
+  if (rc != DMP_OK) return rc;
+  if (m < 0 || n < 0 || k < 0 || bytes == nullptr) return DMP_ERR_INVALID_ARG;
+  if (o.mode == DMP_FP64) {
+    *bytes = 0;
+    return DMP_OK;
+  }
+  Carver c;
+  const int64_t m_pad = round_up(std::max<int64_t>(m, 1), kTileM);
+  const int64_t n_pad = round_up(std::max<int64_t>(n, 1), kTileN);
+  const int64_t k_pad = round_up(std::max<int64_t>(k, 1), kPadK);
+  c.take(m_pad * sizeof(int32_t));
+  c.take(n_pad * sizeof(int32_t));
+  c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o.executor));
+  c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o.executor));
+  c.take(static_cast<size_t>(n) * k * sizeof(double));
+  *bytes = c.cur;
+  return DMP_OK;
+}
+
+static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                        int64_t ldb, const EpiArgs& epi, int32_t mode, int32_t slices, int32_t executor,
+                        void* ws, size_t ws_bytes, void* stream) {
+  dmp_opts d{};
+  d.mode = mode;
+  d.slices = slices;
+  d.executor = executor;
+  Opts o;
+  const int rc = normalize(&d, o);
+  if (rc != DMP_OK) return rc;
+  if (m < 0 || n < 0 || k < 0) return DMP_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return DMP_OK;
+  if (A == nullptr || B == nullptr || lda < k || ldb < n) return DMP_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (o.mode == DMP_FP64) {
+    if (epi.kind == EPI_LEVELS) return DMP_ERR_INVALID_ARG;
+    DMP_CUDA(launch_gemm_f64(A, lda, B, ldb, m, n, k, 0, epi, nullptr, st));
+    return DMP_OK;
+  }
+  if (!levels_fit_int32(k, o.s, o.beta)) return DMP_ERR_UNSUPPORTED;
+  size_t need = 0;
+  ozaki_gemm_workspace_size(m, n, k, mode, slices, executor, &need);
+  if (ws == nullptr || ws_bytes < need) return DMP_ERR_WORKSPACE;
+  Carver c;
+  const int64_t m_pad = round_up(m, kTileM);
+  const int64_t n_pad = round_up(n, kTileN);
+  const int64_t k_pad = round_up(std::max<int64_t>(k, 1), kPadK);
+  int32_t* ea = reinterpret_cast<int32_t*>(at(ws, c.take(m_pad * sizeof(int32_t))));
+  int32_t* eb = reinterpret_cast<int32_t*>(at(ws, c.take(n_pad * sizeof(int32_t))));
+  void* pa = at(ws, c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o.executor)));
+  void* pb = at(ws, c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o.executor)));
+  double* Bt = reinterpret_cast<double*>(at(ws, c.take(static_cast<size_t>(n) * k * sizeof(double))));
+  DMP_CUDA(launch_split_rows(A, m, k, lda, o.s, o.beta, ea, pa, m_pad, k_pad, elem_kind(o.executor), nullptr,
+                             nullptr, st));
+  DMP_CUDA(launch_transpose(B, k, n, ldb, Bt, st));
+  DMP_CUDA(launch_split_rows(Bt, n, k, k, o.s, o.beta, eb, pb, n_pad, k_pad, elem_kind(o.executor), nullptr,
+                             nullptr, st));
+  DMP_CUDA(launch_ozaki_imma(static_cast<const int8_t*>(pa), static_cast<const int8_t*>(pb), ea, eb, m, n,
+                             m_pad, n_pad, k_pad, o.s, o.beta, 0, epi, nullptr, st));
+  return DMP_OK;
+}
+
+int ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+               int64_t ldb, double* C, int64_t ldc, int32_t mode, int32_t slices, int32_t executor,
+               void* ws, size_t ws_bytes, void* stream) {
+  if (C == nullptr || ldc < n) return DMP_ERR_INVALID_ARG;
+  EpiArgs e{};
+  e.kind = EPI_STORE;
+  e.C = C;
+  e.ldc = ldc;
+  return ozaki_common(m, n, k, A, lda, B, ldb, e, mode, slices, executor, ws, ws_bytes, stream);
+}
+
+int ozaki_level_sums(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                     int64_t ldb, int32_t* S, int32_t mode, int32_t slices, int32_t executor, void* ws,
+                     size_t ws_bytes, void* stream) {
+  if (S == nullptr || mode == DMP_FP64) return DMP_ERR_INVALID_ARG;
+  EpiArgs e{};
+  e.kind = EPI_LEVELS;
+  e.levels = S;
+  return ozaki_common(m, n, k, A, lda, B, ldb, e, mode, slices, executor, ws, ws_bytes, stream);
+}
+
+int ozaki_split(int64_t m, int64_t k, const double* A, int64_t lda, int32_t mode, int32_t slices,
+                int32_t executor, int32_t* exps, void* digits, void* ws, size_t ws_bytes, void* stream) {
+  dmp_opts d{};
+  d.mode = mode;
+  d.slices = slices;
+  d.executor = executor;
+  Opts o;
+  const int rc = normalize(&d, o);
+  if (rc != DMP_OK) return rc;
+  if (o.mode == DMP_FP64) return DMP_ERR_INVALID_ARG;
+  if (m <= 0 || k <= 0 || A == nullptr || lda < k || exps == nullptr || digits == nullptr)
+    return DMP_ERR_INVALID_ARG;
+  size_t need = 0;
+  ozaki_gemm_workspace_size(m, 1, k, mode, slices, executor, &need);
+  if (ws == nullptr || ws_bytes < need) return DMP_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver c;
+  const int64_t m_pad = round_up(m, kTileM);
+  const int64_t k_pad = round_up(k, kPadK);
+  int32_t* ea = reinterpret_cast<int32_t*>(at(ws, c.take(m_pad * sizeof(int32_t))));
+  c.take(round_up(1, kTileN) * sizeof(int32_t));
+  const int eb = elem_bytes(o.executor);
+  char* pa = at(ws, c.take(static_cast<size_t>(o.s) * m_pad * k_pad * eb));
+  DMP_CUDA(launch_split_rows(A, m, k, lda, o.s, o.beta, ea, pa, m_pad, k_pad, elem_kind(o.executor), nullptr,
+                             nullptr, st));
+  DMP_CUDA(cudaMemcpyAsync(exps, ea, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  for (int i = 0; i < o.s; ++i) {
+    DMP_CUDA(cudaMemcpy2DAsync(static_cast<char*>(digits) + static_cast<size_t>(i) * m * k * eb, k * eb,
+                               pa + static_cast<size_t>(i) * m_pad * k_pad * eb, k_pad * eb, k * eb, m,
+                               cudaMemcpyDeviceToDevice, st));
+  }
+  return DMP_OK;
+}
+
+int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* opts, size_t* bytes) {
+  (void)batch;
+  (void)n;
+  (void)opts;
+  (void)bytes;
+  return DMP_ERR_UNSUPPORTED;
+}
+
+int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, const int64_t* n_occ,
+                      double* const* P, const dmp_opts* opts, dmp_info* infos, void* ws, size_t ws_bytes,
+                      void* stream) {
+  (void)batch; (void)H; (void)n; (void)n_occ; (void)P; (void)opts; (void)infos; (void)ws;
+  (void)ws_bytes; (void)stream;
+  return DMP_ERR_UNSUPPORTED;
+}
+
+int dmp_backward_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes) {
+  (void)n; (void)opts; (void)bytes;
+  return DMP_ERR_UNSUPPORTED;
+}
+
+int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts* opts, const void* tape,
+                       size_t tape_bytes, const double* dLdP, double* dLdH, void* ws, size_t ws_bytes,
+                       void* stream) {
+  (void)H; (void)n; (void)n_occ; (void)opts; (void)tape; (void)tape_bytes; (void)dLdP; (void)dLdH;
+  (void)ws; (void)ws_bytes; (void)stream;
+  return DMP_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal declarations shared by the libdmp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/dmp.h"
+
+namespace dmp {
+
+// ---------------------------------------------------------------- constants
+constexpr int kMaxSlices = 10;   // beta = 7: 70 bits; beta = 8 is limited to 9 (72 bits)
+constexpr int kTileM = 128;      // output tile rows of the slice-pair GEMMs
+constexpr int kTileN = 128;      // output tile columns
+constexpr int kPadK = 64;        // digit planes are padded to a multiple of this along K
+constexpr int32_t kBadExp = 0x7fffffff;  // row exponent of a row holding NaN/Inf
+
+inline int beta_of(int mode) { return mode == DMP_OZAKI_BF16 ? 8 : 7; }
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ---------------------------------------------------------------- launch accounting
+extern std::atomic<long long> g_launches;
+inline void count_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------- device-side run state
+// One per purification. Written by the measurement kernel, read by the update
+// epilogue and the host.
+struct PurifyState {
+  // measures of the current iterate P_k
+  double t1, t2, t3, idem2, energy;
+  // band-energy history (Tr(HK) of the last three iterates, newest first)
+  double band[3];
+  // coefficient and update weights P' = alpha P + b2 P^2 + b3 P^3
+  double c, alpha, b2, b3;
+  // initial-guess scalars
+  double h_min, h_max, mu, lam;
+  int32_t row_min, row_max, lam_branch;
+  int32_t iter;     // updates applied so far
+  int32_t status;   // DMP_* code once done
+  int32_t done;     // nonzero once a stopping rule fired (kernels then skip work)
+  int32_t nonfinite;
+  int32_t branch;   // 1: c >= 1/2, 2: c < 1/2
+  // options copied for the device
+  double tol, energy_tol;
+  int32_t max_iter;
+  int32_t pad_;
+};
+
+// ---------------------------------------------------------------- kernels (host launchers)
+// All launchers return cudaSuccess or the launch error; they count launches.
+
+// Row split: exponents e_r and `s` digit planes of beta bits of the m x k matrix
+// A (leading dimension lda). Planes are [s][m_pad][k_pad], element type int8
+// (elem_bytes 1), int16 (2, plain integers) or bfloat16 (3, same integers in
+// bf16). Padding rows/columns are zero. Sets *flag to 1 if A holds a NaN/Inf.
+cudaError_t launch_split_rows(const double* A, int64_t m, int64_t k, int64_t lda, int s, int beta,
+                              int32_t* exps, void* planes, int64_t m_pad, int64_t k_pad,
+                              int elem_kind, int* flag, const int* done, cudaStream_t st);
+
+// Out-of-place transpose (m x n, lda) -> (n x m, leading dimension m).
+cudaError_t launch_transpose(const double* A, int64_t m, int64_t n, int64_t lda, double* At,
+                             cudaStream_t st);
+
+enum EpiKind { EPI_STORE = 0, EPI_SYM_STORE = 1, EPI_PM_UPDATE = 2, EPI_LEVELS = 3 };
+
+struct EpiArgs {
+  int kind;
+  double* C;          // output (EPI_STORE / EPI_SYM_STORE / EPI_PM_UPDATE: P_next)
+  int64_t ldc;
+  const double* P;    // EPI_PM_UPDATE: current iterate
+  const double* X2;   // EPI_PM_UPDATE: P^2
+  int64_t ldp;        // leading dimension of P
+  int64_t ldx;        // leading dimension of X2
+  const PurifyState* state;  // EPI_PM_UPDATE weights
+  int32_t* levels;    // EPI_LEVELS: [s][m][n]
+};
+
+// IMMA executor: level sums of int8 planes with fused FP64 recombination.
+// sym != 0 computes only the tiles on and above the diagonal (m == n, B planes
+// are the transposed operand of a symmetric product) and mirrors them.
+cudaError_t launch_ozaki_imma(const int8_t* A, const int8_t* B, const int32_t* ea, const int32_t* eb,
+                              int64_t m, int64_t n, int64_t m_pad, int64_t n_pad, int64_t k_pad,
+                              int s, int beta, int sym, const EpiArgs& epi, const int* done,
+                              cudaStream_t st);
+
+// FP64 executor: C = A B (A m x k, B k x n row-major) with the same epilogues.
+cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m,
+                            int64_t n, int64_t k, int sym, const EpiArgs& epi, const int* done,
+                            cudaStream_t st);
+
+// Purification support kernels.
+cudaError_t launch_gershgorin_init(const double* H, int64_t n, int64_t ldh, int64_t n_occ,
+                                   double* rowbuf, PurifyState* state, double* P, int64_t ldp,
+                                   cudaStream_t st);
+size_t gershgorin_rowbuf_bytes(int64_t n);
+cudaError_t launch_measure(const double* P, int64_t ldp, const double* X2, int64_t ldx,
+                           const double* H, int64_t ldh, int64_t n, double* partials,
+                           PurifyState* state, cudaStream_t st);
+cudaError_t launch_copy_matrix(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t m,
+                               int64_t n, cudaStream_t st);
+
+constexpr int kMeasureBlocks = 304;  // 2 x 152 SMs; fixed so sums are reproducible
+
+}  // namespace dmp
+
+namespace dmp {
+
+// ---------------------------------------------------------------- shared epilogue
+// Applies one output element v = C[r][c] of a product. `mirror` writes the
+// transposed element as well (off-diagonal tiles of a symmetric product).
+__device__ __forceinline__ void epi_apply(const EpiArgs& e, int64_t r, int64_t c, double v,
+                                          bool mirror) {
+  if (e.kind == EPI_PM_UPDATE) {
+    const double p = e.P[r * e.ldp + c];
+    const double x2 = e.X2[r * e.ldx + c];
+    v = e.state->alpha * p + e.state->b2 * x2 + e.state->b3 * v;
+  }
+  e.C[r * e.ldc + c] = v;
+  if (mirror) e.C[c * e.ldc + r] = v;
+}
+
+// Upper-triangle tile enumeration: tile index -> (bi, bj) with bi <= bj, row-major.
+__device__ __forceinline__ void upper_tile(int idx, int T, int& bi, int& bj) {
+  int b = 0;
+  int start = 0;
+  while (start + (T - b) <= idx) {
+    start += T - b;
+    ++b;
+  }
+  bi = b;
+  bj = b + (idx - start);
+}
+
+}  // namespace dmp

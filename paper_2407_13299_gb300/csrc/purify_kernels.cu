@@ -1,0 +1,331 @@
+// Initial guess, per-iterate measures and the stopping rules of canonical
+// purification (the Palser-Manolopoulos method cited in Sec. "Introduction";
+// halt rules of Sec. "Implementation Details"). All in float64.
+//
+// Symmetry: only the upper triangle of H is read (element (i, j) is taken as
+// H[min(i,j)][max(i,j)]), so P_0 and every iterate are exactly symmetric. The
+// measures of an iterate use that symmetry too: each reduction reads the upper
+// triangle and doubles the strictly-upper part.
+//
+// Reductions are deterministic: fixed grid, fixed per-thread order, fixed tree.
+
+#include "dmp_internal.cuh"
+
+namespace dmp {
+
+namespace {
+
+constexpr int kRowThreads = 256;
+constexpr int kColChunks = 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Strictly-upper row sums U_i = sum_{j>i} |H_ij| and the diagonal, one CTA per row.
+__global__ void __launch_bounds__(kRowThreads)
+gersh_rows_kernel(const double* __restrict__ H, int64_t n, int64_t ldh, double* __restrict__ U,
+                  double* __restrict__ D, int* __restrict__ flag) {
+  const int64_t i = blockIdx.x;
+  __shared__ double red[kRowThreads / 32];
+  double sacc = 0.0;
+  bool bad = false;
+  const double* row = H + i * ldh;
+  for (int64_t j = i + 1 + threadIdx.x; j < n; j += kRowThreads) {
+    const double v = row[j];
+    bad |= !isfinite(v);
+    sacc += fabs(v);
+  }
+  sacc = warp_sum(sacc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sacc;
+  if (bad) atomicExch(flag, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kRowThreads / 32; ++w) t += red[w];
+    U[i] = t;
+    const double d = row[i];
+    if (!isfinite(d)) atomicExch(flag, 1);
+    D[i] = d;
+  }
+}
+
+// Column partial sums of the strict upper triangle: Cp[chunk][c] = sum over rows
+// r < c of the chunk of |H_rc|. Threads own columns, so reads are coalesced.
+__global__ void gersh_cols_kernel(const double* __restrict__ H, int64_t n, int64_t ldh,
+                                  double* __restrict__ Cp) {
+  const int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int chunk = blockIdx.y;
+  if (c >= n) return;
+  const int64_t rows_per = (n + kColChunks - 1) / kColChunks;
+  const int64_t r0 = chunk * rows_per;
+  const int64_t r1 = min(r0 + rows_per, c);
+  double sacc = 0.0;
+  for (int64_t r = r0; r < r1; ++r) sacc += fabs(H[r * ldh + c]);
+  Cp[static_cast<int64_t>(chunk) * n + c] = sacc;
+}
+
+// Bounds, mu, lambda -> state. One CTA.
+__global__ void __launch_bounds__(1024)
+gersh_final_kernel(int64_t n, int64_t n_occ, const double* __restrict__ U, const double* __restrict__ D,
+                   const double* __restrict__ Cp, PurifyState* st, const int* flag) {
+  __shared__ double s_lo[1024], s_hi[1024], s_tr[1024];
+  __shared__ int s_ilo[1024], s_ihi[1024];
+  const int t = threadIdx.x;
+  double lo = 1.0 / 0.0, hi = -1.0 / 0.0, tr = 0.0;
+  int ilo = 0x7fffffff, ihi = 0x7fffffff;
+  for (int64_t i = t; i < n; i += blockDim.x) {
+    double rad = U[i];
+    for (int ch = 0; ch < kColChunks; ++ch) rad += Cp[static_cast<int64_t>(ch) * n + i];
+    const double l = D[i] - rad, h = D[i] + rad;
+    if (l < lo) { lo = l; ilo = static_cast<int>(i); }
+    if (h > hi) { hi = h; ihi = static_cast<int>(i); }
+    tr += D[i];
+  }
+  s_lo[t] = lo; s_hi[t] = hi; s_tr[t] = tr; s_ilo[t] = ilo; s_ihi[t] = ihi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      // keep the first index on ties
+      if (s_lo[t + o] < s_lo[t] || (s_lo[t + o] == s_lo[t] && s_ilo[t + o] < s_ilo[t])) {
+        s_lo[t] = s_lo[t + o];
+        s_ilo[t] = s_ilo[t + o];
+      }
+      if (s_hi[t + o] > s_hi[t] || (s_hi[t + o] == s_hi[t] && s_ihi[t + o] < s_ihi[t])) {
+        s_hi[t] = s_hi[t + o];
+        s_ihi[t] = s_ihi[t + o];
+      }
+      s_tr[t] += s_tr[t + o];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double dn = static_cast<double>(n);
+    const double mu = s_tr[0] / dn;
+    st->h_min = s_lo[0];
+    st->h_max = s_hi[0];
+    st->row_min = s_ilo[0];
+    st->row_max = s_ihi[0];
+    st->mu = mu;
+    if (*flag) {
+      st->nonfinite = 1;
+      st->status = DMP_ERR_NONFINITE;
+      st->done = 1;
+      st->lam = 0.0;
+      return;
+    }
+    if (!(s_hi[0] > mu && mu > s_lo[0])) {  // H is a multiple of the identity
+      st->status = DMP_ERR_INVALID_ARG;
+      st->done = 1;
+      st->lam = 0.0;
+      return;
+    }
+    const double lam1 = static_cast<double>(n_occ) / (s_hi[0] - mu);
+    const double lam2 = static_cast<double>(n - n_occ) / (mu - s_lo[0]);
+    st->lam_branch = lam1 <= lam2 ? 1 : 2;
+    st->lam = lam1 <= lam2 ? lam1 : lam2;
+  }
+}
+
+// P0 = (lambda/n)(mu I - H) + (n_occ/n) I on 32 x 32 upper tiles, mirrored.
+__global__ void p0_kernel(const double* __restrict__ H, int64_t n, int64_t ldh, int64_t n_occ,
+                          const PurifyState* st, double* __restrict__ P, int64_t ldp, int T) {
+  __shared__ double tile[32][33];
+  int bi, bj;
+  upper_tile(blockIdx.x, T, bi, bj);
+  const double dn = static_cast<double>(n);
+  const double a = st->lam / dn, mu = st->mu, occ = static_cast<double>(n_occ) / dn;
+  const int64_t r0 = static_cast<int64_t>(bi) * 32, c0 = static_cast<int64_t>(bj) * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + y, c = c0 + threadIdx.x;
+    if (r < n && c < n) tile[y][threadIdx.x] = H[r * ldh + c];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int x = threadIdx.x;
+    const int64_t r = r0 + y, c = c0 + x;
+    if (r < n && c < n) {
+      double v;
+      if (bi == bj) {
+        // on the diagonal tile the lower half takes the mirror of the upper half
+        const double h = (y <= x) ? tile[y][x] : tile[x][y];
+        v = (r == c) ? a * (mu - h) + occ : -a * h;
+      } else {
+        v = -a * tile[y][x];
+      }
+      P[r * ldp + c] = v;
+    }
+  }
+  if (bi != bj) {
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+      // write the transposed tile: P[c0 + y][r0 + x] = -a H[r0 + x][c0 + y]
+      const int64_t r = c0 + y, c = r0 + threadIdx.x;
+      if (r < n && c < n) P[r * ldp + c] = -a * tile[threadIdx.x][y];
+    }
+  }
+}
+
+// Per-block partial measures of the iterate over the upper triangle: rows
+// i = blockIdx.x + k * gridDim.x.
+//   0: sum P_ii      1: sum X2_ii
+//   2: diag P X2     3: upper P X2
+//   4: diag (X2-P)^2 5: upper (X2-P)^2
+//   6: diag P H      7: upper P H
+__global__ void __launch_bounds__(256)
+measure_kernel(const double* __restrict__ P, int64_t ldp, const double* __restrict__ X2, int64_t ldx,
+               const double* __restrict__ H, int64_t ldh, int64_t n, double* __restrict__ part,
+               const PurifyState* st) {
+  if (st->done) return;
+  double u_px = 0.0, u_id = 0.0, u_ph = 0.0;
+  double d_p = 0.0, d_x = 0.0, d_px = 0.0, d_id = 0.0, d_ph = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double* pr = P + i * ldp;
+    const double* xr = X2 + i * ldx;
+    const double* hr = H + i * ldh;
+    if (threadIdx.x == 0) {
+      const double p = pr[i], x = xr[i], h = hr[i];
+      d_p += p;
+      d_x += x;
+      d_px += p * x;
+      d_id += (x - p) * (x - p);
+      d_ph += p * h;
+    }
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const double p = pr[j], x = xr[j], h = hr[j];
+      u_px += p * x;
+      u_id += (x - p) * (x - p);
+      u_ph += p * h;
+    }
+  }
+  __shared__ double red[8][8];
+  double v[8] = {d_p, d_x, d_px, u_px, d_id, u_id, d_ph, u_ph};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = warp_sum(v[q]);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[w][q] = v[q];
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double t = 0.0;
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][threadIdx.x];
+    part[static_cast<int64_t>(blockIdx.x) * 8 + threadIdx.x] = t;
+  }
+}
+
+// Sum the partials in fixed order and apply the stopping rules; one CTA.
+__global__ void measure_final_kernel(const double* __restrict__ part, int nblocks, PurifyState* st) {
+  if (st->done) return;
+  __shared__ double tot[8];
+  if (threadIdx.x < 8) {
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += part[static_cast<int64_t>(b) * 8 + threadIdx.x];
+    tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double t1 = tot[0], t2 = tot[1];
+  const double t3 = tot[2] + 2.0 * tot[3];
+  const double idem2 = tot[4] + 2.0 * tot[5];
+  const double energy = tot[6] + 2.0 * tot[7];
+  st->t1 = t1;
+  st->t2 = t2;
+  st->t3 = t3;
+  st->idem2 = idem2;
+  st->energy = energy;
+  if (!isfinite(t1) || !isfinite(t2) || !isfinite(t3) || !isfinite(idem2) || !isfinite(energy)) {
+    st->nonfinite = 1;
+    st->status = DMP_ERR_NONFINITE;
+    st->done = 1;
+    return;
+  }
+  const int k = st->iter;
+  st->band[2] = st->band[1];
+  st->band[1] = st->band[0];
+  st->band[0] = 2.0 * energy;
+  const double idem = sqrt(idem2);
+  if (idem < st->tol) {
+    st->status = DMP_OK;
+    st->done = 1;
+    return;
+  }
+  const double b0 = st->band[0], b1 = st->band[1], b2 = st->band[2];
+  if (k >= 2 && b0 > b1 && b1 > b2 && fabs(b0 - b1) < 1e-2 && fabs(b1 - b2) < 1e-2) {
+    st->status = DMP_STALLED;
+    st->done = 1;
+    return;
+  }
+  if (st->energy_tol > 0.0 && k >= 1 && fabs(b0 - b1) < st->energy_tol) {
+    st->status = DMP_OK;
+    st->done = 1;
+    return;
+  }
+  if (k >= st->max_iter) {
+    st->status = DMP_NOT_CONVERGED;
+    st->done = 1;
+    return;
+  }
+  const double td = t1 - t2;
+  if (!(td > 0.0)) {
+    st->status = DMP_C_OUT_OF_RANGE;
+    st->done = 1;
+    return;
+  }
+  const double c = (t2 - t3) / td;
+  if (!(c >= 0.0 && c <= 1.0)) {
+    st->status = DMP_C_OUT_OF_RANGE;
+    st->done = 1;
+    return;
+  }
+  st->c = c;
+  if (c >= 0.5) {
+    st->alpha = 0.0;
+    st->b2 = (1.0 + c) / c;
+    st->b3 = -1.0 / c;
+    st->branch = 1;
+  } else {
+    st->alpha = (1.0 - 2.0 * c) / (1.0 - c);
+    st->b2 = (1.0 + c) / (1.0 - c);
+    st->b3 = -1.0 / (1.0 - c);
+    st->branch = 2;
+  }
+  st->iter = k + 1;
+}
+
+}  // namespace
+
+cudaError_t launch_gershgorin_init(const double* H, int64_t n, int64_t ldh, int64_t n_occ,
+                                   double* rowbuf, PurifyState* state, double* P, int64_t ldp,
+                                   cudaStream_t st) {
+  double* U = rowbuf;
+  double* D = rowbuf + n;
+  double* Cp = rowbuf + 2 * n;
+  int* flag = reinterpret_cast<int*>(rowbuf + 2 * n + static_cast<int64_t>(kColChunks) * n);
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  gersh_rows_kernel<<<static_cast<unsigned>(n), kRowThreads, 0, st>>>(H, n, ldh, U, D, flag);
+  dim3 cg(static_cast<unsigned>((n + 127) / 128), kColChunks);
+  gersh_cols_kernel<<<cg, 128, 0, st>>>(H, n, ldh, Cp);
+  gersh_final_kernel<<<1, 1024, 0, st>>>(n, n_occ, U, D, Cp, state, flag);
+  const int T = static_cast<int>((n + 31) / 32);
+  p0_kernel<<<T * (T + 1) / 2, dim3(32, 8), 0, st>>>(H, n, ldh, n_occ, state, P, ldp, T);
+  count_launch(4);
+  return cudaGetLastError();
+}
+
+size_t gershgorin_rowbuf_bytes(int64_t n) {
+  return static_cast<size_t>((2 + kColChunks) * n + 1) * sizeof(double);
+}
+
+cudaError_t launch_measure(const double* P, int64_t ldp, const double* X2, int64_t ldx,
+                           const double* H, int64_t ldh, int64_t n, double* partials,
+                           PurifyState* state, cudaStream_t st) {
+  measure_kernel<<<kMeasureBlocks, 256, 0, st>>>(P, ldp, X2, ldx, H, ldh, n, partials, state);
+  measure_final_kernel<<<1, 32, 0, st>>>(partials, kMeasureBlocks, state);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+}  // namespace dmp

@@ -1,0 +1,235 @@
+"""Python binding of libdmp (include/dmp.h).
+
+Argument marshalling only: tensors are passed to the C ABI as raw device
+pointers, workspaces are allocated as torch byte tensors, and every step of the
+computation runs in libdmp's CUDA kernels. There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmp.so")
+
+MODES = {"fp64": 0, "int8": 1, "bf16": 2}
+EXECUTORS = {"auto": 0, "imma": 1, "tc": 2}
+BETA = {"int8": 7, "bf16": 8}
+
+OK, NOT_CONVERGED, STALLED, C_OUT_OF_RANGE = 0, 1, 2, 3
+ERR_INVALID_ARG, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_WORKSPACE = -1, -2, -3, -4, -5, -6
+
+
+class DmpError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {status_str(code)} ({code})")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("slices", ctypes.c_int32), ("executor", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tol", ctypes.c_double), ("energy_tol", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("slices_used", ctypes.c_int32),
+                ("executor_used", ctypes.c_int32), ("energy", ctypes.c_double),
+                ("band_energy", ctypes.c_double), ("idem", ctypes.c_double), ("trace", ctypes.c_double),
+                ("c_last", ctypes.c_double), ("h_min", ctypes.c_double), ("h_max", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_szp = ctypes.POINTER(ctypes.c_size_t)
+
+# exported symbol -> (restype, argtypes); the test suite checks this list against include/dmp.h
+SIGNATURES = {
+    "dmp_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
+    "dmp_tape_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
+    "dm_purify": (ctypes.c_int, [_vp, _i64, _i64, _i64, ctypes.POINTER(Opts), _vp, _i64,
+                                 ctypes.POINTER(Info), _vp, _sz, _vp, _sz, _vp]),
+    "ozaki_gemm_workspace_size": (ctypes.c_int, [_i64, _i64, _i64, _i32, _i32, _i32, _szp]),
+    "ozaki_gemm": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _i32, _i32,
+                                  _vp, _sz, _vp]),
+    "ozaki_level_sums": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i32, _i32, _i32,
+                                        _vp, _sz, _vp]),
+    "ozaki_split": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "dmp_batched_workspace_size": (ctypes.c_int, [_i32, ctypes.POINTER(_i64), ctypes.POINTER(Opts), _szp]),
+    "dm_purify_batched": (ctypes.c_int, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                         ctypes.POINTER(_vp), ctypes.POINTER(Opts), ctypes.POINTER(Info), _vp,
+                                         _sz, _vp]),
+    "dmp_backward_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
+    "dm_purify_backward": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(Opts), _vp, _sz, _vp, _vp, _vp,
+                                          _sz, _vp]),
+    "dmp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "dmp_launch_count": (ctypes.c_longlong, []),
+    "dmp_version": (ctypes.c_char_p, []),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdmp.so (built by paper_2407_13299_gb300.build) once."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libdmp.so not built ({LIB_PATH}); run paper_2407_13299_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_str(code: int) -> str:
+    try:
+        return lib().dmp_status_str(int(code)).decode()
+    except ImportError:
+        return str(code)
+
+
+def launch_count() -> int:
+    """Kernels launched by libdmp in this process so far."""
+    return int(lib().dmp_launch_count())
+
+
+def _check(code: int, where: str, allow_status: bool = False) -> int:
+    if code < 0 or (code > 0 and not allow_status):
+        raise DmpError(code, where)
+    return code
+
+
+def _stream_ptr(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+            raise TypeError("expected a float64 CUDA tensor")
+
+
+def make_opts(mode="int8", slices=7, executor="auto", tol=1e-10, energy_tol=0.0, max_iter=100,
+              checkpoint_every=8) -> Opts:
+    return Opts(MODES[mode], int(slices) if mode != "fp64" else 0, EXECUTORS[executor], int(max_iter),
+                int(checkpoint_every), 0, float(tol), float(energy_tol))
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def purify_workspace_bytes(n: int, opts: Opts) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().dmp_workspace_size(n, ctypes.byref(opts), ctypes.byref(b)), "dmp_workspace_size")
+    return b.value
+
+
+def tape_bytes(n: int, opts: Opts) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().dmp_tape_size(n, ctypes.byref(opts), ctypes.byref(b)), "dmp_tape_size")
+    return b.value
+
+
+def purify(H: torch.Tensor, n_occ: int, mode="int8", slices=7, executor="auto", tol=1e-10,
+           energy_tol=0.0, max_iter=100, P=None, ws=None, tape=None, stream=None, checkpoint_every=8):
+    """dm_purify on a float64 CUDA tensor H. Returns (P, info dict).
+
+    `ws`, `P` and `tape` may be passed preallocated (see purify_workspace_bytes,
+    tape_bytes) so that repeated calls allocate nothing.
+    """
+    _require_cuda(H)
+    n = H.shape[0]
+    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every)
+    if P is None:
+        P = torch.empty_like(H)
+    if ws is None:
+        ws = workspace(purify_workspace_bytes(n, opts), H.device)
+    info = Info()
+    tp = tape.data_ptr() if tape is not None else None
+    tb = tape.numel() if tape is not None else 0
+    code = lib().dm_purify(H.data_ptr(), n, H.stride(0), int(n_occ), ctypes.byref(opts), P.data_ptr(),
+                           P.stride(0), ctypes.byref(info), ws.data_ptr(), ws.numel(), tp, tb,
+                           _stream_ptr(stream))
+    _check(code, "dm_purify", allow_status=True)
+    return P, info.as_dict()
+
+
+def purify_host(H_host: torch.Tensor, n_occ: int, **kw):
+    """End-to-end call from host memory: copies H to the device, purifies, and
+    copies P back (pinned host tensors keep the copies asynchronous)."""
+    H = H_host.to("cuda", non_blocking=True)
+    P, info = purify(H, n_occ, **kw)
+    out = torch.empty(P.shape, dtype=P.dtype, pin_memory=H_host.is_pinned())
+    out.copy_(P, non_blocking=False)
+    return out, info
+
+
+def gemm_workspace_bytes(m, n, k, mode="int8", slices=7, executor="auto") -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().ozaki_gemm_workspace_size(m, n, k, MODES[mode], slices, EXECUTORS[executor],
+                                           ctypes.byref(b)), "ozaki_gemm_workspace_size")
+    return b.value
+
+
+def ozaki_gemm(A: torch.Tensor, B: torch.Tensor, mode="int8", slices=7, executor="auto", C=None, ws=None,
+               stream=None) -> torch.Tensor:
+    _require_cuda(A, B)
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k:
+        raise ValueError("shape mismatch")
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = workspace(gemm_workspace_bytes(m, n, k, mode, slices, executor), A.device)
+    code = lib().ozaki_gemm(m, n, k, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), C.data_ptr(),
+                            C.stride(0), MODES[mode], slices, EXECUTORS[executor], ws.data_ptr(), ws.numel(),
+                            _stream_ptr(stream))
+    _check(code, "ozaki_gemm")
+    return C
+
+
+def ozaki_level_sums(A: torch.Tensor, B: torch.Tensor, mode="int8", slices=7, executor="auto",
+                     stream=None) -> torch.Tensor:
+    """Exact integer level sums S[L-2] = sum_{i+j=L} A_i B_j, int32 (s, m, n)."""
+    _require_cuda(A, B)
+    m, k = A.shape
+    n = B.shape[1]
+    S = torch.zeros((slices, m, n), dtype=torch.int32, device=A.device)
+    ws = workspace(gemm_workspace_bytes(m, n, k, mode, slices, executor), A.device)
+    code = lib().ozaki_level_sums(m, n, k, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), S.data_ptr(),
+                                  MODES[mode], slices, EXECUTORS[executor], ws.data_ptr(), ws.numel(),
+                                  _stream_ptr(stream))
+    _check(code, "ozaki_level_sums")
+    return S
+
+
+def ozaki_split(A: torch.Tensor, mode="int8", slices=7, executor="auto", stream=None):
+    """(row exponents int32 (m,), digit planes (s, m, k)): int8 for the IMMA
+    executor, bfloat16 for the tcgen05 executor."""
+    _require_cuda(A)
+    m, k = A.shape
+    ex = executor if executor != "auto" else ("imma" if mode == "int8" else "tc")
+    dt = torch.int8 if ex == "imma" else torch.bfloat16
+    exps = torch.empty(m, dtype=torch.int32, device=A.device)
+    digits = torch.empty((slices, m, k), dtype=dt, device=A.device)
+    ws = workspace(gemm_workspace_bytes(m, 1, k, mode, slices, ex), A.device)
+    code = lib().ozaki_split(m, k, A.data_ptr(), A.stride(0), MODES[mode], slices, EXECUTORS[ex], exps.data_ptr(),
+                             digits.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(code, "ozaki_split")
+    return exps, digits

@@ -24,3 +24,18 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return GOLDEN
+
+
+@pytest.fixture(scope="session")
+def dmp():
+    """The compiled library's binding, on a CUDA device. Fails (does not skip)
+    when the library cannot be built or loaded: there is no fallback path."""
+    import torch
+
+    from paper_2407_13299_gb300 import build
+    from paper_2407_13299_gb300 import dmp as binding
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    binding.lib()
+    return binding

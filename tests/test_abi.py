@@ -1,0 +1,81 @@
+"""The C-ABI library: it builds, loads without a GPU and exports exactly what
+include/dmp.h declares. No compute call is made here."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dmp.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2407_13299_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("dm_purify", "ozaki_gemm", "dm_purify_batched", "dm_purify_backward"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    L = ctypes.CDLL(built)
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_binding_covers_the_header(built):
+    from paper_2407_13299_gb300 import dmp
+
+    assert sorted(dmp.SIGNATURES) == _declared_functions()
+    L = dmp.lib()
+    assert L.dmp_version().decode().startswith("dmp")
+    assert dmp.status_str(-5) == "DMP_ERR_UNSUPPORTED"
+
+
+def test_struct_layouts_match_header(built):
+    from paper_2407_13299_gb300 import dmp
+
+    assert ctypes.sizeof(dmp.Opts) == 6 * 4 + 2 * 8
+    assert ctypes.sizeof(dmp.Info) == 4 * 4 + 7 * 8
+
+
+def test_workspace_sizes_are_host_side(built):
+    from paper_2407_13299_gb300 import dmp
+
+    o = dmp.make_opts("int8", 7, "imma")
+    small = dmp.purify_workspace_bytes(256, o)
+    big = dmp.purify_workspace_bytes(8192, o)
+    # two FP64 n x n buffers + two int8 digit stacks dominate
+    assert big >= 2 * 8192 * 8192 * 8 + 2 * 7 * 8192 * 8192
+    assert small < big
+    f = dmp.purify_workspace_bytes(256, dmp.make_opts("fp64"))
+    assert f < small
+    assert dmp.tape_bytes(1024, dmp.make_opts("fp64", max_iter=100, checkpoint_every=8)) >= 13 * 1024 * 1024 * 8
+
+
+def test_argument_errors_without_gpu(built):
+    from paper_2407_13299_gb300 import dmp
+
+    L = dmp.lib()
+    b = ctypes.c_size_t(0)
+    bad = dmp.make_opts("int8", 11, "imma")  # s out of range for beta 7
+    assert L.dmp_workspace_size(256, ctypes.byref(bad), ctypes.byref(b)) == dmp.ERR_INVALID_ARG
+    assert L.dmp_workspace_size(1, ctypes.byref(dmp.make_opts()), ctypes.byref(b)) == dmp.ERR_INVALID_ARG
+    o = dmp.make_opts()
+    info = dmp.Info()
+    rc = L.dm_purify(None, 16, 16, 4, ctypes.byref(o), None, 16, ctypes.byref(info), None, 0, None, 0, None)
+    assert rc == dmp.ERR_INVALID_ARG
