@@ -49,10 +49,9 @@ int normalize(const dmp_opts* o, Opts& out) {
   }
   out.executor = o->executor;
   if (out.executor < DMP_EXEC_AUTO || out.executor > DMP_EXEC_TC) return DMP_ERR_INVALID_ARG;
-  if (out.mode == DMP_OZAKI_INT8 && out.executor == DMP_EXEC_AUTO) out.executor = DMP_EXEC_IMMA;
-  if (out.mode == DMP_OZAKI_BF16 && out.executor == DMP_EXEC_AUTO) out.executor = DMP_EXEC_TC;
+  // the tcgen05 executor is the fast one on this GPU (bf16 tensor rate >> int8 mma.sync rate)
+  if (out.mode != DMP_FP64 && out.executor == DMP_EXEC_AUTO) out.executor = DMP_EXEC_TC;
   if (out.mode == DMP_OZAKI_BF16 && out.executor == DMP_EXEC_IMMA) return DMP_ERR_UNSUPPORTED;
-  if (out.mode != DMP_FP64 && out.executor == DMP_EXEC_TC) return DMP_ERR_UNSUPPORTED;
   if (out.mode == DMP_FP64) out.executor = 0;
   out.max_iter = o->max_iter == 0 ? 100 : o->max_iter;
   if (out.max_iter < 0) return DMP_ERR_INVALID_ARG;
@@ -64,15 +63,21 @@ int normalize(const dmp_opts* o, Opts& out) {
   return DMP_OK;
 }
 
-// Level sums stay exact in int32 while s k (2^beta - 1)^2 < 2^31.
+// Level sums stay exact in int32 while s k (2^beta - 1)^2 < 2^31 (the IMMA
+// executor and the tcgen05 executor with beta = 7 keep them in int32; the
+// tcgen05 executor with beta = 8 keeps a two-word integer).
 bool levels_fit_int32(int64_t k, int s, int beta) {
   const double bound = static_cast<double>(s) * static_cast<double>(k) *
                        std::pow(2.0, beta) * std::pow(2.0, beta);
   return bound < 2147483648.0;
 }
 
+bool needs_int32(int mode, int executor) { return !(mode == DMP_OZAKI_BF16 && executor == DMP_EXEC_TC); }
 int elem_bytes(int executor) { return executor == DMP_EXEC_TC ? 2 : 1; }
 int elem_kind(int executor) { return executor == DMP_EXEC_TC ? 3 : 1; }
+// digit-plane rows are padded to the executor's tile height (tcgen05: 256 so
+// that one plane set serves as A (128-row tiles) and B (256-row tiles))
+int64_t row_pad(int executor) { return executor == DMP_EXEC_TC ? 256 : kTileM; }
 
 #define DMP_CUDA(call)                       \
   do {                                       \
@@ -82,20 +87,21 @@ int elem_kind(int executor) { return executor == DMP_EXEC_TC ? 3 : 1; }
 
 // ---------------------------------------------------------------- dm_purify layout
 struct PurifyLayout {
-  size_t state, partials, rowbuf, expsP, expsX, Palt, X2, planesP, planesX, total;
+  size_t state, partials, rowbuf, expsP, expsX, err, Palt, X2, planesP, planesX, total;
   int64_t n_pad, k_pad;
 };
 
 PurifyLayout purify_layout(int64_t n, const Opts& o) {
   PurifyLayout L;
   Carver c;
-  L.n_pad = round_up(n, kTileM);
+  L.n_pad = round_up(n, o.mode == DMP_FP64 ? kTileM : row_pad(o.executor));
   L.k_pad = round_up(n, kPadK);
   L.state = c.take(sizeof(PurifyState));
   L.partials = c.take(static_cast<size_t>(kMeasureBlocks) * 8 * sizeof(double));
   L.rowbuf = c.take(gershgorin_rowbuf_bytes(n));
   L.expsP = c.take(static_cast<size_t>(L.n_pad) * sizeof(int32_t));
   L.expsX = c.take(static_cast<size_t>(L.n_pad) * sizeof(int32_t));
+  L.err = c.take(sizeof(int32_t));
   L.Palt = c.take(static_cast<size_t>(n) * n * sizeof(double));
   L.X2 = c.take(static_cast<size_t>(n) * n * sizeof(double));
   if (o.mode != DMP_FP64) {
@@ -107,6 +113,16 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
   }
   L.total = c.cur;
   return L;
+}
+
+// One Ozaki product from prepared digit planes on the chosen executor.
+cudaError_t launch_product(const Opts& o, const void* pa, const void* pb, const int32_t* ea, const int32_t* eb,
+                           int64_t m, int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int sym,
+                           const EpiArgs& epi, const int* done, int* err, cudaStream_t st) {
+  if (o.executor == DMP_EXEC_TC)
+    return launch_ozaki_tc(pa, pb, ea, eb, m, n, rows_a, rows_b, k_pad, o.s, o.beta, sym, epi, done, err, st);
+  return launch_ozaki_imma(static_cast<const int8_t*>(pa), static_cast<const int8_t*>(pb), ea, eb, m, n, rows_a,
+                           rows_b, k_pad, o.s, o.beta, sym, epi, done, st);
 }
 
 // Tape: header, per-step coefficients, then checkpoints P_0, P_k, P_2k, ...
@@ -188,7 +204,8 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   if (rc != DMP_OK) return rc;
   if (H == nullptr || P == nullptr || ws == nullptr) return DMP_ERR_INVALID_ARG;
   if (n < 2 || ldh < n || ldp < n || n_occ <= 0 || n_occ >= n) return DMP_ERR_INVALID_ARG;
-  if (o.mode != DMP_FP64 && !levels_fit_int32(n, o.s, o.beta)) return DMP_ERR_UNSUPPORTED;
+  if (o.mode != DMP_FP64 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.s, o.beta))
+    return DMP_ERR_UNSUPPORTED;
   const PurifyLayout L = purify_layout(n, o);
   if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
   TapeLayout TL{};
@@ -207,6 +224,8 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   double* X2 = reinterpret_cast<double*>(at(ws, L.X2));
   void* planesP = o.mode != DMP_FP64 ? at(ws, L.planesP) : nullptr;
   void* planesX = o.mode != DMP_FP64 ? at(ws, L.planesX) : nullptr;
+  int* err = reinterpret_cast<int*>(at(ws, L.err));
+  DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
   PurifyState init;
   std::memset(&init, 0, sizeof(init));
@@ -240,14 +259,16 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     } else {
       DMP_CUDA(launch_split_rows(cur, n, n, ldcur, o.s, o.beta, expsP, planesP, L.n_pad, L.k_pad,
                                  elem_kind(o.executor), nullptr, done, st));
-      DMP_CUDA(launch_ozaki_imma(static_cast<const int8_t*>(planesP), static_cast<const int8_t*>(planesP),
-                                 expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, o.s, o.beta, 1, e2, done, st));
+      DMP_CUDA(launch_product(o, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e2, done,
+                              err, st));
     }
     DMP_CUDA(launch_measure(cur, ldcur, X2, n, H, ldh, n, partials, state, st));
-    int32_t flag_done = 0;
-    DMP_CUDA(cudaMemcpyAsync(&flag_done, &state->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    int32_t flags[2] = {0, 0};
+    DMP_CUDA(cudaMemcpyAsync(&flags[0], &state->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DMP_CUDA(cudaMemcpyAsync(&flags[1], err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     DMP_CUDA(cudaStreamSynchronize(st));
-    if (flag_done) break;
+    if (flags[1]) return DMP_ERR_TIMEOUT;
+    if (flags[0]) break;
     if (tape != nullptr) {
       DMP_CUDA(cudaMemcpyAsync(tape_c + k, &state->c, sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
@@ -265,8 +286,8 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     } else {
       DMP_CUDA(launch_split_rows(X2, n, n, n, o.s, o.beta, expsX, planesX, L.n_pad, L.k_pad,
                                  elem_kind(o.executor), nullptr, done, st));
-      DMP_CUDA(launch_ozaki_imma(static_cast<const int8_t*>(planesP), static_cast<const int8_t*>(planesX),
-                                 expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, o.s, o.beta, 1, e3, done, st));
+      DMP_CUDA(launch_product(o, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e3, done,
+                              err, st));
     }
     std::swap(cur, alt);
     std::swap(ldcur, ldalt);
@@ -331,11 +352,12 @@ int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int
     return DMP_OK;
   }
   Carver c;
-  const int64_t m_pad = round_up(std::max<int64_t>(m, 1), kTileM);
-  const int64_t n_pad = round_up(std::max<int64_t>(n, 1), kTileN);
+  const int64_t m_pad = round_up(std::max<int64_t>(m, 1), row_pad(o.executor));
+  const int64_t n_pad = round_up(std::max<int64_t>(n, 1), row_pad(o.executor));
   const int64_t k_pad = round_up(std::max<int64_t>(k, 1), kPadK);
   c.take(m_pad * sizeof(int32_t));
   c.take(n_pad * sizeof(int32_t));
+  c.take(sizeof(int32_t));
   c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o.executor));
   c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o.executor));
   c.take(static_cast<size_t>(n) * k * sizeof(double));
@@ -362,16 +384,18 @@ static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_
     DMP_CUDA(launch_gemm_f64(A, lda, B, ldb, m, n, k, 0, epi, nullptr, st));
     return DMP_OK;
   }
-  if (!levels_fit_int32(k, o.s, o.beta)) return DMP_ERR_UNSUPPORTED;
+  if ((needs_int32(o.mode, o.executor) || epi.kind == EPI_LEVELS) && !levels_fit_int32(k, o.s, o.beta))
+    return DMP_ERR_UNSUPPORTED;
   size_t need = 0;
   ozaki_gemm_workspace_size(m, n, k, mode, slices, executor, &need);
   if (ws == nullptr || ws_bytes < need) return DMP_ERR_WORKSPACE;
   Carver c;
-  const int64_t m_pad = round_up(m, kTileM);
-  const int64_t n_pad = round_up(n, kTileN);
+  const int64_t m_pad = round_up(m, row_pad(o.executor));
+  const int64_t n_pad = round_up(n, row_pad(o.executor));
   const int64_t k_pad = round_up(std::max<int64_t>(k, 1), kPadK);
   int32_t* ea = reinterpret_cast<int32_t*>(at(ws, c.take(m_pad * sizeof(int32_t))));
   int32_t* eb = reinterpret_cast<int32_t*>(at(ws, c.take(n_pad * sizeof(int32_t))));
+  int* err = reinterpret_cast<int*>(at(ws, c.take(sizeof(int32_t))));
   void* pa = at(ws, c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o.executor)));
   void* pb = at(ws, c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o.executor)));
   double* Bt = reinterpret_cast<double*>(at(ws, c.take(static_cast<size_t>(n) * k * sizeof(double))));
@@ -380,8 +404,19 @@ static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_
   DMP_CUDA(launch_transpose(B, k, n, ldb, Bt, st));
   DMP_CUDA(launch_split_rows(Bt, n, k, k, o.s, o.beta, eb, pb, n_pad, k_pad, elem_kind(o.executor), nullptr,
                              nullptr, st));
-  DMP_CUDA(launch_ozaki_imma(static_cast<const int8_t*>(pa), static_cast<const int8_t*>(pb), ea, eb, m, n,
-                             m_pad, n_pad, k_pad, o.s, o.beta, 0, epi, nullptr, st));
+  if (o.executor == DMP_EXEC_TC) DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  DMP_CUDA(launch_product(o, pa, pb, ea, eb, m, n, m_pad, n_pad, k_pad, 0, epi, nullptr, err, st));
+  if (o.executor == DMP_EXEC_TC) {
+    // report an expired device wait; skipped while the stream is being captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DMP_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      int flag = 0;
+      DMP_CUDA(cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      DMP_CUDA(cudaStreamSynchronize(st));
+      if (flag) return DMP_ERR_TIMEOUT;
+    }
+  }
   return DMP_OK;
 }
 
@@ -423,10 +458,11 @@ int ozaki_split(int64_t m, int64_t k, const double* A, int64_t lda, int32_t mode
   if (ws == nullptr || ws_bytes < need) return DMP_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carver c;
-  const int64_t m_pad = round_up(m, kTileM);
+  const int64_t m_pad = round_up(m, row_pad(o.executor));
   const int64_t k_pad = round_up(k, kPadK);
   int32_t* ea = reinterpret_cast<int32_t*>(at(ws, c.take(m_pad * sizeof(int32_t))));
-  c.take(round_up(1, kTileN) * sizeof(int32_t));
+  c.take(round_up(1, row_pad(o.executor)) * sizeof(int32_t));
+  c.take(sizeof(int32_t));
   const int eb = elem_bytes(o.executor);
   char* pa = at(ws, c.take(static_cast<size_t>(o.s) * m_pad * k_pad * eb));
   DMP_CUDA(launch_split_rows(A, m, k, lda, o.s, o.beta, ea, pa, m_pad, k_pad, elem_kind(o.executor), nullptr,

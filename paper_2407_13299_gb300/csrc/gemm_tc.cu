@@ -1,0 +1,549 @@
+// tcgen05 executor for the Ozaki slice-pair products (Sec. "Ozaki Scheme", Fig. 2).
+//
+// The digits are small integers (|d| <= 127 for beta = 7, <= 255 for beta = 8),
+// exactly representable in bfloat16, so the slice-pair products run on the
+// 5th-generation tensor cores (tcgen05.mma kind::f16, bf16 x bf16 -> fp32 in
+// tensor memory). An fp32 sum of such products is exact while every partial
+// sum stays below 2^24 in magnitude; the K loop is therefore cut into chunks of
+// 1024 (beta = 7: 1024 * 127^2 < 2^24) or 256 (beta = 8) K elements. Each chunk
+// lands in one of two TMEM accumulators; while the tensor core fills the other,
+// eight epilogue warps drain the finished one into exact integer level sums in
+// registers (int32; for beta = 8 a two-word hi/lo integer). At the end of a
+// level L the exact S_L is folded into a float64 accumulator kept in the output
+// buffer: acc = S_L 2^(-beta L) + acc, levels from L = s+1 down to 2 -- the
+// same operation sequence as the definition, so the float64 result is
+// bit-for-bit the one the IMMA executor and the oracle produce.
+//
+// CTA layout (320 threads, one CTA per SM):
+//   warp 0      TMA producer: A tile 128 x 64 and B tile BN x 64 bf16 per stage,
+//               128-byte swizzle, into a 4- or 6-stage shared-memory ring
+//   warp 1      TMEM owner and MMA issuer (one thread): 4 MMAs of K = 16 per
+//               stage, commits free the stage and publish finished chunks
+//   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one output
+//               row per thread) and half of the BN columns
+// Output tile 128 x BN (BN = 256 for beta = 7, 128 for beta = 8). In symmetric
+// mode only tiles holding some element with row <= column run; each element
+// with row <= column is accumulated and written once, and mirrored.
+//
+// Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the CTA
+// raises an error flag, drains what it has in flight (bounded again), frees
+// its TMEM and returns.
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "dmp_internal.cuh"
+
+namespace dmp {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;  // bf16 elements per K block: one 128-byte swizzle row
+constexpr int TC_THREADS = 320;
+constexpr int TC_EPI_WARPS = 8;
+
+template <int BN>
+struct TcCfg {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr int B_BYTES = BN * TC_BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = BN == 256 ? 4 : 6;
+  static constexpr int TMEM_COLS = 2 * BN;      // two fp32 chunk accumulators
+  static constexpr int COLS = BN / 2;           // columns per epilogue thread
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;  // + alignment slack
+};
+
+struct TcParams {
+  int s, beta, KT, CH;
+  int64_t m, n;
+  int64_t rows_a, rows_b;  // padded rows per digit plane
+  int sym, tiles_m, tiles_n;
+  const int32_t* ea;
+  const int32_t* eb;
+  EpiArgs epi;
+  const int* done;
+  int* err;
+  unsigned long long timeout_ns;
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(dst), "l"(tm), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap* tm) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(tm) : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand tile, rows of 128 bytes,
+// 128-byte swizzle, 8-row groups 1024 bytes apart (tile base 1024-aligned).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                  // leading byte offset (unused for this layout)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;          // stride byte offset: 8 rows
+  d |= static_cast<uint64_t>(1) << 46;                  // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                  // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::f16: fp32 D, bf16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// bounded wait; false on timeout or when another role aborted
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                         const TcParams& p) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t deadline = globaltimer() + p.timeout_ns;
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() > deadline) {
+        *abort_flag = 1;
+        if (p.err != nullptr) atomicExch(p.err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int npairs_of(int L, int s) { return min(s, L - 1) - max(1, L - s) + 1; }
+
+template <int BN>
+__device__ __forceinline__ void tile_of(const TcParams& p, int& bi, int& bj) {
+  int idx = blockIdx.x;
+  if (!p.sym) {
+    bj = idx / p.tiles_m;  // column-block major: neighbouring CTAs share B
+    bi = idx % p.tiles_m;
+    return;
+  }
+  bj = 0;
+  for (;;) {
+    const int cnt = min(p.tiles_m, (BN * (bj + 1)) / TC_BM);
+    if (idx < cnt) break;
+    idx -= cnt;
+    ++bj;
+  }
+  bi = idx;
+}
+
+template <int BN, bool WIDE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const TcParams p) {
+  using Cfg = TcCfg<BN>;
+  if (p.done != nullptr && *p.done) return;  // uniform: the whole CTA leaves before any setup
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = smem_u32(smem);
+  uint8_t* barp = smem + Cfg::STAGES * Cfg::STAGE_BYTES;
+  const uint32_t bar0 = smem_u32(barp);
+  auto full_bar = [&](int st) { return bar0 + 8u * st; };
+  auto empty_bar = [&](int st) { return bar0 + 8u * (Cfg::STAGES + st); };
+  auto accfull_bar = [&](int b) { return bar0 + 8u * (2 * Cfg::STAGES + b); };
+  auto accempty_bar = [&](int b) { return bar0 + 8u * (2 * Cfg::STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * Cfg::STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 8 * (2 * Cfg::STAGES + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  int bi, bj;
+  tile_of<BN>(p, bi, bj);
+  const int64_t m0 = static_cast<int64_t>(bi) * TC_BM;
+  const int64_t n0 = static_cast<int64_t>(bj) * BN;
+
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < Cfg::STAGES; ++st) {
+      mbar_init(full_bar(st), 1);
+      mbar_init(empty_bar(st), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accfull_bar(b), 1);
+      mbar_init(accempty_bar(b), TC_EPI_WARPS);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch(&tmA);
+    tma_prefetch(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int s = p.s;
+  const int KT = p.KT;
+  const int CH = p.CH;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      uint32_t armed = 0;  // stages armed in the current ring pass (for the abort drain)
+      for (int L = s + 1; L >= 2 && ok; --L) {
+        const int i_lo = max(1, L - s), i_hi = min(s, L - 1);
+        for (int i = i_lo; i <= i_hi && ok; ++i) {
+          const int j = L - i;
+          const int ya = static_cast<int>((i - 1) * p.rows_a + m0);
+          const int yb = static_cast<int>((j - 1) * p.rows_b + n0);
+          for (int kt = 0; kt < KT; ++kt) {
+            if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, p)) {
+              ok = false;
+              break;
+            }
+            const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
+            mbar_arrive_expect_tx(full_bar(stage), Cfg::STAGE_BYTES);
+            tma_load_2d(sa, &tmA, full_bar(stage), kt * TC_BK, ya);
+            tma_load_2d(sa + Cfg::A_BYTES, &tmB, full_bar(stage), kt * TC_BK, yb);
+            armed |= 1u << stage;
+            if (++stage == Cfg::STAGES) {
+              stage = 0;
+              phase ^= 1u;
+              armed = 0;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // let copies already issued land before shared memory is released
+        for (int st = 0; st < Cfg::STAGES; ++st) {
+          if (armed & (1u << st)) {
+            const uint64_t dl = globaltimer() + 100000000ull;
+            while (!mbar_try_wait(full_bar(st), phase) && globaltimer() < dl) {
+            }
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      int buf = 0;
+      uint32_t aph[2] = {0u, 0u};
+      bool ok = true;
+      bool issued = false;
+      for (int L = s + 1; L >= 2 && ok; --L) {
+        const int nkb = npairs_of(L, s) * KT;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int kc = kb % CH;
+          const bool first = kc == 0;
+          const bool last = (kc == CH - 1) || (kb == nkb - 1);
+          if (first) {
+            if (!wait_bar(accempty_bar(buf), aph[buf] ^ 1u, abort_flag, p)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          if (!wait_bar(full_bar(stage), phase, abort_flag, p)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
+          const uint64_t ad = sdesc_sw128(sa);
+          const uint64_t bd = sdesc_sw128(sa + Cfg::A_BYTES);
+          const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
+#pragma unroll
+          for (int ks = 0; ks < TC_BK / 16; ++ks) {
+            // advance 16 bf16 = 32 bytes along K inside the swizzled row
+            umma_bf16(d, ad + 2ull * ks, bd + 2ull * ks, idesc, (first && ks == 0) ? 0u : 1u);
+          }
+          issued = true;
+          umma_commit(empty_bar(stage));
+          if (last) {
+            umma_commit(accfull_bar(buf));
+            aph[buf] ^= 1u;
+            buf ^= 1;
+          }
+          if (++stage == Cfg::STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok && issued) {
+        // wait for the MMAs in flight before TMEM is released
+        umma_commit(drain_bar);
+        const uint64_t dl = globaltimer() + 100000000ull;
+        while (!mbar_try_wait(drain_bar, 0) && globaltimer() < dl) {
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    constexpr int COLS = Cfg::COLS;
+    const int e = warp - 2;
+    const int q = warp & 3;   // TMEM lane quadrant this warp may access
+    const int h = e >> 2;     // which half of the BN columns
+    const int row = 32 * q + lane;
+    const int64_t r = m0 + row;
+    const int cbase = h * COLS;
+    const uint32_t taddr_row = tmem + (static_cast<uint32_t>(32 * q) << 16);
+    const bool row_ok = r < p.m;
+    const int32_t er = row_ok ? p.ea[r] : 0;
+
+    int32_t S[COLS];
+    int32_t Shi[WIDE ? COLS : 1];
+    int buf = 0;
+    uint32_t aph[2] = {0u, 0u};
+    bool ok = true;
+    for (int L = s + 1; L >= 2 && ok; --L) {
+#pragma unroll
+      for (int c = 0; c < COLS; ++c) {
+        S[c] = 0;
+        if (WIDE) Shi[c] = 0;
+      }
+      const int nkb = npairs_of(L, s) * KT;
+      const int nch = (nkb + CH - 1) / CH;
+      for (int ch = 0; ch < nch; ++ch) {
+        // the whole warp takes the same branch: tcgen05.ld below is warp-collective
+        const bool got = wait_bar(accfull_bar(buf), aph[buf], abort_flag, p);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int g = 0; g < COLS / 32; ++g) {
+          uint32_t v[32];
+          tmem_ld32(taddr_row + static_cast<uint32_t>(buf * BN + cbase + 32 * g), v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int t = 0; t < 32; ++t) S[32 * g + t] += __float2int_rn(__uint_as_float(v[t]));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(accempty_bar(buf));
+        aph[buf] ^= 1u;
+        buf ^= 1;
+        if (WIDE && ((ch & 63) == 63 || ch == nch - 1)) {
+          // keep the low word in [0, 2^24): value = hi 2^24 + lo
+#pragma unroll
+          for (int c = 0; c < COLS; ++c) {
+            Shi[c] += S[c] >> 24;
+            S[c] &= 0xFFFFFF;
+          }
+        }
+      }
+      if (!ok) break;
+      // ---- fold the exact level sum S_L
+      if (p.epi.kind == EPI_LEVELS) {
+        if (row_ok) {
+#pragma unroll
+          for (int c = 0; c < COLS; ++c) {
+            const int64_t col = n0 + cbase + c;
+            if (col < p.n) {
+              const int32_t val = WIDE ? static_cast<int32_t>(static_cast<int64_t>(Shi[c]) * 16777216ll + S[c]) : S[c];
+              p.epi.levels[static_cast<int64_t>(L - 2) * p.m * p.n + r * p.n + col] = val;
+            }
+          }
+        }
+        continue;
+      }
+      const double scale = ldexp(1.0, -p.beta * L);
+      const bool first_level = (L == s + 1);
+      const bool final_level = (L == 2);
+      if (row_ok) {
+        double* accrow = p.epi.C + r * p.epi.ldc;
+#pragma unroll
+        for (int c = 0; c < COLS; ++c) {
+          const int64_t col = n0 + cbase + c;
+          if (col >= p.n) continue;
+          if (p.sym && r > col) continue;  // the (col, r) element's mirror covers it
+          const double Sd = WIDE ? static_cast<double>(Shi[c]) * 16777216.0 + static_cast<double>(S[c])
+                                 : static_cast<double>(S[c]);
+          double acc = first_level ? Sd * scale : fma(Sd, scale, accrow[col]);
+          if (!final_level) {
+            accrow[col] = acc;
+          } else {
+            const int32_t ec = p.eb[col];
+            const double v = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                              : ldexp(acc, er + ec);
+            epi_apply(p.epi, r, col, v, p.sym && r < col);
+          }
+        }
+      }
+    }
+  }
+
+  // ------------------------------------------------------------ teardown
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (fn == nullptr) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// 2-D view of s stacked bf16 digit planes: dim0 = k_pad (contiguous), dim1 = s * rows.
+bool make_plane_map(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(k_pad), static_cast<cuuint64_t>(rows_total)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(k_pad * 2)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(TC_BK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(planes), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, bool WIDE>
+cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& p, int ntiles,
+                           cudaStream_t st) {
+  using Cfg = TcCfg<BN>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(ozaki_tc_kernel<BN, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  ozaki_tc_kernel<BN, WIDE><<<ntiles, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_row_pad() { return 256; }
+
+cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, const int32_t* eb, int64_t m,
+                            int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int s, int beta, int sym,
+                            const EpiArgs& epi, const int* done, int* err, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  const bool wide = beta == 8;
+  const int BN = wide ? 128 : 256;
+  if (rows_a % TC_BM != 0 || rows_b % BN != 0 || k_pad % TC_BK != 0) return cudaErrorInvalidValue;
+  CUtensorMap ta, tb;
+  if (!make_plane_map(&ta, A, k_pad, static_cast<int64_t>(s) * rows_a, TC_BM)) return cudaErrorInvalidValue;
+  if (!make_plane_map(&tb, B, k_pad, static_cast<int64_t>(s) * rows_b, BN)) return cudaErrorInvalidValue;
+  TcParams p;
+  p.s = s;
+  p.beta = beta;
+  p.KT = static_cast<int>(k_pad / TC_BK);
+  p.CH = wide ? 4 : 16;  // K chunk: 256 (beta 8) or 1024 (beta 7) keeps fp32 partial sums below 2^24
+  p.m = m;
+  p.n = n;
+  p.rows_a = rows_a;
+  p.rows_b = rows_b;
+  p.sym = sym;
+  p.tiles_m = static_cast<int>(rows_a / TC_BM);
+  p.tiles_n = static_cast<int>(rows_b / BN);
+  p.ea = ea;
+  p.eb = eb;
+  p.epi = epi;
+  p.done = done;
+  p.err = err;
+  p.timeout_ns = 5000000000ull;
+  int ntiles = 0;
+  if (sym) {
+    for (int bj = 0; bj < p.tiles_n; ++bj) ntiles += std::min(p.tiles_m, (BN * (bj + 1)) / TC_BM);
+  } else {
+    ntiles = p.tiles_m * p.tiles_n;
+  }
+  return wide ? launch_tc_impl<128, true>(ta, tb, p, ntiles, st) : launch_tc_impl<256, false>(ta, tb, p, ntiles, st);
+}
+
+}  // namespace dmp

@@ -15,7 +15,7 @@ from oracle import ozaki as oz
 
 pytestmark = pytest.mark.gpu
 
-EXECUTORS = ["imma"]
+EXECUTORS = ["imma", "tc"]
 
 
 def _mixed(m, k, seed, zero_row=True):
@@ -56,7 +56,8 @@ def test_level_sums_bit_exact(dmp, executor, m, n, k, s):
 
 
 @pytest.mark.parametrize("executor", EXECUTORS)
-@pytest.mark.parametrize("m,n,k,s", [(300, 200, 257, 7), (256, 256, 256, 3), (33, 500, 77, 10), (1, 1, 1, 2)])
+@pytest.mark.parametrize("m,n,k,s", [(300, 200, 257, 7), (256, 256, 256, 3), (33, 500, 77, 10), (1, 1, 1, 2),
+                                     (520, 700, 2100, 7)])
 def test_ozaki_gemm_bit_exact(dmp, executor, m, n, k, s):
     A = _mixed(m, k, seed=3)
     B = _mixed(k, n, seed=4)
@@ -91,14 +92,15 @@ def test_fp64_gemm_matches_float64(dmp):
     assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want)) * 10
 
 
-def test_full_size_sampled_outputs(dmp):
+@pytest.mark.parametrize("executor", EXECUTORS)
+def test_full_size_sampled_outputs(dmp, executor):
     """8192^3 at s = 7, the size of the purification benchmark: 48 sampled
     outputs, each recomputed by the oracle from its own row and column."""
     n, s = 8192, 7
     rng = np.random.default_rng(8)
     A = rng.standard_normal((n, n)) * 0.01
     B = rng.standard_normal((n, n)) * 0.01
-    C = dmp.ozaki_gemm(_dev(A), _dev(B), "int8", s, "imma")
+    C = dmp.ozaki_gemm(_dev(A), _dev(B), "int8", s, executor)
     rows = rng.integers(0, n, size=48)
     cols = rng.integers(0, n, size=48)
     rows[:2] = [0, n - 1]
@@ -107,6 +109,57 @@ def test_full_size_sampled_outputs(dmp):
     for t, (r, c) in enumerate(zip(rows, cols)):
         want = oz.ozaki_gemm(A[r:r + 1, :], B[:, c:c + 1], s, 7)[0, 0]
         assert Cs[t] == want, (r, c)
+
+
+@pytest.mark.parametrize("executor", EXECUTORS)
+def test_extreme_digits_stay_exact(dmp, executor):
+    """Entries 1 - 2^-49 give seven digits of 127 each: every fp32 chunk sum of
+    the tensor-core executor sits at its bound 1024 * 127^2 (just under 2^24),
+    with both signs, so any loss in the accumulator shows up as a wrong bit."""
+    n, k, s = 256, 2048, 7
+    v = 1.0 - 2.0 ** -49
+    rng = np.random.default_rng(12)
+    A = np.full((n, k), v)
+    B = np.full((k, n), v)
+    A[n // 2:, :] *= -1.0
+    B[:, ::3] *= -1.0
+    A[7, :] = rng.choice([-v, v], size=k)
+    _, parts = oz.ozaki_gemm(A, B, s, 7, return_parts=True)
+    assert np.all(np.abs(parts["DA"]) == 127)
+    S = dmp.ozaki_level_sums(_dev(A), _dev(B), "int8", s, executor).cpu().numpy()
+    for L in range(2, s + 2):
+        assert np.array_equal(S[L - 2].astype(np.int64), parts["S"][L]), L
+    want = oz.ozaki_gemm(A, B, s, 7)
+    got = dmp.ozaki_gemm(_dev(A), _dev(B), "int8", s, executor).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("m,n,k,s", [(300, 260, 520, 6), (128, 128, 4096, 5), (64, 500, 77, 9)])
+def test_bf16_mode_bit_exact(dmp, m, n, k, s):
+    """beta = 8 digits (|d| <= 255) on the tensor-core executor: 256-wide K
+    chunks and two-word integer level sums."""
+    A = _mixed(m, k, seed=21)
+    B = _mixed(k, n, seed=22)
+    want = oz.ozaki_gemm(A, B, s, 8)
+    got = dmp.ozaki_gemm(_dev(A), _dev(B), "bf16", s, "tc").cpu().numpy()
+    assert np.array_equal(got.view(np.int64), want.view(np.int64))
+    e, D, _ = oz.split_rows(A, s, 8)
+    ge, gd = dmp.ozaki_split(_dev(A), "bf16", s, "tc")
+    assert np.array_equal(ge.cpu().numpy(), e.astype(np.int32))
+    assert np.array_equal(gd.float().cpu().numpy().astype(np.int64), D)
+
+
+def test_bf16_mode_large_level_sums(dmp):
+    """beta = 8 level sums beyond int32 (s k 255^2 > 2^31) stay exact in the
+    two-word accumulators: max-magnitude digits, k = 8192."""
+    n, k, s = 128, 8192, 6
+    v = 1.0 - 2.0 ** -48  # six digits of 255
+    A = np.full((n, k), v)
+    B = np.full((k, n), v)
+    B[:, 1::2] *= -1.0
+    want = oz.ozaki_gemm(A, B, s, 8)
+    got = dmp.ozaki_gemm(_dev(A), _dev(B), "bf16", s, "tc").cpu().numpy()
+    assert np.array_equal(got, want)
 
 
 def test_invalid_arguments(dmp):

@@ -43,11 +43,12 @@ def test_config0_fp64_matches_oracle(dmp):
     assert np.array_equal(P, P.T)
 
 
-@pytest.mark.parametrize("n,n_occ,s", [(300, 75, 7), (300, 75, 8), (200, 13, 9)])
-def test_ozaki_int8_matches_oracle(dmp, n, n_occ, s):
+@pytest.mark.parametrize("executor", ["imma", "tc"])
+@pytest.mark.parametrize("n,n_occ,s", [(300, 75, 7), (300, 75, 8), (200, 13, 9), (600, 150, 7)])
+def test_ozaki_int8_matches_oracle(dmp, executor, n, n_occ, s):
     h = make_hamiltonian(n, n_occ, seed=n + s)
     ref = pu.purify(h.H, n_occ, tol=1e-10, product=partial(oz.ozaki_gemm, s=s, beta=7))
-    P, info = dmp.purify(_dev(h.H), n_occ, mode="int8", slices=s, executor="imma", tol=1e-10)
+    P, info = dmp.purify(_dev(h.H), n_occ, mode="int8", slices=s, executor=executor, tol=1e-10)
     P = P.cpu().numpy()
     assert info["status"] in (dmp.OK, dmp.C_OUT_OF_RANGE, dmp.STALLED)
     assert np.max(np.abs(P - ref["P"])) <= 1e-8
@@ -57,12 +58,22 @@ def test_ozaki_int8_matches_oracle(dmp, n, n_occ, s):
     assert np.array_equal(P, P.T)
 
 
-def test_ozaki_error_falls_with_slices(dmp):
+def test_bf16_mode_matches_oracle(dmp):
+    h = make_hamiltonian(300, 75, seed=17)
+    ref = pu.purify(h.H, 75, tol=1e-10, product=partial(oz.ozaki_gemm, s=6, beta=8))
+    P, info = dmp.purify(_dev(h.H), 75, mode="bf16", slices=6, executor="tc", tol=1e-10)
+    P = P.cpu().numpy()
+    assert np.max(np.abs(P - ref["P"])) <= 1e-8
+    assert np.max(np.abs(P - _projector(h))) <= 1e-8
+
+
+@pytest.mark.parametrize("executor", ["imma", "tc"])
+def test_ozaki_error_falls_with_slices(dmp, executor):
     h = make_hamiltonian(384, 96, seed=11)
     P_star = _projector(h)
     errs = []
     for s in (3, 5, 7, 9):
-        P, _ = dmp.purify(_dev(h.H), 96, mode="int8", slices=s, executor="imma", tol=1e-10)
+        P, _ = dmp.purify(_dev(h.H), 96, mode="int8", slices=s, executor=executor, tol=1e-10)
         errs.append(np.max(np.abs(P.cpu().numpy() - P_star)))
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
 
@@ -107,17 +118,21 @@ def test_errors_and_statuses(dmp):
     assert np.max(np.abs(P.cpu().numpy() - ref["P"])) <= 1e-12
 
 
-def test_deterministic(dmp):
+def test_deterministic_and_executors_agree(dmp):
+    """The two executors produce the same level sums, so the whole purification
+    is bit-identical between them (and between runs)."""
     h = make_hamiltonian(260, 65, seed=5)
-    P1, i1 = dmp.purify(_dev(h.H), 65, mode="int8", slices=7)
-    P2, i2 = dmp.purify(_dev(h.H), 65, mode="int8", slices=7)
+    P1, i1 = dmp.purify(_dev(h.H), 65, mode="int8", slices=7, executor="tc")
+    P2, i2 = dmp.purify(_dev(h.H), 65, mode="int8", slices=7, executor="tc")
+    P3, i3 = dmp.purify(_dev(h.H), 65, mode="int8", slices=7, executor="imma")
     assert torch.equal(P1, P2) and i1 == i2
+    assert torch.equal(P1, P3) and i1["iters"] == i3["iters"]
 
 
 def test_full_size_config2_int8(dmp):
     """n = 8192, n_occ = 2048, gap 0.02: the benchmark workload at s = 7."""
     h = config_hamiltonian(2, device="cuda")
-    P, info = dmp.purify(h.H, h.n_occ, mode="int8", slices=7, tol=1e-10)
+    P, info = dmp.purify(h.H, h.n_occ, mode="int8", slices=7, executor="tc", tol=1e-10)
     E_star = float(np.sum(h.e[: h.n_occ]))
     assert info["status"] in (dmp.OK, dmp.C_OUT_OF_RANGE, dmp.STALLED), info
     assert abs(info["energy"] - E_star) <= 1e-8 * abs(E_star), info
