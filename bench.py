@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark: canonical purification of an n = 8192 Hamiltonian with Ozaki-INT8
+products on one GB300, against FP64 on the same GPU.
+
+Workload (synthetic; the paper's Hamiltonians are not available): H = Q diag(e)
+Q^T, n = 8192, n_occ = 2048, Q from QR of a seeded N(0,1) matrix, occupied
+eigenvalues uniform in [-1.5, -0.01], virtual in [0.01, 1.5] (gap 0.02). A step
+is one full dm_purify call (Gershgorin initial guess, every split, slice-pair
+product, trace/norm reduction and update, device-side stopping rules) on H
+already resident in HBM. The slice count is the smallest s >= 6 whose band
+energy is within 1e-8 (relative) of the exact sum of the occupied eigenvalues;
+the check runs before the timed region and the error is reported.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank purifies its own copy (replicas: the method has no
+exchange step); rank 0 prints one JSON line. `--impl reference` times the CPU
+oracle on bounded samples of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "n=8192 purification time, Ozaki-INT8 vs FP64, at 1e-8 rel energy error"
+UNIT = "s"
+REL_ENERGY_TARGET = 1e-8
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=8192, help="matrix size (8192 is the benchmark workload)")
+    ap.add_argument("--slices", type=int, default=0, help="0: smallest s >= 6 meeting the energy target")
+    ap.add_argument("--executor", default="tc", choices=["tc", "imma"])
+    ap.add_argument("--fp64", default="full", choices=["full", "skip"], help="time the FP64 purification once")
+    ap.add_argument("--cpu-samples", type=int, default=5, help="oracle samples for cpu_baseline (0: skip)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+def workload_params(n):
+    if n == 8192:
+        from synth import CONFIGS
+
+        c = CONFIGS[2]
+        return dict(n=c["n"], n_occ=c["n_occ"], occ=c["occ"], virt=c["virt"], seed=c["seed"])
+    return dict(n=n, n_occ=n // 4, occ=(-1.5, -0.01), virt=(0.01, 1.5), seed=1002)
+
+
+def workload_name(w):
+    return (f"canonical purification, n={w['n']}, n_occ={w['n_occ']}, H=Q diag(e) Q^T, "
+            f"spectrum {list(w['occ'])} u {list(w['virt'])} (gap 0.02), seed {w['seed']}")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def kernel_traffic(kernel_file, summary):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (matching sha256 prefix); else None."""
+    src = os.path.join(ROOT, "paper_2407_13299_gb300", "csrc", kernel_file)
+    path = os.path.join(ROOT, "profiles", summary)
+    if not (os.path.exists(src) and os.path.exists(path)):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256")):
+            k, v = line.split(":", 1)
+            vals[k.strip().lstrip("- ")] = v.strip().split()[0]
+    if vals.get("source_sha256") != digest:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(H, n_occ, s, beta, iters, rows=512, cols=512, seed=0):
+    """One bounded sample of the CPU oracle on this workload, extrapolated to a
+    whole purification (seconds).
+
+    Timed pieces of the oracle's Ozaki product X2 = P P with P the oracle's
+    initial guess: the row split of a `rows`-row block of A, the column split of
+    a `cols`-column block of B, the exact level sums and the FP64 recombination
+    of that rows x cols output block; plus one pass of the oracle's per-iterate
+    work on the full n x n arrays (traces, idempotency, energy, update). The
+    product time is scaled to the full n x n output (splits by n/rows and
+    n/cols, level sums and recombination by (n/rows)(n/cols)), two products per
+    iteration, times the iteration count.
+    """
+    import numpy as np
+
+    from oracle import ozaki as oz
+    from oracle import purify as pu
+
+    n = H.shape[0]
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    P, _ = pu.initial_guess(H, n_occ)
+    t_init = time.perf_counter() - t0
+    r0 = int(rng.integers(0, n - rows + 1))
+    c0 = int(rng.integers(0, n - cols + 1))
+    t0 = time.perf_counter()
+    e, DA, _ = oz.split_rows(P[r0:r0 + rows], s, beta)
+    t_sa = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    f, DBt, _ = oz.split_cols(P[:, c0:c0 + cols], s, beta)
+    t_sb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    S = oz.level_sums(DA, DBt, beta)
+    t_lv = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oz.recombine(S, e, f, s, beta)
+    t_rc = time.perf_counter() - t0
+    X2 = P  # stand-in operand of the same size for the O(n^2) per-iterate work
+    t0 = time.perf_counter()
+    float(np.trace(P)), float(np.trace(X2)), float(np.linalg.norm(X2 - P)), float(np.sum(P * H))
+    pu.pm_update(P, X2, X2, 0.3)
+    t_it = time.perf_counter() - t0
+    per_product = t_sa * (n / rows) + t_sb * (n / cols) + (t_lv + t_rc) * (n / rows) * (n / cols)
+    total = t_init + iters * (2.0 * per_product + t_it)
+    return total, dict(t_init=t_init, t_split_rows=t_sa, t_split_cols=t_sb, t_levels=t_lv, t_recombine=t_rc,
+                       t_iterate=t_it, per_product=per_product)
+
+
+def oracle_iterations(H, n_occ, e, tol):
+    """Iteration count of the oracle's loop on this H (eigenvalue form, O(n) per step)."""
+    from oracle import purify as pu
+
+    x0 = pu.initial_eigenvalues(H, n_occ, e)
+    return pu.spectral_purify(x0, e, tol=tol)["iters"]
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0  # the oracle runs on rank 0 only
+    import numpy as np
+
+    from synth import make_hamiltonian
+
+    w = workload_params(args.n)
+    h = make_hamiltonian(w["n"], w["n_occ"], w["occ"], w["virt"], w["seed"])
+    s = args.slices or 6
+    iters = oracle_iterations(h.H, h.n_occ, h.e, 1e-10)
+    for _ in range(args.warmup):
+        oracle_sample(h.H, h.n_occ, s, 7, iters, seed=1)
+    vals = []
+    for k in range(args.steps):
+        v, _ = oracle_sample(h.H, h.n_occ, s, 7, iters, seed=100 + k)
+        vals.append(v)
+    value = float(np.median(vals))
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w), "mode": "ozaki-int8 (oracle)", "slices": s, "iters": iters},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step: the oracle's Ozaki product on a 512x512 output block of P0 P0 "
+                                   "(row/column splits, exact level sums, recombination) plus one pass of its "
+                                   "per-iterate n x n work, scaled to 2 products per iteration x the oracle's "
+                                   "iteration count; median over steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2407_13299_gb300 import build as _build
+    from paper_2407_13299_gb300 import dmp
+    from synth import make_hamiltonian
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    dmp.lib()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = workload_params(args.n)
+    h = make_hamiltonian(w["n"], w["n_occ"], w["occ"], w["virt"], w["seed"], device=dev)
+    n, n_occ = w["n"], w["n_occ"]
+    H = h.H.contiguous()
+    E_star = float(np.sum(h.e[:n_occ]))
+    stream = torch.cuda.current_stream(dev)
+
+    # ---- slice count: smallest s >= 6 meeting the energy target (untimed)
+    s = args.slices
+    tune = []
+    if s == 0:
+        for cand in (6, 7, 8, 9):
+            _, info = dmp.purify(H, n_occ, mode="int8", slices=cand, executor=args.executor)
+            rel = abs(info["energy"] - E_star) / abs(E_star)
+            tune.append({"slices": cand, "rel_energy": rel, "iters": info["iters"]})
+            if rel <= REL_ENERGY_TARGET:
+                s = cand
+                break
+        if s == 0:
+            s = 9
+    opts = dmp.make_opts("int8", s, args.executor)
+    P = torch.empty_like(H)
+    ws = dmp.workspace(dmp.purify_workspace_bytes(n, opts), dev)
+
+    def step():
+        return dmp.purify(H, n_occ, mode="int8", slices=s, executor=args.executor, P=P, ws=ws)
+
+    for _ in range(max(args.warmup, 0)):
+        _, info = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K full purifications, H resident in HBM (512 MiB > L2)
+    dmp.profile_enable(True)
+    dmp.profile_reset()
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    launches0 = dmp.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        _, info = step()
+        infos.append(info)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = dmp.launch_count() - launches0
+    clk = clocks.stop() if clocks else None
+    dmp.profile_enable(False)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    per_step = elapsed / args.steps
+    prod_ms, prod_n = dmp.profile_read(dmp.PROF_PRODUCT)
+    split_ms, split_n = dmp.profile_read(dmp.PROF_SPLIT)
+    meas_ms, meas_n = dmp.profile_read(dmp.PROF_MEASURE)
+    init_ms, init_n = dmp.profile_read(dmp.PROF_INIT)
+    info = infos[-1]
+    rel_energy = abs(info["energy"] - E_star) / abs(E_star)
+
+    # ---- roofline of the dominant kernel (the tcgen05 slice-pair product)
+    peaks, peak_src = load_peaks()
+    p_pairs = s * (s + 1) // 2
+    flops_per_launch = p_pairs * n * n * (n + 1)  # upper triangle incl. diagonal, 2 k flops per output and pair
+    avg_launch_s = (prod_ms / 1e3) / max(prod_n, 1)
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
+    traffic = kernel_traffic("gemm_tc.cu", "ozaki_tc_kernel_n8192.md") if args.executor == "tc" else None
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "ozaki_tc_kernel<256,false>" if args.executor == "tc" else
+                "ozaki_imma_kernel",
+                "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)",
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                "launches": prod_n}
+
+    # ---- end to end through the public API with host buffers
+    H_host = h.H.to("cpu").pin_memory()
+    P_host = torch.empty_like(H_host).pin_memory()
+    e2e_times = []
+    for _ in range(max(args.e2e_steps, 1)):
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dmp.purify_host(H_host, n_occ, out=P_host, mode="int8", slices=s, executor=args.executor, ws=ws, P=P)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    te = torch.tensor([statistics.median(e2e_times)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": float(te.item()), "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8}
+
+    # ---- FP64 purification on the same GPU (once)
+    fp64 = None
+    if args.fp64 == "full":
+        ws64 = dmp.workspace(dmp.purify_workspace_bytes(n, dmp.make_opts("fp64")), dev)
+        P64 = torch.empty_like(H)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, i64 = dmp.purify(H, n_occ, mode="fp64", P=P64, ws=ws64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3
+        fp64 = {"value": t64, "unit": UNIT, "iters": i64["iters"], "status": dmp.status_str(i64["status"]),
+                "rel_energy": abs(i64["energy"] - E_star) / abs(E_star), "speedup_of_ozaki": t64 / per_step,
+                "max_abs_diff_vs_ozaki": float((P64 - P).abs().max().item())}
+        del ws64, P64
+
+    # ---- CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_samples > 0:
+        H_np = h.H.cpu().numpy()
+        vals = []
+        for k in range(args.cpu_samples):
+            v, _ = oracle_sample(H_np, n_occ, s, 7, info["iters"], seed=100 + k)
+            vals.append(v)
+        cpu = {"value": float(statistics.median(vals)), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{args.cpu_samples} samples: the oracle's Ozaki product (s={s}) on a 512x512 output block "
+                         f"of P0 P0 (row/column splits, exact level sums, recombination) plus one pass of its "
+                         f"n x n per-iterate work, scaled to the full product, 2 products per iteration and "
+                         f"{info['iters']} iterations; median"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": workload_name(w), "mode": "ozaki-int8", "slices": s, "executor": args.executor,
+                       "iters": info["iters"], "status": dmp.status_str(info["status"]),
+                       "rel_energy_error": rel_energy, "idempotency": info["idem"],
+                       "l2": "inputs larger than L2 (H 512 MiB, digit planes 1.8 GiB)", "slice_tuning": tune,
+                       "replicas": world},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "fp64_reference": fp64,
+            "phases_ms_per_step": {"products": prod_ms / args.steps, "splits": split_ms / args.steps,
+                                   "measures": meas_ms / args.steps, "init": init_ms / args.steps},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -200,6 +200,19 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
                        const void* tape, size_t tape_bytes, const double* dLdP, double* dLdH,
                        void* ws, size_t ws_bytes, void* stream);
 
+/* Kernel timing. While enabled, every kernel launch of the library is
+ * bracketed by two CUDA events recorded on the launching stream, tagged with
+ * its class: DMP_PROF_PRODUCT (slice-pair / FP64 product kernels), DMP_PROF_SPLIT
+ * (scaling and digit split), DMP_PROF_MEASURE (traces, norms, stopping rules),
+ * DMP_PROF_INIT (Gershgorin bounds and initial guess), DMP_PROF_OTHER.
+ * dmp_profile_read synchronises the recorded events and returns the summed
+ * device time (ms) and the launch count of one class. Host-side, process-wide,
+ * guarded by a mutex. */
+enum { DMP_PROF_PRODUCT = 0, DMP_PROF_SPLIT = 1, DMP_PROF_MEASURE = 2, DMP_PROF_INIT = 3, DMP_PROF_OTHER = 4 };
+int dmp_profile_enable(int on);
+int dmp_profile_reset(void);
+int dmp_profile_read(int32_t kind, double* total_ms, long long* launches);
+
 /* Name of a return code. */
 const char* dmp_status_str(int code);
 

@@ -189,6 +189,63 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
     return out
 
 
+def spectral_purify(x0, e, tol: float = 1e-10, max_iter: int = 100, energy_tol: float = 0.0):
+    """The purification loop of `purify` acting on eigenvalues.
+
+    When H = V diag(e) V^T, P_0 = V diag(x0) V^T with x0 = (lambda/n)(mu - e)
+    + n_occ/n, and every iterate is a polynomial in P_0, so all iterates share
+    V and each step maps the eigenvalues alone: tr(P^k) = sum x^k,
+    ||P^2 - P||_F = ||x^2 - x||_2 and tr(P H) = sum x e. This runs the same
+    stopping rules in O(n) per step (exact arithmetic; rounding differs from
+    the matrix loop). Returns iters, status, the final x and the histories.
+    """
+    x = np.asarray(x0, dtype=np.float64).copy()
+    e = np.asarray(e, dtype=np.float64)
+    band, cs = [], []
+    status = NOT_CONVERGED
+    k = 0
+    while True:
+        x2 = x * x
+        t1, t2 = float(np.sum(x)), float(np.sum(x2))
+        idem = float(np.linalg.norm(x2 - x))
+        band.append(2.0 * float(np.sum(x * e)))
+        if idem < tol:
+            status = CONVERGED
+            break
+        if k >= 2 and band[-1] > band[-2] > band[-3] and abs(band[-1] - band[-2]) < STALL_ABS \
+                and abs(band[-2] - band[-3]) < STALL_ABS:
+            status = STALLED
+            break
+        if energy_tol > 0 and k >= 1 and abs(band[-1] - band[-2]) < energy_tol:
+            status = CONVERGED
+            break
+        if k >= max_iter:
+            break
+        x3 = x2 * x
+        t3 = float(np.sum(x3))
+        if not (t1 - t2 > 0):
+            status = C_OUT_OF_RANGE
+            break
+        c = pm_coefficient(t1, t2, t3)
+        if not (0.0 <= c <= 1.0):
+            status = C_OUT_OF_RANGE
+            break
+        alpha, b2, b3, _ = pm_weights(c)
+        x = alpha * x + b2 * x2 + b3 * x3
+        cs.append(c)
+        k += 1
+    return dict(x=x, iters=k, status=status, band_history=band, c_history=cs)
+
+
+def initial_eigenvalues(H, n_occ: int, e):
+    """Eigenvalues of P_0 for H with eigenvalues e (same order as e)."""
+    n = np.asarray(H).shape[0]
+    h_min, h_max, _, _ = gershgorin(H)
+    mu = float(np.trace(H)) / n
+    lam = min(n_occ / (h_max - mu), (n - n_occ) / (mu - h_min))
+    return (lam / n) * (mu - np.asarray(e, dtype=np.float64)) + n_occ / n
+
+
 def error_metrics(P, H, P_ref=None, E_ref=None):
     """Error measures of Sec. "Error Evaluation Criteria", with K = 2P.
 

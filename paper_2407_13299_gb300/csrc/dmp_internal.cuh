@@ -142,3 +142,20 @@ __device__ __forceinline__ void upper_tile(int idx, int T, int& bi, int& bj) {
 }
 
 }  // namespace dmp
+
+namespace dmp {
+
+// Brackets one launch with profiling events when dmp_profile_enable(1) is on.
+class ProfScope {
+ public:
+  ProfScope(int kind, cudaStream_t st);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  cudaStream_t st_;
+  int idx_;
+};
+
+}  // namespace dmp

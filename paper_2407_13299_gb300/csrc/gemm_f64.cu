@@ -143,6 +143,7 @@ cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64
   p.done = done;
   const int tiles_m = static_cast<int>((m + BM - 1) / BM);
   const int ntiles = sym ? p.T * (p.T + 1) / 2 : tiles_m * p.tiles_n;
+  ProfScope prof(DMP_PROF_PRODUCT, st);
   gemm_f64_kernel<<<ntiles, THREADS, 0, st>>>(p);
   count_launch();
   return cudaGetLastError();

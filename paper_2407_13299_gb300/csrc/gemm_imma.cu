@@ -262,6 +262,7 @@ cudaError_t launch_ozaki_imma(const int8_t* A, const int8_t* B, const int32_t* e
   p.done = done;
   const int tiles_m = static_cast<int>(m_pad / BM);
   const int ntiles = sym ? p.T * (p.T + 1) / 2 : tiles_m * p.tiles_n;
+  ProfScope prof(DMP_PROF_PRODUCT, st);
   ozaki_imma_kernel<<<ntiles, THREADS, SMEM_BYTES, st>>>(p);
   count_launch();
   return cudaGetLastError();

@@ -543,6 +543,7 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   } else {
     ntiles = p.tiles_m * p.tiles_n;
   }
+  ProfScope prof(DMP_PROF_PRODUCT, st);
   return wide ? launch_tc_impl<128, true>(ta, tb, p, ntiles, st) : launch_tc_impl<256, false>(ta, tb, p, ntiles, st);
 }
 

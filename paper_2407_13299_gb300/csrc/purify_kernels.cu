@@ -305,6 +305,7 @@ cudaError_t launch_gershgorin_init(const double* H, int64_t n, int64_t ldh, int6
   int* flag = reinterpret_cast<int*>(rowbuf + 2 * n + static_cast<int64_t>(kColChunks) * n);
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
+  ProfScope prof(DMP_PROF_INIT, st);
   gersh_rows_kernel<<<static_cast<unsigned>(n), kRowThreads, 0, st>>>(H, n, ldh, U, D, flag);
   dim3 cg(static_cast<unsigned>((n + 127) / 128), kColChunks);
   gersh_cols_kernel<<<cg, 128, 0, st>>>(H, n, ldh, Cp);
@@ -322,6 +323,7 @@ size_t gershgorin_rowbuf_bytes(int64_t n) {
 cudaError_t launch_measure(const double* P, int64_t ldp, const double* X2, int64_t ldx,
                            const double* H, int64_t ldh, int64_t n, double* partials,
                            PurifyState* state, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_MEASURE, st);
   measure_kernel<<<kMeasureBlocks, 256, 0, st>>>(P, ldp, X2, ldx, H, ldh, n, partials, state);
   measure_final_kernel<<<1, 32, 0, st>>>(partials, kMeasureBlocks, state);
   count_launch(2);

@@ -161,6 +161,7 @@ cudaError_t launch_split_rows(const double* A, int64_t m, int64_t k, int64_t lda
   if (m_pad <= 0 || k_pad <= 0) return cudaSuccess;
   const int64_t plane_stride = m_pad * k_pad;
   dim3 grid(static_cast<unsigned>(m_pad));
+  ProfScope prof(DMP_PROF_SPLIT, st);
   if (elem_kind == 1) {
     split_rows_kernel<1><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, beta, exps, planes, k_pad,
                                                          plane_stride, flag, done);
@@ -179,6 +180,7 @@ cudaError_t launch_transpose(const double* A, int64_t m, int64_t n, int64_t lda,
                              cudaStream_t st) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   dim3 grid(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((m + 31) / 32));
+  ProfScope prof(DMP_PROF_OTHER, st);
   transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(A, m, n, lda, At);
   count_launch();
   return cudaGetLastError();

@@ -73,6 +73,9 @@ SIGNATURES = {
     "dmp_backward_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
     "dm_purify_backward": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(Opts), _vp, _sz, _vp, _vp, _vp,
                                           _sz, _vp]),
+    "dmp_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "dmp_profile_reset": (ctypes.c_int, []),
+    "dmp_profile_read": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "dmp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "dmp_launch_count": (ctypes.c_longlong, []),
     "dmp_version": (ctypes.c_char_p, []),
@@ -104,6 +107,26 @@ def status_str(code: int) -> str:
 def launch_count() -> int:
     """Kernels launched by libdmp in this process so far."""
     return int(lib().dmp_launch_count())
+
+
+PROF_PRODUCT, PROF_SPLIT, PROF_MEASURE, PROF_INIT, PROF_OTHER = 0, 1, 2, 3, 4
+
+
+def profile_enable(on: bool = True) -> None:
+    """Bracket every libdmp launch with CUDA events on its stream (dmp_profile_*)."""
+    lib().dmp_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    lib().dmp_profile_reset()
+
+
+def profile_read(kind: int):
+    """(total device ms, launches) of one kernel class since the last reset."""
+    ms = ctypes.c_double(0.0)
+    cnt = ctypes.c_longlong(0)
+    _check(lib().dmp_profile_read(int(kind), ctypes.byref(ms), ctypes.byref(cnt)), "dmp_profile_read")
+    return ms.value, cnt.value
 
 
 def _check(code: int, where: str, allow_status: bool = False) -> int:
@@ -169,12 +192,14 @@ def purify(H: torch.Tensor, n_occ: int, mode="int8", slices=7, executor="auto", 
     return P, info.as_dict()
 
 
-def purify_host(H_host: torch.Tensor, n_occ: int, **kw):
+def purify_host(H_host: torch.Tensor, n_occ: int, out: torch.Tensor | None = None, **kw):
     """End-to-end call from host memory: copies H to the device, purifies, and
-    copies P back (pinned host tensors keep the copies asynchronous)."""
+    copies P back into `out` (a host tensor; pinned memory keeps the copies at
+    full PCIe/C2C speed). Returns (P on the host, info)."""
     H = H_host.to("cuda", non_blocking=True)
     P, info = purify(H, n_occ, **kw)
-    out = torch.empty(P.shape, dtype=P.dtype, pin_memory=H_host.is_pinned())
+    if out is None:
+        out = torch.empty(P.shape, dtype=P.dtype, pin_memory=H_host.is_pinned())
     out.copy_(P, non_blocking=False)
     return out, info
 
