@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--fp64", default="full", choices=["full", "skip"], help="time the FP64 purification once")
     ap.add_argument("--cpu-samples", type=int, default=5, help="oracle samples for cpu_baseline (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--gen", default="device", choices=["device", "host"],
+                    help="where the QR of the input generator runs (host: numpy, for profiler runs)")
     return ap.parse_args()
 
 
@@ -270,9 +272,10 @@ def run_ours(args):
             dist.barrier()
 
     w = workload_params(args.n)
-    h = make_hamiltonian(w["n"], w["n_occ"], w["occ"], w["virt"], w["seed"], device=dev)
+    h = make_hamiltonian(w["n"], w["n_occ"], w["occ"], w["virt"], w["seed"],
+                         device=dev if args.gen == "device" else None)
     n, n_occ = w["n"], w["n_occ"]
-    H = h.H.contiguous()
+    H = torch.as_tensor(h.H).to(dev).contiguous()
     E_star = float(np.sum(h.e[:n_occ]))
     stream = torch.cuda.current_stream(dev)
 
@@ -352,7 +355,7 @@ def run_ours(args):
                 "launches": prod_n}
 
     # ---- end to end through the public API with host buffers
-    H_host = h.H.to("cpu").pin_memory()
+    H_host = H.to("cpu").pin_memory()
     P_host = torch.empty_like(H_host).pin_memory()
     e2e_times = []
     for _ in range(max(args.e2e_steps, 1)):
@@ -388,7 +391,7 @@ def run_ours(args):
     # ---- CPU oracle baseline (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and args.cpu_samples > 0:
-        H_np = h.H.cpu().numpy()
+        H_np = H.cpu().numpy()
         vals = []
         for k in range(args.cpu_samples):
             v, _ = oracle_sample(H_np, n_occ, s, 7, info["iters"], seed=100 + k)

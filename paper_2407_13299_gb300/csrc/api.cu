@@ -87,7 +87,7 @@ int64_t row_pad(int executor) { return executor == DMP_EXEC_TC ? 256 : kTileM; }
 
 // ---------------------------------------------------------------- dm_purify layout
 struct PurifyLayout {
-  size_t state, partials, rowbuf, expsP, expsX, err, Palt, X2, planesP, planesX, total;
+  size_t state, partials, rowbuf, expsP, expsX, err, Palt, X2, planesP, planesX, scratch, total;
   int64_t n_pad, k_pad;
 };
 
@@ -111,6 +111,7 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
   } else {
     L.planesP = L.planesX = 0;
   }
+  L.scratch = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_scratch_bytes()) : 0;
   L.total = c.cur;
   return L;
 }
@@ -118,9 +119,10 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
 // One Ozaki product from prepared digit planes on the chosen executor.
 cudaError_t launch_product(const Opts& o, const void* pa, const void* pb, const int32_t* ea, const int32_t* eb,
                            int64_t m, int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int sym,
-                           const EpiArgs& epi, const int* done, int* err, cudaStream_t st) {
+                           const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st) {
   if (o.executor == DMP_EXEC_TC)
-    return launch_ozaki_tc(pa, pb, ea, eb, m, n, rows_a, rows_b, k_pad, o.s, o.beta, sym, epi, done, err, st);
+    return launch_ozaki_tc(pa, pb, ea, eb, m, n, rows_a, rows_b, k_pad, o.s, o.beta, sym, epi, done, err, scratch,
+                           st);
   return launch_ozaki_imma(static_cast<const int8_t*>(pa), static_cast<const int8_t*>(pb), ea, eb, m, n, rows_a,
                            rows_b, k_pad, o.s, o.beta, sym, epi, done, st);
 }
@@ -225,6 +227,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   void* planesP = o.mode != DMP_FP64 ? at(ws, L.planesP) : nullptr;
   void* planesX = o.mode != DMP_FP64 ? at(ws, L.planesX) : nullptr;
   int* err = reinterpret_cast<int*>(at(ws, L.err));
+  double* scratch = L.scratch ? reinterpret_cast<double*>(at(ws, L.scratch)) : nullptr;
   DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
   PurifyState init;
@@ -260,7 +263,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
       DMP_CUDA(launch_split_rows(cur, n, n, ldcur, o.s, o.beta, expsP, planesP, L.n_pad, L.k_pad,
                                  elem_kind(o.executor), nullptr, done, st));
       DMP_CUDA(launch_product(o, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e2, done,
-                              err, st));
+                              err, scratch, st));
     }
     DMP_CUDA(launch_measure(cur, ldcur, X2, n, H, ldh, n, partials, state, st));
     int32_t flags[2] = {0, 0};
@@ -287,7 +290,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
       DMP_CUDA(launch_split_rows(X2, n, n, n, o.s, o.beta, expsX, planesX, L.n_pad, L.k_pad,
                                  elem_kind(o.executor), nullptr, done, st));
       DMP_CUDA(launch_product(o, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e3, done,
-                              err, st));
+                              err, scratch, st));
     }
     std::swap(cur, alt);
     std::swap(ldcur, ldalt);
@@ -358,6 +361,7 @@ int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int
   c.take(m_pad * sizeof(int32_t));
   c.take(n_pad * sizeof(int32_t));
   c.take(sizeof(int32_t));
+  c.take(o.executor == DMP_EXEC_TC ? tc_scratch_bytes() : 0);
   c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o.executor));
   c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o.executor));
   c.take(static_cast<size_t>(n) * k * sizeof(double));
@@ -396,6 +400,7 @@ static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_
   int32_t* ea = reinterpret_cast<int32_t*>(at(ws, c.take(m_pad * sizeof(int32_t))));
   int32_t* eb = reinterpret_cast<int32_t*>(at(ws, c.take(n_pad * sizeof(int32_t))));
   int* err = reinterpret_cast<int*>(at(ws, c.take(sizeof(int32_t))));
+  double* scratch = reinterpret_cast<double*>(at(ws, c.take(o.executor == DMP_EXEC_TC ? tc_scratch_bytes() : 0)));
   void* pa = at(ws, c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o.executor)));
   void* pb = at(ws, c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o.executor)));
   double* Bt = reinterpret_cast<double*>(at(ws, c.take(static_cast<size_t>(n) * k * sizeof(double))));
@@ -405,7 +410,7 @@ static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_
   DMP_CUDA(launch_split_rows(Bt, n, k, k, o.s, o.beta, eb, pb, n_pad, k_pad, elem_kind(o.executor), nullptr,
                              nullptr, st));
   if (o.executor == DMP_EXEC_TC) DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  DMP_CUDA(launch_product(o, pa, pb, ea, eb, m, n, m_pad, n_pad, k_pad, 0, epi, nullptr, err, st));
+  DMP_CUDA(launch_product(o, pa, pb, ea, eb, m, n, m_pad, n_pad, k_pad, 0, epi, nullptr, err, scratch, st));
   if (o.executor == DMP_EXEC_TC) {
     // report an expired device wait; skipped while the stream is being captured
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

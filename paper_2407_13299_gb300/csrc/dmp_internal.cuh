@@ -88,10 +88,14 @@ cudaError_t launch_ozaki_imma(const int8_t* A, const int8_t* B, const int32_t* e
 // tcgen05 executor (bf16-carried digits, TMEM accumulators, TMA operands).
 // A planes [s][rows_a][k_pad], B planes [s][rows_b][k_pad] in bfloat16; rows_a
 // a multiple of 128, rows_b of 256 (beta 7) or 128 (beta 8), k_pad of 64.
-// *err is set to 1 if a bounded device wait expired.
+// *err is set to 1 if a bounded device wait expired. `scratch` holds
+// tc_scratch_bytes() of per-CTA float64 partial sums (the kernel is persistent:
+// at most kTcMaxCtas CTAs, one per SM).
+constexpr int kTcMaxCtas = 160;
+size_t tc_scratch_bytes();
 cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, const int32_t* eb, int64_t m,
                             int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int s, int beta, int sym,
-                            const EpiArgs& epi, const int* done, int* err, cudaStream_t st);
+                            const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st);
 
 // FP64 executor: C = A B (A m x k, B k x n row-major) with the same epilogues.
 cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m,

@@ -56,7 +56,8 @@ struct TcCfg {
 };
 
 struct TcParams {
-  int s, beta, KT, CH;
+  int s, beta, KT, CH, ntiles;
+  double* scratch;  // per-CTA float64 partial sums, TC_BM * BN doubles per CTA
   int64_t m, n;
   int64_t rows_a, rows_b;  // padded rows per digit plane
   int sym, tiles_m, tiles_n;
@@ -142,6 +143,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major operand tile, rows of 128 bytes,
@@ -182,10 +190,9 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
 __device__ __forceinline__ int npairs_of(int L, int s) { return min(s, L - 1) - max(1, L - s) + 1; }
 
 template <int BN>
-__device__ __forceinline__ void tile_of(const TcParams& p, int& bi, int& bj) {
-  int idx = blockIdx.x;
+__device__ __forceinline__ void tile_of(const TcParams& p, int idx, int& bi, int& bj) {
   if (!p.sym) {
-    bj = idx / p.tiles_m;  // column-block major: neighbouring CTAs share B
+    bj = idx / p.tiles_m;  // column-block major: CTAs running together share B blocks
     bi = idx % p.tiles_m;
     return;
   }
@@ -199,6 +206,9 @@ __device__ __forceinline__ void tile_of(const TcParams& p, int& bi, int& bj) {
   bi = idx;
 }
 
+// Persistent: one CTA per SM walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// The three roles keep their ring and buffer phases across tiles, so the next
+// tile's loads and MMAs overlap the current tile's last fold and output.
 template <int BN, bool WIDE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -220,11 +230,6 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-
-  int bi, bj;
-  tile_of<BN>(p, bi, bj);
-  const int64_t m0 = static_cast<int64_t>(bi) * TC_BM;
-  const int64_t n0 = static_cast<int64_t>(bj) * BN;
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < Cfg::STAGES; ++st) {
@@ -263,26 +268,32 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       uint32_t phase = 0;
       bool ok = true;
       uint32_t armed = 0;  // stages armed in the current ring pass (for the abort drain)
-      for (int L = s + 1; L >= 2 && ok; --L) {
-        const int i_lo = max(1, L - s), i_hi = min(s, L - 1);
-        for (int i = i_lo; i <= i_hi && ok; ++i) {
-          const int j = L - i;
-          const int ya = static_cast<int>((i - 1) * p.rows_a + m0);
-          const int yb = static_cast<int>((j - 1) * p.rows_b + n0);
-          for (int kt = 0; kt < KT; ++kt) {
-            if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, p)) {
-              ok = false;
-              break;
-            }
-            const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
-            mbar_arrive_expect_tx(full_bar(stage), Cfg::STAGE_BYTES);
-            tma_load_2d(sa, &tmA, full_bar(stage), kt * TC_BK, ya);
-            tma_load_2d(sa + Cfg::A_BYTES, &tmB, full_bar(stage), kt * TC_BK, yb);
-            armed |= 1u << stage;
-            if (++stage == Cfg::STAGES) {
-              stage = 0;
-              phase ^= 1u;
-              armed = 0;
+      for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+        int bi, bj;
+        tile_of<BN>(p, tile, bi, bj);
+        const int64_t m0 = static_cast<int64_t>(bi) * TC_BM;
+        const int64_t n0 = static_cast<int64_t>(bj) * BN;
+        for (int L = s + 1; L >= 2 && ok; --L) {
+          const int i_lo = max(1, L - s), i_hi = min(s, L - 1);
+          for (int i = i_lo; i <= i_hi && ok; ++i) {
+            const int j = L - i;
+            const int ya = static_cast<int>((i - 1) * p.rows_a + m0);
+            const int yb = static_cast<int>((j - 1) * p.rows_b + n0);
+            for (int kt = 0; kt < KT; ++kt) {
+              if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, p)) {
+                ok = false;
+                break;
+              }
+              const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
+              mbar_arrive_expect_tx(full_bar(stage), Cfg::STAGE_BYTES);
+              tma_load_2d(sa, &tmA, full_bar(stage), kt * TC_BK, ya);
+              tma_load_2d(sa + Cfg::A_BYTES, &tmB, full_bar(stage), kt * TC_BK, yb);
+              armed |= 1u << stage;
+              if (++stage == Cfg::STAGES) {
+                stage = 0;
+                phase ^= 1u;
+                armed = 0;
+              }
             }
           }
         }
@@ -308,43 +319,45 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       uint32_t aph[2] = {0u, 0u};
       bool ok = true;
       bool issued = false;
-      for (int L = s + 1; L >= 2 && ok; --L) {
-        const int nkb = npairs_of(L, s) * KT;
-        for (int kb = 0; kb < nkb; ++kb) {
-          const int kc = kb % CH;
-          const bool first = kc == 0;
-          const bool last = (kc == CH - 1) || (kb == nkb - 1);
-          if (first) {
-            if (!wait_bar(accempty_bar(buf), aph[buf] ^ 1u, abort_flag, p)) {
+      for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+        for (int L = s + 1; L >= 2 && ok; --L) {
+          const int nkb = npairs_of(L, s) * KT;
+          for (int kb = 0; kb < nkb; ++kb) {
+            const int kc = kb % CH;
+            const bool first = kc == 0;
+            const bool last = (kc == CH - 1) || (kb == nkb - 1);
+            if (first) {
+              if (!wait_bar(accempty_bar(buf), aph[buf] ^ 1u, abort_flag, p)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+            }
+            if (!wait_bar(full_bar(stage), phase, abort_flag, p)) {
               ok = false;
               break;
             }
             tc_fence_after();
-          }
-          if (!wait_bar(full_bar(stage), phase, abort_flag, p)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
-          const uint64_t ad = sdesc_sw128(sa);
-          const uint64_t bd = sdesc_sw128(sa + Cfg::A_BYTES);
-          const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
+            const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
+            const uint64_t ad = sdesc_sw128(sa);
+            const uint64_t bd = sdesc_sw128(sa + Cfg::A_BYTES);
+            const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
 #pragma unroll
-          for (int ks = 0; ks < TC_BK / 16; ++ks) {
-            // advance 16 bf16 = 32 bytes along K inside the swizzled row
-            umma_bf16(d, ad + 2ull * ks, bd + 2ull * ks, idesc, (first && ks == 0) ? 0u : 1u);
-          }
-          issued = true;
-          umma_commit(empty_bar(stage));
-          if (last) {
-            umma_commit(accfull_bar(buf));
-            aph[buf] ^= 1u;
-            buf ^= 1;
-          }
-          if (++stage == Cfg::STAGES) {
-            stage = 0;
-            phase ^= 1u;
+            for (int ks = 0; ks < TC_BK / 16; ++ks) {
+              // advance 16 bf16 = 32 bytes along K inside the swizzled row
+              umma_bf16(d, ad + 2ull * ks, bd + 2ull * ks, idesc, (first && ks == 0) ? 0u : 1u);
+            }
+            issued = true;
+            umma_commit(empty_bar(stage));
+            if (last) {
+              umma_commit(accfull_bar(buf));
+              aph[buf] ^= 1u;
+              buf ^= 1;
+            }
+            if (++stage == Cfg::STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
         }
       }
@@ -363,75 +376,96 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const int q = warp & 3;   // TMEM lane quadrant this warp may access
     const int h = e >> 2;     // which half of the BN columns
     const int row = 32 * q + lane;
-    const int64_t r = m0 + row;
     const int cbase = h * COLS;
     const uint32_t taddr_row = tmem + (static_cast<uint32_t>(32 * q) << 16);
-    const bool row_ok = r < p.m;
-    const int32_t er = row_ok ? p.ea[r] : 0;
+    // this thread's float64 partial sums: element c at scr[32 c] (a warp touches
+    // 256 contiguous bytes per column), private to this CTA and L2-resident
+    double* scr = p.scratch + static_cast<int64_t>(blockIdx.x) * (TC_BM * BN) + e * (COLS * 32) + lane;
 
     int32_t S[COLS];
     int32_t Shi[WIDE ? COLS : 1];
     int buf = 0;
     uint32_t aph[2] = {0u, 0u};
     bool ok = true;
-    for (int L = s + 1; L >= 2 && ok; --L) {
+    for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+      int bi, bj;
+      tile_of<BN>(p, tile, bi, bj);
+      const int64_t m0 = static_cast<int64_t>(bi) * TC_BM;
+      const int64_t n0 = static_cast<int64_t>(bj) * BN;
+      const int64_t r = m0 + row;
+      const bool row_ok = r < p.m;
+      const int32_t er = row_ok ? p.ea[r] : 0;
+      for (int L = s + 1; L >= 2 && ok; --L) {
 #pragma unroll
-      for (int c = 0; c < COLS; ++c) {
-        S[c] = 0;
-        if (WIDE) Shi[c] = 0;
-      }
-      const int nkb = npairs_of(L, s) * KT;
-      const int nch = (nkb + CH - 1) / CH;
-      for (int ch = 0; ch < nch; ++ch) {
-        // the whole warp takes the same branch: tcgen05.ld below is warp-collective
-        const bool got = wait_bar(accfull_bar(buf), aph[buf], abort_flag, p);
-        if (!__all_sync(0xffffffffu, got)) {
-          ok = false;
-          break;
+        for (int c = 0; c < COLS; ++c) {
+          S[c] = 0;
+          if (WIDE) Shi[c] = 0;
         }
-        tc_fence_after();
-#pragma unroll
-        for (int g = 0; g < COLS / 32; ++g) {
-          uint32_t v[32];
-          tmem_ld32(taddr_row + static_cast<uint32_t>(buf * BN + cbase + 32 * g), v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int t = 0; t < 32; ++t) S[32 * g + t] += __float2int_rn(__uint_as_float(v[t]));
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(accempty_bar(buf));
-        aph[buf] ^= 1u;
-        buf ^= 1;
-        if (WIDE && ((ch & 63) == 63 || ch == nch - 1)) {
-          // keep the low word in [0, 2^24): value = hi 2^24 + lo
-#pragma unroll
-          for (int c = 0; c < COLS; ++c) {
-            Shi[c] += S[c] >> 24;
-            S[c] &= 0xFFFFFF;
+        const int nkb = npairs_of(L, s) * KT;
+        const int nch = (nkb + CH - 1) / CH;
+        for (int ch = 0; ch < nch; ++ch) {
+          // the whole warp takes the same branch: tcgen05.ld below is warp-collective
+          const bool got = wait_bar(accfull_bar(buf), aph[buf], abort_flag, p);
+          if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
           }
-        }
-      }
-      if (!ok) break;
-      // ---- fold the exact level sum S_L
-      if (p.epi.kind == EPI_LEVELS) {
-        if (row_ok) {
+          tc_fence_after();
 #pragma unroll
-          for (int c = 0; c < COLS; ++c) {
-            const int64_t col = n0 + cbase + c;
-            if (col < p.n) {
-              const int32_t val = WIDE ? static_cast<int32_t>(static_cast<int64_t>(Shi[c]) * 16777216ll + S[c]) : S[c];
-              p.epi.levels[static_cast<int64_t>(L - 2) * p.m * p.n + r * p.n + col] = val;
+          for (int g = 0; g < COLS / 16; ++g) {
+            uint32_t v[16];
+            tmem_ld16(taddr_row + static_cast<uint32_t>(buf * BN + cbase + 16 * g), v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int t = 0; t < 16; ++t) S[16 * g + t] += __float2int_rn(__uint_as_float(v[t]));
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(accempty_bar(buf));
+          aph[buf] ^= 1u;
+          buf ^= 1;
+          if (WIDE && ((ch & 63) == 63 || ch == nch - 1)) {
+            // keep the low word in [0, 2^24): value = hi 2^24 + lo
+#pragma unroll
+            for (int c = 0; c < COLS; ++c) {
+              Shi[c] += S[c] >> 24;
+              S[c] &= 0xFFFFFF;
             }
           }
         }
-        continue;
-      }
-      const double scale = ldexp(1.0, -p.beta * L);
-      const bool first_level = (L == s + 1);
-      const bool final_level = (L == 2);
-      if (row_ok) {
-        double* accrow = p.epi.C + r * p.epi.ldc;
+        if (!ok) break;
+        // ---- fold the exact level sum S_L
+        if (p.epi.kind == EPI_LEVELS) {
+          if (row_ok) {
+#pragma unroll
+            for (int c = 0; c < COLS; ++c) {
+              const int64_t col = n0 + cbase + c;
+              if (col < p.n) {
+                const int32_t val =
+                    WIDE ? static_cast<int32_t>(static_cast<int64_t>(Shi[c]) * 16777216ll + S[c]) : S[c];
+                p.epi.levels[static_cast<int64_t>(L - 2) * p.m * p.n + r * p.n + col] = val;
+              }
+            }
+          }
+          continue;
+        }
+        const double scale = ldexp(1.0, -p.beta * L);
+        const bool first_level = (L == s + 1);
+        if (L != 2) {
+#pragma unroll
+          for (int c = 0; c < COLS; ++c) {
+            const double Sd = WIDE ? static_cast<double>(Shi[c]) * 16777216.0 + static_cast<double>(S[c])
+                                   : static_cast<double>(S[c]);
+            scr[32 * c] = first_level ? Sd * scale : fma(Sd, scale, scr[32 * c]);
+          }
+          continue;
+        }
+        // last level: finish the sum, unscale, and apply the output step
+        if (!row_ok) continue;
+        const bool upd = p.epi.kind == EPI_PM_UPDATE;
+        const double wa = upd ? p.epi.state->alpha : 0.0;
+        const double w2 = upd ? p.epi.state->b2 : 0.0;
+        const double w3 = upd ? p.epi.state->b3 : 0.0;
 #pragma unroll
         for (int c = 0; c < COLS; ++c) {
           const int64_t col = n0 + cbase + c;
@@ -439,15 +473,16 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           if (p.sym && r > col) continue;  // the (col, r) element's mirror covers it
           const double Sd = WIDE ? static_cast<double>(Shi[c]) * 16777216.0 + static_cast<double>(S[c])
                                  : static_cast<double>(S[c]);
-          double acc = first_level ? Sd * scale : fma(Sd, scale, accrow[col]);
-          if (!final_level) {
-            accrow[col] = acc;
-          } else {
-            const int32_t ec = p.eb[col];
-            const double v = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                              : ldexp(acc, er + ec);
-            epi_apply(p.epi, r, col, v, p.sym && r < col);
+          const double acc = first_level ? Sd * scale : fma(Sd, scale, scr[32 * c]);
+          const int32_t ec = p.eb[col];
+          double v = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                      : ldexp(acc, er + ec);
+          if (upd) {
+            // P and P^2 are exactly symmetric: read them at (col, r), coalesced across the warp
+            v = wa * p.epi.P[col * p.epi.ldp + r] + w2 * p.epi.X2[col * p.epi.ldx + r] + w3 * v;
           }
+          p.epi.C[r * p.epi.ldc + col] = v;
+          if (p.sym && r < col) p.epi.C[col * p.epi.ldc + r] = v;
         }
       }
     }
@@ -507,11 +542,22 @@ cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const T
 
 }  // namespace
 
-int tc_row_pad() { return 256; }
+int tc_max_ctas() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return std::min(sms, kTcMaxCtas);
+}
+
+size_t tc_scratch_bytes() { return static_cast<size_t>(kTcMaxCtas) * TC_BM * 256 * sizeof(double); }
 
 cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, const int32_t* eb, int64_t m,
                             int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int s, int beta, int sym,
-                            const EpiArgs& epi, const int* done, int* err, cudaStream_t st) {
+                            const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   const bool wide = beta == 8;
   const int BN = wide ? 128 : 256;
@@ -543,8 +589,11 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   } else {
     ntiles = p.tiles_m * p.tiles_n;
   }
+  p.ntiles = ntiles;
+  p.scratch = scratch;
+  const int grid = std::min(ntiles, tc_max_ctas());
   ProfScope prof(DMP_PROF_PRODUCT, st);
-  return wide ? launch_tc_impl<128, true>(ta, tb, p, ntiles, st) : launch_tc_impl<256, false>(ta, tb, p, ntiles, st);
+  return wide ? launch_tc_impl<128, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
 }
 
 }  // namespace dmp
