@@ -146,6 +146,36 @@ int ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, co
                void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * ozaki_gemm_noalloc: ozaki_gemm without a workspace argument. (The paper has
+ * no counterpart; this is a convenience of this library.)
+ *
+ * Some callers cannot supply device scratch memory: a C or Fortran host code
+ * that has no device allocator of its own to size and keep a buffer alive, or
+ * a caller in the middle of its own GPU pipeline that must not allocate
+ * because a device allocation can synchronise the device and stall its other
+ * streams. This entry point serves them. It computes exactly what ozaki_gemm
+ * computes (same kernels, same bits), with all scratch taken from one fixed
+ * 128 MiB array in device memory that the library defines. The call makes no
+ * allocation of its own (no cudaMalloc/cudaFree, no allocating library call).
+ *   - The array belongs to the library: every GPU that loads it keeps the
+ *     128 MiB until the process exits.
+ *   - Its first call on a device looks up the array's device address (one
+ *     cudaGetSymbolAddress with that device current) and caches it; make that
+ *     first call before any stream capture.
+ *   - All calls share the one array, so calls that overlap on the GPU (on
+ *     different streams, or from several threads) race and give undefined
+ *     results. Serialise them.
+ *   - Problems whose scratch (as ozaki_gemm_workspace_size reports it) exceeds
+ *     128 MiB are rejected with DMP_ERR_WORKSPACE before any work is enqueued;
+ *     at s = 7 square problems fit up to m = n = k = 1536 on the tcgen05
+ *     executor and 2432 on the int8 mma executor. DMP_FP64 needs no scratch.
+ * Arguments and the other return codes are those of ozaki_gemm.
+ */
+int ozaki_gemm_noalloc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                       const double* B, int64_t ldb, double* C, int64_t ldc, int32_t mode,
+                       int32_t slices, int32_t executor, void* stream);
+
+/*
  * ozaki_level_sums: the exact integer slice-pair products of ozaki_gemm,
  * S[L-2][i][j] = (sum_{a+b=L} A_a B_b)[i][j] as int32, L = 2..s+1, written to
  * S (s x m x n, row-major, leading dimension n). Exposed so that the integer

@@ -63,6 +63,8 @@ SIGNATURES = {
     "ozaki_gemm_workspace_size": (ctypes.c_int, [_i64, _i64, _i64, _i32, _i32, _i32, _szp]),
     "ozaki_gemm": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _i32, _i32,
                                   _vp, _sz, _vp]),
+    "ozaki_gemm_noalloc": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _i32, _i32,
+                                          _vp]),
     "ozaki_level_sums": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i32, _i32, _i32,
                                         _vp, _sz, _vp]),
     "ozaki_split": (ctypes.c_int, [_i64, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
