@@ -19,7 +19,8 @@
  *     enqueued on it.
  *   - Workspace: every call that needs scratch takes a caller-allocated device
  *     buffer `ws` of `ws_bytes`, sized by the matching *_workspace_size call;
- *     the library allocates no device memory of its own.
+ *     the library allocates no device memory of its own (the one exception
+ *     is the fixed array behind ozaki_gemm_noalloc).
  *   - Return value: 0 (DMP_OK) or a positive numerical status for purification
  *     (see below), or a negative error. No C++ exception crosses this ABI.
  *   - Thread safety: calls on different streams with different workspaces may
@@ -67,6 +68,12 @@ enum {
   DMP_ERR_WORKSPACE = -6    /* ws_bytes (or tape_bytes) smaller than required      */
 };
 
+/* DMP_FLAG_BOUNDS_CONSTANT: dm_purify_backward treats the Gershgorin bounds
+ * h_min, h_max of the initial guess as constants (no gradient through their
+ * extreme rows). At convergence both choices agree to the convergence level,
+ * because the converged projector does not depend on P_0. */
+enum { DMP_FLAG_BOUNDS_CONSTANT = 1 };
+
 /* Options. Zero-initialise and set what you need; zeros select defaults. */
 typedef struct {
   int32_t mode;             /* DMP_FP64 / DMP_OZAKI_INT8 / DMP_OZAKI_BF16           */
@@ -74,7 +81,7 @@ typedef struct {
   int32_t executor;         /* DMP_EXEC_*                                            */
   int32_t max_iter;         /* 0 -> 100 (the paper's cap)                            */
   int32_t checkpoint_every; /* forward iterates kept every k steps for the adjoint; 0 -> 8 */
-  int32_t reserved;
+  int32_t flags;            /* DMP_FLAG_* bits                                       */
   double tol;               /* ||P^2 - P||_F threshold; 0 -> 1e-10                   */
   double energy_tol;        /* optional |change of Tr(HK)| threshold; 0 = off        */
 } dmp_opts;
@@ -217,14 +224,26 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n,
 int dmp_backward_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
 
 /*
- * dm_purify_backward: reverse mode through the purification dm_purify ran with
- * `tape`, giving dL/dH for a loss L(P) from G = dL/dP (n x n, leading dimension
- * n). Each step k is differentiated with its branch and iteration count frozen
- * and with the dependence of c_k on P_k kept; the iterates are recomputed from
- * the checkpoints of the tape. dLdH (n x n, leading dimension n) is the
- * gradient with respect to H as a general matrix (the Gershgorin bounds enter
- * through their extreme rows); for a symmetric perturbation of H_ij and H_ji
- * the change of L is dLdH[i][j] + dLdH[j][i]. Products use the forward's mode.
+ * dm_purify_backward: reverse mode through the purification that dm_purify
+ * ran with `tape` and the same options, giving dL/dH for a loss L(P) from
+ * G = dL/dP (n x n, leading dimension n). Each step k is differentiated with
+ * its branch and the iteration count frozen and with the dependence of the
+ * coefficient c_k on P_k kept:
+ *   dL/dP_k = alpha G + b2 (G P + P G) + b3 (G P^2 + P G P + P^2 G)
+ *             + <G, alpha' P + b2' P^2 + b3' P^3> dc/dP,
+ *   dc/dP = ((2P - 3P^2) tr(P - P^2) - tr(P^2 - P^3)(I - 2P)) / tr(P - P^2)^2,
+ * (alpha, b2, b3) the weights of the branch c selected and ' their derivatives
+ * in c), then through the initial guess: the direct term -(lambda/n) G_0, the
+ * trace term of mu = tr(H)/n and lambda through its active branch and the
+ * Gershgorin extreme rows (unless opts->flags has DMP_FLAG_BOUNDS_CONSTANT).
+ * The iterates are recomputed from the tape's checkpoints segment by segment
+ * (bit-identical to the forward's); products run in the forward's mode.
+ *   H     the forward's H, leading dimension n.
+ *   dLdH  n x n, leading dimension n: the gradient for symmetric H, i.e. the
+ *         symmetric part of the gradient with respect to H as a general
+ *         matrix. A perturbation of H_ij and H_ji by h changes L by
+ *         2 h dLdH[i][j] (i != j); of H_ii by h, by h dLdH[i][i].
+ * The call synchronises `stream` once per checkpoint segment and on return.
  */
 int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts* opts,
                        const void* tape, size_t tape_bytes, const double* dLdP, double* dLdH,

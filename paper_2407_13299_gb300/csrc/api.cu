@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "dmp_internal.cuh"
 
@@ -152,6 +153,48 @@ TapeLayout tape_layout(int64_t n, const Opts& o) {
 }
 
 inline char* at(void* base, size_t off) { return static_cast<char*>(base) + off; }
+
+// dm_purify_backward workspace: six n x n matrices (G, G', Y, Z, YP, ZP), the
+// recomputed iterates and squares of one checkpoint segment, and the split
+// buffers of one product.
+struct BackwardLayout {
+  size_t state, scalars, p0, partials, err, expsP, expsA, G, Gn, Y, Z, YP, ZP, segP, segX, planesP, planesA,
+      scratch, total;
+  int64_t n_pad, k_pad;
+};
+
+BackwardLayout backward_layout(int64_t n, const Opts& o) {
+  BackwardLayout B;
+  Carver c;
+  const size_t nn = static_cast<size_t>(n) * n * sizeof(double);
+  B.n_pad = round_up(n, o.mode == DMP_FP64 ? kTileM : row_pad(o.executor));
+  B.k_pad = round_up(n, kPadK);
+  B.state = c.take(sizeof(PurifyState));
+  B.scalars = c.take(sizeof(AdjScalars));
+  B.p0 = c.take(sizeof(P0Adjoint));
+  B.partials = c.take(304 * 5 * sizeof(double));
+  B.err = c.take(sizeof(int32_t));
+  B.expsP = c.take(static_cast<size_t>(B.n_pad) * sizeof(int32_t));
+  B.expsA = c.take(static_cast<size_t>(B.n_pad) * sizeof(int32_t));
+  B.G = c.take(nn);
+  B.Gn = c.take(nn);
+  B.Y = c.take(nn);
+  B.Z = c.take(nn);
+  B.YP = c.take(nn);
+  B.ZP = c.take(nn);
+  B.segP = c.take(nn * o.every);
+  B.segX = c.take(nn * o.every);
+  if (o.mode != DMP_FP64) {
+    const size_t plane = static_cast<size_t>(o.s) * B.n_pad * B.k_pad * elem_bytes(o.executor);
+    B.planesP = c.take(plane);
+    B.planesA = c.take(plane);
+  } else {
+    B.planesP = B.planesA = 0;
+  }
+  B.scratch = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_scratch_bytes()) : 0;
+  B.total = c.cur;
+  return B;
+}
 
 }  // namespace
 }  // namespace dmp
@@ -498,16 +541,177 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
 }
 
 int dmp_backward_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes) {
-  (void)n; (void)opts; (void)bytes;
-  return DMP_ERR_UNSUPPORTED;
+  Opts o;
+  const int rc = normalize(opts, o);
+  if (rc != DMP_OK) return rc;
+  if (n < 2 || bytes == nullptr) return DMP_ERR_INVALID_ARG;
+  *bytes = backward_layout(n, o).total;
+  return DMP_OK;
 }
 
 int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts* opts, const void* tape,
                        size_t tape_bytes, const double* dLdP, double* dLdH, void* ws, size_t ws_bytes,
                        void* stream) {
-  (void)H; (void)n; (void)n_occ; (void)opts; (void)tape; (void)tape_bytes; (void)dLdP; (void)dLdH;
-  (void)ws; (void)ws_bytes; (void)stream;
-  return DMP_ERR_UNSUPPORTED;
+  Opts o;
+  int rc = normalize(opts, o);
+  if (rc != DMP_OK) return rc;
+  if (H == nullptr || tape == nullptr || dLdP == nullptr || dLdH == nullptr || ws == nullptr)
+    return DMP_ERR_INVALID_ARG;
+  if (n < 2 || n_occ <= 0 || n_occ >= n) return DMP_ERR_INVALID_ARG;
+  const TapeLayout TL = tape_layout(n, o);
+  if (tape_bytes < TL.total) return DMP_ERR_WORKSPACE;
+  const BackwardLayout B = backward_layout(n, o);
+  if (ws_bytes < B.total) return DMP_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  // ---- what the forward recorded
+  TapeHeader hd;
+  DMP_CUDA(cudaMemcpyAsync(&hd, static_cast<const char*>(tape) + TL.header, sizeof(hd), cudaMemcpyDeviceToHost, st));
+  std::vector<double> cs(static_cast<size_t>(o.max_iter) + 1, 0.0);
+  DMP_CUDA(cudaMemcpyAsync(cs.data(), static_cast<const char*>(tape) + TL.coeffs, cs.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaStreamSynchronize(st));
+  if (hd.magic != kTapeMagic || hd.n != n || hd.every != o.every || hd.mode != o.mode ||
+      (o.mode != DMP_FP64 && (hd.s != o.s || hd.executor != o.executor)))
+    return DMP_ERR_INVALID_ARG;
+  if (hd.status < 0) return hd.status;
+  const int K = hd.iters;
+  const double* ckpt = reinterpret_cast<const double*>(static_cast<const char*>(tape) + TL.ckpt);
+  const size_t nn = static_cast<size_t>(n) * n;
+
+  double* G = reinterpret_cast<double*>(at(ws, B.G));
+  double* Gn = reinterpret_cast<double*>(at(ws, B.Gn));
+  double* Y = reinterpret_cast<double*>(at(ws, B.Y));
+  double* Z = reinterpret_cast<double*>(at(ws, B.Z));
+  double* YP = reinterpret_cast<double*>(at(ws, B.YP));
+  double* ZP = reinterpret_cast<double*>(at(ws, B.ZP));
+  double* segP = reinterpret_cast<double*>(at(ws, B.segP));
+  double* segX = reinterpret_cast<double*>(at(ws, B.segX));
+  PurifyState* state = reinterpret_cast<PurifyState*>(at(ws, B.state));
+  AdjScalars* sc = reinterpret_cast<AdjScalars*>(at(ws, B.scalars));
+  P0Adjoint* p0s = reinterpret_cast<P0Adjoint*>(at(ws, B.p0));
+  double* part = reinterpret_cast<double*>(at(ws, B.partials));
+  int* err = reinterpret_cast<int*>(at(ws, B.err));
+  int32_t* expsP = reinterpret_cast<int32_t*>(at(ws, B.expsP));
+  int32_t* expsA = reinterpret_cast<int32_t*>(at(ws, B.expsA));
+  void* planesP = o.mode != DMP_FP64 ? at(ws, B.planesP) : nullptr;
+  void* planesA = o.mode != DMP_FP64 ? at(ws, B.planesA) : nullptr;
+  double* scratch = B.scratch ? reinterpret_cast<double*>(at(ws, B.scratch)) : nullptr;
+  DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  const int64_t npad = B.n_pad, kpad = B.k_pad;
+
+  // C = A P (P symmetric; its planes are already in planesP for the Ozaki modes)
+  auto times_P = [&](const double* A, const double* Pk, double* C) -> cudaError_t {
+    EpiArgs e{};
+    e.kind = EPI_STORE;
+    e.C = C;
+    e.ldc = n;
+    if (o.mode == DMP_FP64) return launch_gemm_f64(A, n, Pk, n, n, n, n, 0, e, nullptr, st);
+    cudaError_t r = launch_split_rows(A, n, n, n, o.s, o.beta, expsA, planesA, npad, kpad, elem_kind(o.executor),
+                                      nullptr, nullptr, st);
+    if (r != cudaSuccess) return r;
+    return launch_product(o, planesA, planesP, expsA, expsP, n, n, npad, npad, kpad, 0, e, nullptr, err, scratch, st);
+  };
+  auto split_P = [&](const double* Pk) -> cudaError_t {
+    if (o.mode == DMP_FP64) return cudaSuccess;
+    return launch_split_rows(Pk, n, n, n, o.s, o.beta, expsP, planesP, npad, kpad, elem_kind(o.executor), nullptr,
+                             nullptr, st);
+  };
+
+  // host copies of the per-step update weights (kept alive until the stream syncs)
+  std::vector<PurifyState> wts(static_cast<size_t>(std::max(K, 1)));
+  for (int k = 0; k < K; ++k) {
+    std::memset(&wts[k], 0, sizeof(PurifyState));
+    const double c = cs[k];
+    if (c >= 0.5) {
+      wts[k].alpha = 0.0;
+      wts[k].b2 = (1.0 + c) / c;
+      wts[k].b3 = -1.0 / c;
+    } else {
+      wts[k].alpha = (1.0 - 2.0 * c) / (1.0 - c);
+      wts[k].b2 = (1.0 + c) / (1.0 - c);
+      wts[k].b3 = -1.0 / (1.0 - c);
+    }
+  }
+
+  DMP_CUDA(launch_sym_part(dLdP, n, n, G, st));
+  const int E = o.every;
+  for (int seg = K > 0 ? (K - 1) / E : -1; seg >= 0; --seg) {
+    const int k0 = seg * E;
+    const int k1 = std::min(k0 + E, K);
+    // ---- recompute P_k0 .. P_{k1-1} and their squares from the checkpoint
+    DMP_CUDA(cudaMemcpyAsync(segP, ckpt + static_cast<size_t>(seg) * nn, nn * sizeof(double),
+                             cudaMemcpyDeviceToDevice, st));
+    for (int k = k0; k < k1; ++k) {
+      double* Pk = segP + static_cast<size_t>(k - k0) * nn;
+      double* Xk = segX + static_cast<size_t>(k - k0) * nn;
+      EpiArgs e2{};
+      e2.kind = EPI_SYM_STORE;
+      e2.C = Xk;
+      e2.ldc = n;
+      if (o.mode == DMP_FP64) {
+        DMP_CUDA(launch_gemm_f64(Pk, n, Pk, n, n, n, n, 1, e2, nullptr, st));
+      } else {
+        DMP_CUDA(split_P(Pk));
+        DMP_CUDA(launch_product(o, planesP, planesP, expsP, expsP, n, n, npad, npad, kpad, 1, e2, nullptr, err,
+                                scratch, st));
+      }
+      if (k + 1 < k1) {
+        DMP_CUDA(cudaMemcpyAsync(&state->alpha, &wts[k].alpha, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        EpiArgs e3{};
+        e3.kind = EPI_PM_UPDATE;
+        e3.C = Pk + nn;
+        e3.ldc = n;
+        e3.P = Pk;
+        e3.ldp = n;
+        e3.X2 = Xk;
+        e3.ldx = n;
+        e3.state = state;
+        if (o.mode == DMP_FP64) {
+          DMP_CUDA(launch_gemm_f64(Pk, n, Xk, n, n, n, n, 1, e3, nullptr, st));
+        } else {
+          DMP_CUDA(launch_split_rows(Xk, n, n, n, o.s, o.beta, expsA, planesA, npad, kpad, elem_kind(o.executor),
+                                     nullptr, nullptr, st));
+          DMP_CUDA(launch_product(o, planesP, planesA, expsP, expsA, n, n, npad, npad, kpad, 1, e3, nullptr, err,
+                                  scratch, st));
+        }
+      }
+    }
+    // ---- reverse through the segment
+    for (int k = k1 - 1; k >= k0; --k) {
+      const double* Pk = segP + static_cast<size_t>(k - k0) * nn;
+      const double* Xk = segX + static_cast<size_t>(k - k0) * nn;
+      DMP_CUDA(split_P(Pk));
+      DMP_CUDA(times_P(G, Pk, Y));    // Y = G P
+      DMP_CUDA(launch_transpose(Y, n, n, n, Z, st));  // Z = Y^T = P G
+      DMP_CUDA(times_P(Y, Pk, YP));   // G P^2
+      DMP_CUDA(times_P(Z, Pk, ZP));   // P G P
+      DMP_CUDA(launch_adj_reduce(Pk, Xk, G, Z, n, part, cs[k], sc, st));
+      DMP_CUDA(launch_adj_step(G, Y, YP, ZP, Pk, Xk, n, sc, Gn, st));
+      std::swap(G, Gn);
+    }
+    int flag = 0;
+    DMP_CUDA(cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DMP_CUDA(cudaStreamSynchronize(st));
+    if (flag) return DMP_ERR_TIMEOUT;
+  }
+  // ---- through the initial guess
+  P0Adjoint h0;
+  std::memset(&h0, 0, sizeof(h0));
+  h0.n = static_cast<double>(n);
+  h0.n_occ = static_cast<double>(n_occ);
+  h0.lam = hd.lam;
+  h0.mu = hd.mu;
+  h0.h_min = hd.h_min;
+  h0.h_max = hd.h_max;
+  h0.lam_branch = hd.lam_branch;
+  h0.row_min = hd.row_min;
+  h0.row_max = hd.row_max;
+  h0.bounds_grad = (opts->flags & DMP_FLAG_BOUNDS_CONSTANT) ? 0 : 1;
+  DMP_CUDA(cudaMemcpyAsync(p0s, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+  DMP_CUDA(launch_p0_adjoint(G, H, n, n, part, p0s, dLdH, n, st));
+  DMP_CUDA(cudaStreamSynchronize(st));
+  return DMP_OK;
 }
 
 }  // extern "C"

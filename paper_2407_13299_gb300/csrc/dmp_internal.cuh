@@ -163,3 +163,27 @@ class ProfScope {
 };
 
 }  // namespace dmp
+
+namespace dmp {
+
+// ---------------------------------------------------------------- adjoint
+struct AdjScalars {
+  double alpha, b2, b3, td, tn, dLdc;
+};
+
+struct P0Adjoint {
+  double n, n_occ, lam, mu, h_min, h_max;
+  int32_t lam_branch, row_min, row_max, bounds_grad;
+  double diag_add, dhmax, dhmin;  // written on the device
+};
+
+cudaError_t launch_adj_reduce(const double* P, const double* X2, const double* G, const double* Z, int64_t n,
+                              double* part, double c, AdjScalars* sc, cudaStream_t st);
+cudaError_t launch_adj_step(const double* G, const double* Y, const double* YP, const double* ZP,
+                            const double* P, const double* X2, int64_t n, const AdjScalars* sc, double* Gn,
+                            cudaStream_t st);
+cudaError_t launch_sym_part(const double* A, int64_t ld, int64_t n, double* out, cudaStream_t st);
+cudaError_t launch_p0_adjoint(const double* G0, const double* H, int64_t ldh, int64_t n, double* part,
+                              P0Adjoint* s, double* out, int64_t ldo, cudaStream_t st);
+
+}  // namespace dmp

@@ -33,7 +33,7 @@ class DmpError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("slices", ctypes.c_int32), ("executor", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tol", ctypes.c_double), ("energy_tol", ctypes.c_double)]
+                ("flags", ctypes.c_int32), ("tol", ctypes.c_double), ("energy_tol", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -260,3 +260,64 @@ def ozaki_split(A: torch.Tensor, mode="int8", slices=7, executor="auto", stream=
                              digits.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
     _check(code, "ozaki_split")
     return exps, digits
+
+
+def backward_workspace_bytes(n: int, opts: Opts) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().dmp_backward_workspace_size(n, ctypes.byref(opts), ctypes.byref(b)), "dmp_backward_workspace_size")
+    return b.value
+
+
+def purify_backward(H: torch.Tensor, n_occ: int, tape: torch.Tensor, G: torch.Tensor, mode="int8", slices=7,
+                    executor="auto", tol=1e-10, energy_tol=0.0, max_iter=100, checkpoint_every=8,
+                    bounds_constant=False, ws=None, stream=None) -> torch.Tensor:
+    """dm_purify_backward: dL/dH (symmetric) from G = dL/dP for the purification
+    that `purify(..., tape=tape)` ran with the same options."""
+    _require_cuda(H, G)
+    n = H.shape[0]
+    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every)
+    opts.flags = 1 if bounds_constant else 0
+    H = H.contiguous()
+    G = G.contiguous()
+    out = torch.empty_like(H)
+    if ws is None:
+        ws = workspace(backward_workspace_bytes(n, opts), H.device)
+    code = lib().dm_purify_backward(H.data_ptr(), n, int(n_occ), ctypes.byref(opts), tape.data_ptr(), tape.numel(),
+                                    G.data_ptr(), out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(code, "dm_purify_backward")
+    return out
+
+
+class PurifyFunction(torch.autograd.Function):
+    """P = purify(H) with a hand-written backward (dm_purify_backward).
+
+    The forward keeps the adjoint tape (checkpoints every `checkpoint_every`
+    iterates); the backward returns the gradient for symmetric H."""
+
+    @staticmethod
+    def forward(ctx, H, n_occ, mode, slices, executor, tol, max_iter, checkpoint_every, bounds_constant):
+        H = H.contiguous()
+        n = H.shape[0]
+        opts = make_opts(mode, slices, executor, tol, 0.0, max_iter, checkpoint_every)
+        tape = torch.empty(tape_bytes(n, opts), dtype=torch.uint8, device=H.device)
+        P, info = purify(H, n_occ, mode=mode, slices=slices, executor=executor, tol=tol, max_iter=max_iter,
+                         tape=tape, checkpoint_every=checkpoint_every)
+        ctx.save_for_backward(H)
+        ctx.tape = tape
+        ctx.cfg = (n_occ, mode, slices, executor, tol, max_iter, checkpoint_every, bounds_constant)
+        ctx.info = info
+        return P
+
+    @staticmethod
+    def backward(ctx, gP):
+        (H,) = ctx.saved_tensors
+        n_occ, mode, slices, executor, tol, max_iter, every, bc = ctx.cfg
+        dH = purify_backward(H, n_occ, ctx.tape, gP.to(torch.float64), mode=mode, slices=slices, executor=executor,
+                             tol=tol, max_iter=max_iter, checkpoint_every=every, bounds_constant=bc)
+        return dH, None, None, None, None, None, None, None, None
+
+
+def purify_autograd(H, n_occ, mode="int8", slices=7, executor="auto", tol=1e-10, max_iter=100, checkpoint_every=8,
+                    bounds_constant=False):
+    """Differentiable purification: P = purify(H), backward through dm_purify_backward."""
+    return PurifyFunction.apply(H, n_occ, mode, slices, executor, tol, max_iter, checkpoint_every, bounds_constant)
