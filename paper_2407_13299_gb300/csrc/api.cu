@@ -524,22 +524,6 @@ int ozaki_split(int64_t m, int64_t k, const double* A, int64_t lda, int32_t mode
   return DMP_OK;
 }
 
-int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* opts, size_t* bytes) {
-  (void)batch;
-  (void)n;
-  (void)opts;
-  (void)bytes;
-  return DMP_ERR_UNSUPPORTED;
-}
-
-int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, const int64_t* n_occ,
-                      double* const* P, const dmp_opts* opts, dmp_info* infos, void* ws, size_t ws_bytes,
-                      void* stream) {
-  (void)batch; (void)H; (void)n; (void)n_occ; (void)P; (void)opts; (void)infos; (void)ws;
-  (void)ws_bytes; (void)stream;
-  return DMP_ERR_UNSUPPORTED;
-}
-
 int dmp_backward_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes) {
   Opts o;
   const int rc = normalize(opts, o);

@@ -1,0 +1,535 @@
+// Batched purification: many Hamiltonians of different sizes purified
+// together (dm_purify_batched).
+//
+// Every phase of an iteration is one grouped launch over all matrices -- the
+// row split, the tcgen05 product over the upper tiles of every matrix (one
+// persistent kernel with per-matrix TMA descriptors in global memory), the
+// measures and stopping rules, the split of P^2 and the product with the fused
+// update. Matrices that stopped are skipped by every kernel. Two iterations
+// (ping-pong between the caller's P and a workspace copy) form the body of a
+// CUDA graph WHILE loop whose condition the stopping-rule kernel clears once
+// every matrix has stopped, so the whole loop runs as one graph launch with no
+// host round trip. Graphs are cached per argument set.
+//
+// The autotuner picks the tile width (128 or 256 columns) by timing the P^2
+// product of the batch with both, and, when opts->slices is 0, the slice count:
+// the smallest s whose band energy on the largest matrix agrees with that of
+// s + 2 to the target (1e-8 relative, or opts->energy_tol when set). Choices are
+// cached per batch shape for the life of the process.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dmp_internal.cuh"
+
+namespace dmp {
+
+namespace {
+
+constexpr int kMeasBlk = 32;  // measure CTAs per matrix
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-matrix partial measures (same quantities and order as the single path).
+__global__ void __launch_bounds__(256)
+measure_grouped_kernel(const BatchMat* __restrict__ mats, int cur, double* __restrict__ part) {
+  const BatchMat& M = mats[blockIdx.y];
+  if (M.state->done) return;
+  const int64_t n = M.n;
+  const double* P = M.buf[cur];
+  const int64_t ldp = cur == 0 ? M.ldp : n;
+  const double* X2 = M.X2;
+  const double* H = M.H;
+  const int64_t ldh = M.ldh;
+  double u_px = 0.0, u_id = 0.0, u_ph = 0.0;
+  double d_p = 0.0, d_x = 0.0, d_px = 0.0, d_id = 0.0, d_ph = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double* pr = P + i * ldp;
+    const double* xr = X2 + i * n;
+    const double* hr = H + i * ldh;
+    if (threadIdx.x == 0) {
+      const double p = pr[i], x = xr[i], h = hr[i];
+      d_p += p;
+      d_x += x;
+      d_px += p * x;
+      d_id += (x - p) * (x - p);
+      d_ph += p * h;
+    }
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+      const double p = pr[j], x = xr[j], h = hr[j];
+      u_px += p * x;
+      u_id += (x - p) * (x - p);
+      u_ph += p * h;
+    }
+  }
+  __shared__ double red[8][8];
+  double v[8] = {d_p, d_x, d_px, u_px, d_id, u_id, d_ph, u_ph};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = warp_sum(v[q]);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[threadIdx.x >> 5][q] = v[q];
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+    part[(static_cast<int64_t>(blockIdx.y) * kMeasBlk + blockIdx.x) * 8 + threadIdx.x] = t;
+  }
+}
+
+// One thread per matrix applies the stopping rules; the block then tells the
+// graph whether any matrix still runs.
+__global__ void measure_grouped_final_kernel(const BatchMat* __restrict__ mats, int nmats,
+                                             const double* __restrict__ part, cudaGraphConditionalHandle cond,
+                                             int set_cond) {
+  __shared__ int any_active;
+  if (threadIdx.x == 0) any_active = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < nmats; b += blockDim.x) {
+    PurifyState* st = mats[b].state;
+    if (!st->done) {
+      double tot[8];
+      for (int q = 0; q < 8; ++q) {
+        double t = 0.0;
+        for (int k = 0; k < kMeasBlk; ++k) t += part[(static_cast<int64_t>(b) * kMeasBlk + k) * 8 + q];
+        tot[q] = t;
+      }
+      pm_decide(st, tot);
+    }
+    if (!st->done) atomicOr(&any_active, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && set_cond) cudaGraphSetConditional(cond, any_active ? 1u : 0u);
+}
+
+// The result of a matrix that stopped after an odd number of updates sits in
+// the workspace copy: move it to the caller's P.
+__global__ void finish_grouped_kernel(const BatchMat* __restrict__ mats) {
+  const BatchMat& M = mats[blockIdx.y];
+  if ((M.state->iter & 1) == 0) return;
+  const int64_t n = M.n;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n * n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    M.buf[0][i * M.ldp + j] = M.buf[1][e];
+  }
+}
+
+// ---------------------------------------------------------------- host side
+struct BatchLayout {
+  size_t mats, tiles, row_start, partials, err, scratch, tune_ws, total;
+  std::vector<size_t> state, rowbuf, expsP, expsX, buf1, X2, planesP, planesX;
+  std::vector<int64_t> n_pad, k_pad;
+  int ntiles;
+  size_t tune_bytes;
+};
+
+struct Carve {
+  size_t cur = 0;
+  size_t take(size_t bytes, size_t align = 256) {
+    cur = (cur + align - 1) / align * align;
+    const size_t o = cur;
+    cur += bytes;
+    return o;
+  }
+};
+
+int tiles_of(int64_t n_pad, int bn) {
+  const int tm = static_cast<int>(n_pad / 128), tn = static_cast<int>(n_pad / bn);
+  int cnt = 0;
+  for (int bj = 0; bj < tn; ++bj) cnt += std::min(tm, bn * (bj + 1) / 128);
+  return cnt;
+}
+
+BatchLayout batch_layout(int batch, const int64_t* n, int s_max, int beta) {
+  BatchLayout L;
+  Carve c;
+  const int eb = 2;  // bf16 planes (tcgen05 executor)
+  L.mats = c.take(sizeof(BatchMat) * batch, 128);
+  L.ntiles = 0;
+  for (int b = 0; b < batch; ++b) L.ntiles += tiles_of(round_up(n[b], 256), 128);  // the larger of the two counts
+  L.tiles = c.take(sizeof(int4) * std::max(L.ntiles, 1));
+  L.row_start = c.take(sizeof(int64_t) * (batch + 1));
+  L.partials = c.take(sizeof(double) * 8 * kMeasBlk * batch);
+  L.err = c.take(sizeof(int));
+  L.scratch = c.take(tc_scratch_bytes());
+  int64_t nmax = 2;
+  for (int b = 0; b < batch; ++b) {
+    const int64_t np = round_up(n[b], 256), kp = round_up(n[b], kPadK);
+    L.n_pad.push_back(np);
+    L.k_pad.push_back(kp);
+    L.state.push_back(c.take(sizeof(PurifyState)));
+    L.rowbuf.push_back(c.take(gershgorin_rowbuf_bytes(n[b])));
+    L.expsP.push_back(c.take(sizeof(int32_t) * np));
+    L.expsX.push_back(c.take(sizeof(int32_t) * np));
+    L.buf1.push_back(c.take(sizeof(double) * n[b] * n[b]));
+    L.X2.push_back(c.take(sizeof(double) * n[b] * n[b]));
+    L.planesP.push_back(c.take(static_cast<size_t>(s_max) * np * kp * eb));
+    L.planesX.push_back(c.take(static_cast<size_t>(s_max) * np * kp * eb));
+    nmax = std::max(nmax, n[b]);
+  }
+  // room for the slice-count tuner's single-matrix runs on the largest matrix
+  dmp_opts t{};
+  t.mode = beta == 8 ? DMP_OZAKI_BF16 : DMP_OZAKI_INT8;
+  t.slices = beta == 8 ? 9 : 10;
+  t.executor = DMP_EXEC_TC;
+  size_t tb = 0;
+  dmp_workspace_size(nmax, &t, &tb);
+  L.tune_bytes = tb;
+  L.tune_ws = c.take(tb);
+  L.total = c.cur;
+  return L;
+}
+
+struct TuneKey {
+  std::vector<int64_t> n;
+  int mode;
+  bool operator<(const TuneKey& o) const { return std::tie(mode, n) < std::tie(o.mode, o.n); }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tuned;  // -> (slices, bn)
+
+struct GraphEntry {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_graph_mu;
+std::map<std::string, GraphEntry> g_graphs;
+
+cudaStream_t capture_stream() {
+  static cudaStream_t s = nullptr;
+  if (s == nullptr) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  return s;
+}
+
+bool make_map(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows) {
+  return make_plane_map_ext(tm, planes, k_pad, rows_total, box_rows);
+}
+
+#define DMP_CUDA(call)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return DMP_ERR_CUDA; \
+  } while (0)
+
+inline char* at(void* base, size_t off) { return static_cast<char*>(base) + off; }
+
+}  // namespace
+}  // namespace dmp
+
+using namespace dmp;
+
+extern "C" {
+
+int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* opts, size_t* bytes) {
+  if (batch <= 0 || n == nullptr || opts == nullptr || bytes == nullptr) return DMP_ERR_INVALID_ARG;
+  for (int b = 0; b < batch; ++b)
+    if (n[b] < 2) return DMP_ERR_INVALID_ARG;
+  const int beta = opts->mode == DMP_OZAKI_BF16 ? 8 : 7;
+  const int s_max = opts->slices > 0 ? opts->slices : (beta == 8 ? 9 : 10);
+  *bytes = batch_layout(batch, n, s_max, beta).total;
+  return DMP_OK;
+}
+
+int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, const int64_t* n_occ,
+                      double* const* P, const dmp_opts* opts, dmp_info* infos, void* ws, size_t ws_bytes,
+                      void* stream) {
+  if (batch <= 0 || H == nullptr || n == nullptr || n_occ == nullptr || P == nullptr || opts == nullptr ||
+      ws == nullptr)
+    return DMP_ERR_INVALID_ARG;
+  if (opts->mode != DMP_OZAKI_INT8 && opts->mode != DMP_OZAKI_BF16) return DMP_ERR_UNSUPPORTED;
+  if (opts->executor != DMP_EXEC_AUTO && opts->executor != DMP_EXEC_TC) return DMP_ERR_UNSUPPORTED;
+  const int beta = opts->mode == DMP_OZAKI_BF16 ? 8 : 7;
+  const int smax_mode = beta == 8 ? 9 : 10;
+  if (opts->slices < 0 || opts->slices > smax_mode) return DMP_ERR_INVALID_ARG;
+  for (int b = 0; b < batch; ++b) {
+    if (H[b] == nullptr || P[b] == nullptr || n[b] < 2 || n_occ[b] <= 0 || n_occ[b] >= n[b])
+      return DMP_ERR_INVALID_ARG;
+    if (beta == 7 && static_cast<double>(smax_mode) * n[b] * 16129.0 >= 2147483648.0) return DMP_ERR_UNSUPPORTED;
+  }
+  const int s_cap = opts->slices > 0 ? opts->slices : smax_mode;
+  const BatchLayout L = batch_layout(batch, n, s_cap, beta);
+  if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int max_iter = opts->max_iter == 0 ? 100 : opts->max_iter;
+  const double tol = opts->tol == 0.0 ? 1e-10 : opts->tol;
+
+  BatchMat* dmats = reinterpret_cast<BatchMat*>(at(ws, L.mats));
+  int4* dtiles = reinterpret_cast<int4*>(at(ws, L.tiles));
+  int64_t* drow = reinterpret_cast<int64_t*>(at(ws, L.row_start));
+  double* dpart = reinterpret_cast<double*>(at(ws, L.partials));
+  int* derr = reinterpret_cast<int*>(at(ws, L.err));
+  double* scratch = reinterpret_cast<double*>(at(ws, L.scratch));
+  const int64_t nmax_idx = std::max_element(n, n + batch) - n;
+
+  // ---- autotune: slice count (accuracy) and tile width (speed), cached per shape
+  TuneKey key{std::vector<int64_t>(n, n + batch), opts->mode * 16 + opts->slices};
+  int s = opts->slices, bn = 256;
+  bool tuned = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      s = it->second.first;
+      bn = it->second.second;
+      tuned = true;
+    }
+  }
+  if (!tuned && s == 0) {
+    const double target = opts->energy_tol > 0.0 ? opts->energy_tol : 1e-8;
+    const int64_t nb = n[nmax_idx];
+    double* Pt = reinterpret_cast<double*>(at(ws, L.buf1[nmax_idx]));
+    std::vector<double> E(static_cast<size_t>(smax_mode) + 2, 0.0);
+    auto energy_at = [&](int sc, double* out) -> int {
+      dmp_opts t{};
+      t.mode = opts->mode;
+      t.slices = sc;
+      t.executor = DMP_EXEC_TC;
+      t.max_iter = max_iter;
+      t.tol = tol;
+      dmp_info inf;
+      const int r = dm_purify(H[nmax_idx], nb, nb, n_occ[nmax_idx], &t, Pt, nb, &inf, at(ws, L.tune_ws),
+                              L.tune_bytes, nullptr, 0, st);
+      if (r < 0) return r;
+      *out = inf.energy;
+      return DMP_OK;
+    };
+    s = smax_mode;
+    for (int sc = 4; sc + 2 <= smax_mode; ++sc) {
+      double e0 = 0.0, e2 = 0.0;
+      int r = energy_at(sc, &e0);
+      if (r < 0) return r;
+      r = energy_at(sc + 2, &e2);
+      if (r < 0) return r;
+      if (std::fabs(e0 - e2) <= target * std::fabs(e2)) {
+        s = sc;
+        break;
+      }
+    }
+  } else if (!tuned && s > 0) {
+    // keep the caller's s
+  }
+  if (s > s_cap) return DMP_ERR_WORKSPACE;
+
+  // ---- descriptors
+  std::vector<BatchMat> hm(batch);
+  std::vector<int64_t> hrow(batch + 1, 0);
+  for (int b = 0; b < batch; ++b) {
+    BatchMat& M = hm[b];
+    std::memset(&M, 0, sizeof(M));
+    M.n = n[b];
+    M.n_occ = n_occ[b];
+    M.ldh = n[b];
+    M.ldp = n[b];
+    M.n_pad = L.n_pad[b];
+    M.k_pad = L.k_pad[b];
+    M.s = s;
+    M.buf[0] = P[b];
+    M.buf[1] = reinterpret_cast<double*>(at(ws, L.buf1[b]));
+    M.X2 = reinterpret_cast<double*>(at(ws, L.X2[b]));
+    M.H = H[b];
+    M.planesP = at(ws, L.planesP[b]);
+    M.planesX = at(ws, L.planesX[b]);
+    M.expsP = reinterpret_cast<int32_t*>(at(ws, L.expsP[b]));
+    M.expsX = reinterpret_cast<int32_t*>(at(ws, L.expsX[b]));
+    M.state = reinterpret_cast<PurifyState*>(at(ws, L.state[b]));
+    hrow[b + 1] = hrow[b] + M.n_pad;
+  }
+  auto build_maps = [&](int tile_n) -> bool {
+    for (int b = 0; b < batch; ++b) {
+      BatchMat& M = hm[b];
+      const int64_t rows = static_cast<int64_t>(s) * M.n_pad;
+      if (!make_map(&M.tmPa, M.planesP, M.k_pad, rows, 128)) return false;
+      if (!make_map(&M.tmPb, M.planesP, M.k_pad, rows, beta == 8 ? 128 : tile_n)) return false;
+      if (!make_map(&M.tmXb, M.planesX, M.k_pad, rows, beta == 8 ? 128 : tile_n)) return false;
+    }
+    return true;
+  };
+  auto build_tiles = [&](int tile_n, std::vector<int4>& out) {
+    out.clear();
+    // column blocks outermost across all matrices (largest first), so CTAs
+    // running together work on the same matrix and share its B blocks
+    for (int b = 0; b < batch; ++b) {
+      const int tm = static_cast<int>(hm[b].n_pad / 128), tn = static_cast<int>(hm[b].n_pad / tile_n);
+      for (int bj = 0; bj < tn; ++bj)
+        for (int bi = 0; bi < std::min(tm, tile_n * (bj + 1) / 128); ++bi) out.push_back(make_int4(b, bi, bj, 0));
+    }
+  };
+  auto init_states = [&]() -> int {
+    for (int b = 0; b < batch; ++b) {
+      PurifyState init;
+      std::memset(&init, 0, sizeof(init));
+      init.tol = tol;
+      init.energy_tol = opts->energy_tol;
+      init.max_iter = max_iter;
+      init.status = DMP_NOT_CONVERGED;
+      DMP_CUDA(cudaMemcpyAsync(hm[b].state, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+      DMP_CUDA(launch_gershgorin_init(H[b], n[b], n[b], n_occ[b], reinterpret_cast<double*>(at(ws, L.rowbuf[b])),
+                                      hm[b].state, P[b], n[b], st));
+    }
+    DMP_CUDA(cudaStreamSynchronize(st));  // keeps the host copies alive until used
+    return DMP_OK;
+  };
+  const int tbeta = beta;
+  std::vector<int4> htiles;
+  DMP_CUDA(cudaMemcpyAsync(drow, hrow.data(), sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, st));
+
+  if (!tuned && beta == 7) {
+    // tile width: time the P^2 product of the batch's initial guesses with both
+    float best = 1e30f;
+    int best_bn = 256;
+    int rc = init_states();
+    if (rc != DMP_OK) return rc;
+    for (int cand : {128, 256}) {
+      if (!build_maps(cand)) return DMP_ERR_CUDA;
+      build_tiles(cand, htiles);
+      DMP_CUDA(cudaMemcpyAsync(dmats, hm.data(), sizeof(BatchMat) * batch, cudaMemcpyHostToDevice, st));
+      DMP_CUDA(cudaMemcpyAsync(dtiles, htiles.data(), sizeof(int4) * htiles.size(), cudaMemcpyHostToDevice, st));
+      DMP_CUDA(launch_split_grouped(dmats, drow, batch, hrow[batch], 0, tbeta, st));
+      cudaEvent_t e0, e1;
+      DMP_CUDA(cudaEventCreate(&e0));
+      DMP_CUDA(cudaEventCreate(&e1));
+      DMP_CUDA(cudaEventRecord(e0, st));
+      DMP_CUDA(launch_ozaki_tc_grouped(dmats, dtiles, static_cast<int>(htiles.size()), cand, tbeta, 0, 0, derr,
+                                       scratch, st));
+      DMP_CUDA(cudaEventRecord(e1, st));
+      DMP_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      DMP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ms < best) {
+        best = ms;
+        best_bn = cand;
+      }
+    }
+    bn = best_bn;
+  }
+  if (beta == 8) bn = 128;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = std::make_pair(s, bn);
+  }
+
+  // ---- the real run
+  if (!build_maps(bn)) return DMP_ERR_CUDA;
+  build_tiles(bn, htiles);
+  DMP_CUDA(cudaMemcpyAsync(dmats, hm.data(), sizeof(BatchMat) * batch, cudaMemcpyHostToDevice, st));
+  DMP_CUDA(cudaMemcpyAsync(dtiles, htiles.data(), sizeof(int4) * htiles.size(), cudaMemcpyHostToDevice, st));
+  DMP_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+  {
+    const int rc = init_states();
+    if (rc != DMP_OK) return rc;
+  }
+  const int ntiles = static_cast<int>(htiles.size());
+
+  // graph: WHILE(any matrix running) { two iterations }, cached per argument set
+  std::string gkey(reinterpret_cast<const char*>(hm.data()), sizeof(BatchMat) * batch);
+  gkey.append(reinterpret_cast<const char*>(&ws), sizeof(ws));
+  gkey.append(reinterpret_cast<const char*>(&bn), sizeof(bn));
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = g_graphs.find(gkey);
+    if (it != g_graphs.end()) exec = it->second.exec;
+  }
+  if (exec == nullptr) {
+    GraphEntry ge;
+    DMP_CUDA(cudaGraphCreate(&ge.graph, 0));
+    cudaGraphConditionalHandle cond;
+    DMP_CUDA(cudaGraphConditionalHandleCreate(&cond, ge.graph, 1, cudaGraphCondAssignDefault));
+    // cudaGraphNodeParams has no default constructor in C++: zeroed raw storage
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    DMP_CUDA(cudaGraphAddNode(&node, ge.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs = capture_stream();
+    DMP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    for (int cur = 0; cur < 2; ++cur) {
+      launch_split_grouped(dmats, drow, batch, hrow[batch], cur, tbeta, cs);
+      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, bn, tbeta, 0, cur, derr, scratch, cs);
+      launch_measure_grouped(dmats, batch, cur, dpart, cond, 1, cs);
+      launch_split_grouped(dmats, drow, batch, hrow[batch], 2, tbeta, cs);
+      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, bn, tbeta, 1, cur, derr, scratch, cs);
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+    if (ce != cudaSuccess) return DMP_ERR_CUDA;
+    DMP_CUDA(cudaGraphInstantiate(&ge.exec, ge.graph, 0));
+    exec = ge.exec;
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    g_graphs[gkey] = ge;
+  }
+  DMP_CUDA(cudaGraphLaunch(exec, st));
+  count_launch();
+  DMP_CUDA(launch_finish_grouped(dmats, batch, st));
+
+  std::vector<PurifyState> fin(batch);
+  for (int b = 0; b < batch; ++b)
+    DMP_CUDA(cudaMemcpyAsync(&fin[b], hm[b].state, sizeof(PurifyState), cudaMemcpyDeviceToHost, st));
+  int flag = 0;
+  DMP_CUDA(cudaMemcpyAsync(&flag, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaStreamSynchronize(st));
+  if (flag) return DMP_ERR_TIMEOUT;
+  int worst = DMP_OK;
+  for (int b = 0; b < batch; ++b) {
+    const PurifyState& f = fin[b];
+    if (infos != nullptr) {
+      dmp_info& I = infos[b];
+      I.status = f.status;
+      I.iters = f.iter;
+      I.slices_used = s;
+      I.executor_used = DMP_EXEC_TC;
+      I.energy = f.energy;
+      I.band_energy = 2.0 * f.energy;
+      I.idem = std::sqrt(f.idem2);
+      I.trace = f.t1;
+      I.c_last = f.c;
+      I.h_min = f.h_min;
+      I.h_max = f.h_max;
+    }
+    worst = std::max(worst, f.status);
+  }
+  for (int b = 0; b < batch; ++b)
+    if (fin[b].status < 0) return fin[b].status;  // the first member error (every report is filled)
+  return worst;
+}
+
+}  // extern "C"
+
+namespace dmp {
+
+cudaError_t launch_measure_grouped(const BatchMat* mats, int nmats, int cur, double* partials,
+                                   cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_MEASURE, st);
+  measure_grouped_kernel<<<dim3(kMeasBlk, nmats), 256, 0, st>>>(mats, cur, partials);
+  measure_grouped_final_kernel<<<1, 256, 0, st>>>(mats, nmats, partials, cond, set_cond);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_grouped(const BatchMat* mats, int nmats, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_OTHER, st);
+  finish_grouped_kernel<<<dim3(64, nmats), 256, 0, st>>>(mats);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace dmp

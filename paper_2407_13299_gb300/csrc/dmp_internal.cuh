@@ -1,6 +1,7 @@
 // Internal declarations shared by the libdmp translation units.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only; no driver library is linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -185,5 +186,121 @@ cudaError_t launch_adj_step(const double* G, const double* Y, const double* YP, 
 cudaError_t launch_sym_part(const double* A, int64_t ld, int64_t n, double* out, cudaStream_t st);
 cudaError_t launch_p0_adjoint(const double* G0, const double* H, int64_t ldh, int64_t n, double* part,
                               P0Adjoint* s, double* out, int64_t ldo, cudaStream_t st);
+
+}  // namespace dmp
+
+namespace dmp {
+
+// ---------------------------------------------------------------- batched purification
+// One descriptor per matrix of a batch, in device memory. The tcgen05 tensor
+// maps of its digit planes live here (global memory), so that one grouped
+// launch can serve tiles of every matrix.
+struct alignas(128) BatchMat {
+  CUtensorMap tmPa;   // planes of P, 128-row boxes (A operand)
+  CUtensorMap tmPb;   // planes of P, BN-row boxes (B operand of P P)
+  CUtensorMap tmXb;   // planes of X2, BN-row boxes (B operand of P X2)
+  double* buf[2];     // iterates: buf[0] is the caller's P, buf[1] a workspace copy
+  double* X2;
+  const double* H;
+  void* planesP;
+  void* planesX;
+  int32_t* expsP;
+  int32_t* expsX;
+  PurifyState* state;
+  int64_t n, n_occ, ldh, ldp, n_pad, k_pad;
+  int32_t s, pad_;
+};
+
+// 2-D TMA map over s stacked bf16 digit planes (k_pad contiguous, rows_total
+// rows), 64 x box_rows boxes with 128-byte swizzle.
+bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows);
+
+// Grouped kernels (every launch covers all matrices; finished ones are skipped).
+// `which`: 0 = buf[0], 1 = buf[1], 2 = X2.
+cudaError_t launch_split_grouped(const BatchMat* mats, const int64_t* row_start, int nmats, int64_t total_rows,
+                                 int which, int beta, cudaStream_t st);
+cudaError_t launch_measure_grouped(const BatchMat* mats, int nmats, int cur, double* partials,
+                                   cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st);
+cudaError_t launch_finish_grouped(const BatchMat* mats, int nmats, cudaStream_t st);
+// phase 0: X2 = P P from buf[cur]; phase 1: update buf[cur] -> buf[1 - cur].
+cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, int beta,
+                                    int phase, int cur, int* err, double* scratch, cudaStream_t st);
+
+}  // namespace dmp
+
+namespace dmp {
+
+// The stopping rules and the coefficient of canonical purification, applied to
+// the measures of the current iterate (diagonal/strict-upper partial sums:
+// tot = {tr P, tr X2, diag PX2, upper PX2, diag (X2-P)^2, upper (X2-P)^2,
+// diag PH, upper PH}). Sets status/done, or c and the update weights.
+__device__ __forceinline__ void pm_decide(PurifyState* st, const double* tot) {
+  const double t1 = tot[0], t2 = tot[1];
+  const double t3 = tot[2] + 2.0 * tot[3];
+  const double idem2 = tot[4] + 2.0 * tot[5];
+  const double energy = tot[6] + 2.0 * tot[7];
+  st->t1 = t1;
+  st->t2 = t2;
+  st->t3 = t3;
+  st->idem2 = idem2;
+  st->energy = energy;
+  if (!isfinite(t1) || !isfinite(t2) || !isfinite(t3) || !isfinite(idem2) || !isfinite(energy)) {
+    st->nonfinite = 1;
+    st->status = DMP_ERR_NONFINITE;
+    st->done = 1;
+    return;
+  }
+  const int k = st->iter;
+  st->band[2] = st->band[1];
+  st->band[1] = st->band[0];
+  st->band[0] = 2.0 * energy;
+  const double idem = sqrt(idem2);
+  if (idem < st->tol) {
+    st->status = DMP_OK;
+    st->done = 1;
+    return;
+  }
+  const double b0 = st->band[0], b1 = st->band[1], b2 = st->band[2];
+  if (k >= 2 && b0 > b1 && b1 > b2 && fabs(b0 - b1) < 1e-2 && fabs(b1 - b2) < 1e-2) {
+    st->status = DMP_STALLED;
+    st->done = 1;
+    return;
+  }
+  if (st->energy_tol > 0.0 && k >= 1 && fabs(b0 - b1) < st->energy_tol) {
+    st->status = DMP_OK;
+    st->done = 1;
+    return;
+  }
+  if (k >= st->max_iter) {
+    st->status = DMP_NOT_CONVERGED;
+    st->done = 1;
+    return;
+  }
+  const double td = t1 - t2;
+  if (!(td > 0.0)) {
+    st->status = DMP_C_OUT_OF_RANGE;
+    st->done = 1;
+    return;
+  }
+  const double c = (t2 - t3) / td;
+  if (!(c >= 0.0 && c <= 1.0)) {
+    st->status = DMP_C_OUT_OF_RANGE;
+    st->done = 1;
+    return;
+  }
+  st->c = c;
+  if (c >= 0.5) {
+    st->alpha = 0.0;
+    st->b2 = (1.0 + c) / c;
+    st->b3 = -1.0 / c;
+    st->branch = 1;
+  } else {
+    st->alpha = (1.0 - 2.0 * c) / (1.0 - c);
+    st->b2 = (1.0 + c) / (1.0 - c);
+    st->b3 = -1.0 / (1.0 - c);
+    st->branch = 2;
+  }
+  st->iter = k + 1;
+}
 
 }  // namespace dmp

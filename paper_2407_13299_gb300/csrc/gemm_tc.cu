@@ -32,6 +32,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
+
 #include "dmp_internal.cuh"
 
 namespace dmp {
@@ -67,6 +69,11 @@ struct TcParams {
   const int* done;
   int* err;
   unsigned long long timeout_ns;
+  // grouped mode (batched purification): tiles of many matrices in one launch
+  const BatchMat* mats;  // nullptr: the single matrix above
+  const int4* tiles;     // {matrix, bi, bj, 0}
+  int phase;             // 0: X2 = P P;  1: P' = update(P, X2, P X2)
+  int cur;               // the iterate is mats[.].buf[cur]
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -133,16 +140,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -206,6 +203,81 @@ __device__ __forceinline__ void tile_of(const TcParams& p, int idx, int& bi, int
   bi = idx;
 }
 
+// Everything one output tile needs: operands, sizes and the output step.
+struct Job {
+  const CUtensorMap* ta;
+  const CUtensorMap* tb;
+  int64_t m0, n0, rows_a, rows_b, m, n;
+  int s, KT;
+  const int32_t* ea;
+  const int32_t* eb;
+  bool skip, sym;
+  EpiArgs epi;
+};
+
+template <int BN>
+__device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, int tile) {
+  Job j;
+  if (p.mats == nullptr) {
+    int bi, bj;
+    tile_of<BN>(p, tile, bi, bj);
+    j.ta = tmA;
+    j.tb = tmB;
+    j.m0 = static_cast<int64_t>(bi) * TC_BM;
+    j.n0 = static_cast<int64_t>(bj) * BN;
+    j.rows_a = p.rows_a;
+    j.rows_b = p.rows_b;
+    j.m = p.m;
+    j.n = p.n;
+    j.s = p.s;
+    j.KT = p.KT;
+    j.ea = p.ea;
+    j.eb = p.eb;
+    j.skip = false;
+    j.sym = p.sym != 0;
+    j.epi = p.epi;
+    return j;
+  }
+  const int4 t = p.tiles[tile];
+  const BatchMat& M = p.mats[t.x];
+  j.m0 = static_cast<int64_t>(t.y) * TC_BM;
+  j.n0 = static_cast<int64_t>(t.z) * BN;
+  j.rows_a = M.n_pad;
+  j.rows_b = M.n_pad;
+  j.m = M.n;
+  j.n = M.n;
+  j.s = M.s;
+  j.KT = static_cast<int>(M.k_pad / TC_BK);
+  j.skip = M.state->done != 0;
+  j.sym = true;
+  j.ta = &M.tmPa;
+  j.ea = M.expsP;
+  j.epi.state = M.state;
+  j.epi.levels = nullptr;
+  if (p.phase == 0) {
+    j.tb = &M.tmPb;
+    j.eb = M.expsP;
+    j.epi.kind = EPI_SYM_STORE;
+    j.epi.C = M.X2;
+    j.epi.ldc = M.n;
+    j.epi.P = nullptr;
+    j.epi.X2 = nullptr;
+    j.epi.ldp = M.n;
+    j.epi.ldx = M.n;
+  } else {
+    j.tb = &M.tmXb;
+    j.eb = M.expsX;
+    j.epi.kind = EPI_PM_UPDATE;
+    j.epi.P = M.buf[p.cur];
+    j.epi.ldp = p.cur == 0 ? M.ldp : M.n;
+    j.epi.X2 = M.X2;
+    j.epi.ldx = M.n;
+    j.epi.C = M.buf[1 - p.cur];
+    j.epi.ldc = p.cur == 0 ? M.n : M.ldp;
+  }
+  return j;
+}
+
 // Persistent: one CTA per SM walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // The three roles keep their ring and buffer phases across tiles, so the next
 // tile's loads and MMAs overlap the current tile's last fold and output.
@@ -244,7 +316,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
+  if (warp == 0 && lane == 0 && p.mats == nullptr) {
     tma_prefetch(&tmA);
     tma_prefetch(&tmB);
   }
@@ -257,8 +329,6 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const int s = p.s;
-  const int KT = p.KT;
   const int CH = p.CH;
 
   if (warp == 0) {
@@ -269,25 +339,24 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       bool ok = true;
       uint32_t armed = 0;  // stages armed in the current ring pass (for the abort drain)
       for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-        int bi, bj;
-        tile_of<BN>(p, tile, bi, bj);
-        const int64_t m0 = static_cast<int64_t>(bi) * TC_BM;
-        const int64_t n0 = static_cast<int64_t>(bj) * BN;
+        const Job jb = job_of<BN>(p, &tmA, &tmB, tile);
+        if (jb.skip) continue;
+        const int s = jb.s;
         for (int L = s + 1; L >= 2 && ok; --L) {
           const int i_lo = max(1, L - s), i_hi = min(s, L - 1);
           for (int i = i_lo; i <= i_hi && ok; ++i) {
             const int j = L - i;
-            const int ya = static_cast<int>((i - 1) * p.rows_a + m0);
-            const int yb = static_cast<int>((j - 1) * p.rows_b + n0);
-            for (int kt = 0; kt < KT; ++kt) {
+            const int ya = static_cast<int>((i - 1) * jb.rows_a + jb.m0);
+            const int yb = static_cast<int>((j - 1) * jb.rows_b + jb.n0);
+            for (int kt = 0; kt < jb.KT; ++kt) {
               if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, p)) {
                 ok = false;
                 break;
               }
               const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
               mbar_arrive_expect_tx(full_bar(stage), Cfg::STAGE_BYTES);
-              tma_load_2d(sa, &tmA, full_bar(stage), kt * TC_BK, ya);
-              tma_load_2d(sa + Cfg::A_BYTES, &tmB, full_bar(stage), kt * TC_BK, yb);
+              tma_load_2d(sa, jb.ta, full_bar(stage), kt * TC_BK, ya);
+              tma_load_2d(sa + Cfg::A_BYTES, jb.tb, full_bar(stage), kt * TC_BK, yb);
               armed |= 1u << stage;
               if (++stage == Cfg::STAGES) {
                 stage = 0;
@@ -320,8 +389,11 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       bool ok = true;
       bool issued = false;
       for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+        const Job jb = job_of<BN>(p, &tmA, &tmB, tile);
+        if (jb.skip) continue;
+        const int s = jb.s;
         for (int L = s + 1; L >= 2 && ok; --L) {
-          const int nkb = npairs_of(L, s) * KT;
+          const int nkb = npairs_of(L, s) * jb.KT;
           for (int kb = 0; kb < nkb; ++kb) {
             const int kc = kb % CH;
             const bool first = kc == 0;
@@ -388,13 +460,18 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     uint32_t aph[2] = {0u, 0u};
     bool ok = true;
     for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-      int bi, bj;
-      tile_of<BN>(p, tile, bi, bj);
-      const int64_t m0 = static_cast<int64_t>(bi) * TC_BM;
-      const int64_t n0 = static_cast<int64_t>(bj) * BN;
-      const int64_t r = m0 + row;
-      const bool row_ok = r < p.m;
-      const int32_t er = row_ok ? p.ea[r] : 0;
+      int64_t m0, n0;
+      int s, KT;
+      bool skip;
+      {
+        const Job jb = job_of<BN>(p, &tmA, &tmB, tile);
+        m0 = jb.m0;
+        n0 = jb.n0;
+        s = jb.s;
+        KT = jb.KT;
+        skip = jb.skip;
+      }
+      if (skip) continue;
       for (int L = s + 1; L >= 2 && ok; --L) {
 #pragma unroll
         for (int c = 0; c < COLS; ++c) {
@@ -434,9 +511,10 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
         }
         if (!ok) break;
-        // ---- fold the exact level sum S_L
-        if (p.epi.kind == EPI_LEVELS) {
-          if (row_ok) {
+        if (p.epi.kind == EPI_LEVELS && p.mats == nullptr) {
+          // test hook: write the exact level sum itself
+          const int64_t r = m0 + row;
+          if (r < p.m) {
 #pragma unroll
             for (int c = 0; c < COLS; ++c) {
               const int64_t col = n0 + cbase + c;
@@ -449,40 +527,39 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
           continue;
         }
+        // ---- fold the exact level sum: acc = S_L 2^(-beta L) + acc (smallest level first)
         const double scale = ldexp(1.0, -p.beta * L);
         const bool first_level = (L == s + 1);
-        if (L != 2) {
-#pragma unroll
-          for (int c = 0; c < COLS; ++c) {
-            const double Sd = WIDE ? static_cast<double>(Shi[c]) * 16777216.0 + static_cast<double>(S[c])
-                                   : static_cast<double>(S[c]);
-            scr[32 * c] = first_level ? Sd * scale : fma(Sd, scale, scr[32 * c]);
-          }
-          continue;
-        }
-        // last level: finish the sum, unscale, and apply the output step
-        if (!row_ok) continue;
-        const bool upd = p.epi.kind == EPI_PM_UPDATE;
-        const double wa = upd ? p.epi.state->alpha : 0.0;
-        const double w2 = upd ? p.epi.state->b2 : 0.0;
-        const double w3 = upd ? p.epi.state->b3 : 0.0;
 #pragma unroll
         for (int c = 0; c < COLS; ++c) {
-          const int64_t col = n0 + cbase + c;
-          if (col >= p.n) continue;
-          if (p.sym && r > col) continue;  // the (col, r) element's mirror covers it
           const double Sd = WIDE ? static_cast<double>(Shi[c]) * 16777216.0 + static_cast<double>(S[c])
                                  : static_cast<double>(S[c]);
-          const double acc = first_level ? Sd * scale : fma(Sd, scale, scr[32 * c]);
-          const int32_t ec = p.eb[col];
+          scr[32 * c] = first_level ? Sd * scale : fma(Sd, scale, scr[32 * c]);
+        }
+        if (L != 2) continue;
+        // ---- last level: unscale and apply the output step
+        const Job jb = job_of<BN>(p, &tmA, &tmB, tile);
+        const int64_t r = m0 + row;
+        if (r >= jb.m) continue;
+        const int32_t er = jb.ea[r];
+        const bool upd = jb.epi.kind == EPI_PM_UPDATE;
+        const double wa = upd ? jb.epi.state->alpha : 0.0;
+        const double w2 = upd ? jb.epi.state->b2 : 0.0;
+        const double w3 = upd ? jb.epi.state->b3 : 0.0;
+#pragma unroll 4
+        for (int c = 0; c < COLS; ++c) {
+          const int64_t col = n0 + cbase + c;
+          if (col >= jb.n) break;
+          if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
+          const int32_t ec = jb.eb[col];
           double v = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                      : ldexp(acc, er + ec);
+                                                      : ldexp(scr[32 * c], er + ec);
           if (upd) {
             // P and P^2 are exactly symmetric: read them at (col, r), coalesced across the warp
-            v = wa * p.epi.P[col * p.epi.ldp + r] + w2 * p.epi.X2[col * p.epi.ldx + r] + w3 * v;
+            v = wa * jb.epi.P[col * jb.epi.ldp + r] + w2 * jb.epi.X2[col * jb.epi.ldx + r] + w3 * v;
           }
-          p.epi.C[r * p.epi.ldc + col] = v;
-          if (p.sym && r < col) p.epi.C[col * p.epi.ldc + r] = v;
+          jb.epi.C[r * jb.epi.ldc + col] = v;
+          if (jb.sym && r < col) jb.epi.C[col * jb.epi.ldc + r] = v;
         }
       }
     }
@@ -523,6 +600,14 @@ bool make_plane_map(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t 
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
+
+}  // namespace
+
+bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows) {
+  return make_plane_map(tm, planes, k_pad, rows_total, box_rows);
+}
+
+namespace {
 
 template <int BN, bool WIDE>
 cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& p, int ntiles,
@@ -566,6 +651,10 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   if (!make_plane_map(&ta, A, k_pad, static_cast<int64_t>(s) * rows_a, TC_BM)) return cudaErrorInvalidValue;
   if (!make_plane_map(&tb, B, k_pad, static_cast<int64_t>(s) * rows_b, BN)) return cudaErrorInvalidValue;
   TcParams p;
+  p.mats = nullptr;
+  p.tiles = nullptr;
+  p.phase = 0;
+  p.cur = 0;
   p.s = s;
   p.beta = beta;
   p.KT = static_cast<int>(k_pad / TC_BK);
@@ -594,6 +683,32 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   const int grid = std::min(ntiles, tc_max_ctas());
   ProfScope prof(DMP_PROF_PRODUCT, st);
   return wide ? launch_tc_impl<128, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
+}
+
+cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, int beta,
+                                    int phase, int cur, int* err, double* scratch, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.beta = beta;
+  p.CH = beta == 8 ? 4 : 16;
+  p.ntiles = ntiles;
+  p.scratch = scratch;
+  p.sym = 1;
+  p.mats = mats;
+  p.tiles = tiles;
+  p.phase = phase;
+  p.cur = cur;
+  p.err = err;
+  p.done = nullptr;
+  p.timeout_ns = 5000000000ull;
+  CUtensorMap unused;
+  std::memset(&unused, 0, sizeof(unused));
+  const int grid = std::min(ntiles, tc_max_ctas());
+  ProfScope prof(DMP_PROF_PRODUCT, st);
+  if (beta == 8) return launch_tc_impl<128, true>(unused, unused, p, grid, st);
+  if (bn == 128) return launch_tc_impl<128, false>(unused, unused, p, grid, st);
+  return launch_tc_impl<256, false>(unused, unused, p, grid, st);
 }
 
 }  // namespace dmp

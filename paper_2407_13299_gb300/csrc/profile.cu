@@ -27,6 +27,8 @@ size_t g_used = 0;
 ProfScope::ProfScope(int kind, cudaStream_t st) : st_(st), idx_(-1) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;  // not in graphs
   if (g_used == g_pool.size()) {
     Rec r;
     if (cudaEventCreate(&r.a) != cudaSuccess) return;

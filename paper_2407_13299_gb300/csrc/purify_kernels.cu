@@ -225,73 +225,7 @@ __global__ void measure_final_kernel(const double* __restrict__ part, int nblock
     tot[threadIdx.x] = t;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  const double t1 = tot[0], t2 = tot[1];
-  const double t3 = tot[2] + 2.0 * tot[3];
-  const double idem2 = tot[4] + 2.0 * tot[5];
-  const double energy = tot[6] + 2.0 * tot[7];
-  st->t1 = t1;
-  st->t2 = t2;
-  st->t3 = t3;
-  st->idem2 = idem2;
-  st->energy = energy;
-  if (!isfinite(t1) || !isfinite(t2) || !isfinite(t3) || !isfinite(idem2) || !isfinite(energy)) {
-    st->nonfinite = 1;
-    st->status = DMP_ERR_NONFINITE;
-    st->done = 1;
-    return;
-  }
-  const int k = st->iter;
-  st->band[2] = st->band[1];
-  st->band[1] = st->band[0];
-  st->band[0] = 2.0 * energy;
-  const double idem = sqrt(idem2);
-  if (idem < st->tol) {
-    st->status = DMP_OK;
-    st->done = 1;
-    return;
-  }
-  const double b0 = st->band[0], b1 = st->band[1], b2 = st->band[2];
-  if (k >= 2 && b0 > b1 && b1 > b2 && fabs(b0 - b1) < 1e-2 && fabs(b1 - b2) < 1e-2) {
-    st->status = DMP_STALLED;
-    st->done = 1;
-    return;
-  }
-  if (st->energy_tol > 0.0 && k >= 1 && fabs(b0 - b1) < st->energy_tol) {
-    st->status = DMP_OK;
-    st->done = 1;
-    return;
-  }
-  if (k >= st->max_iter) {
-    st->status = DMP_NOT_CONVERGED;
-    st->done = 1;
-    return;
-  }
-  const double td = t1 - t2;
-  if (!(td > 0.0)) {
-    st->status = DMP_C_OUT_OF_RANGE;
-    st->done = 1;
-    return;
-  }
-  const double c = (t2 - t3) / td;
-  if (!(c >= 0.0 && c <= 1.0)) {
-    st->status = DMP_C_OUT_OF_RANGE;
-    st->done = 1;
-    return;
-  }
-  st->c = c;
-  if (c >= 0.5) {
-    st->alpha = 0.0;
-    st->b2 = (1.0 + c) / c;
-    st->b3 = -1.0 / c;
-    st->branch = 1;
-  } else {
-    st->alpha = (1.0 - 2.0 * c) / (1.0 - c);
-    st->b2 = (1.0 + c) / (1.0 - c);
-    st->b3 = -1.0 / (1.0 - c);
-    st->branch = 2;
-  }
-  st->iter = k + 1;
+  if (threadIdx.x == 0) pm_decide(st, tot);
 }
 
 }  // namespace

@@ -51,13 +51,13 @@ __device__ __forceinline__ void digits_of(double a, int e_row, int s, int beta, 
   }
 }
 
+// One row r of A (m x k, leading dimension lda) into exps[r] and the s planes;
+// called by one whole CTA of kSplitThreads threads.
 template <int KIND>  // 1: int8, 2: int16, 3: bfloat16 holding the same integers
-__global__ void __launch_bounds__(kSplitThreads)
-split_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda, int s, int beta,
-                  int32_t* __restrict__ exps, void* __restrict__ planes, int64_t k_pad,
-                  int64_t plane_stride, int* flag, const int* done) {
-  if (done != nullptr && *done) return;
-  const int64_t r = blockIdx.x;
+__device__ __forceinline__ void split_one_row(const double* __restrict__ A, int64_t r, int64_t m, int64_t k,
+                                              int64_t lda, int s, int beta, int32_t* __restrict__ exps,
+                                              void* __restrict__ planes, int64_t k_pad, int64_t plane_stride,
+                                              int* flag) {
   const int tid = threadIdx.x;
   __shared__ unsigned long long red[kSplitThreads / 32];
   __shared__ int e_sh;
@@ -137,6 +137,37 @@ split_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t ld
   }
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(kSplitThreads)
+split_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda, int s, int beta,
+                  int32_t* __restrict__ exps, void* __restrict__ planes, int64_t k_pad,
+                  int64_t plane_stride, int* flag, const int* done) {
+  if (done != nullptr && *done) return;
+  split_one_row<KIND>(A, blockIdx.x, m, k, lda, s, beta, exps, planes, k_pad, plane_stride, flag);
+}
+
+// Grouped: CTA x covers row x - row_start[b] of matrix b (row_start ascending,
+// row_start[nmats] = total padded rows). Finished matrices are skipped.
+template <int KIND>
+__global__ void __launch_bounds__(kSplitThreads)
+split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restrict__ row_start, int nmats,
+                     int which, int beta) {
+  const int64_t x = blockIdx.x;
+  int lo = 0, hi = nmats - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row_start[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  const BatchMat& M = mats[lo];
+  if (M.state->done) return;
+  const int64_t r = x - row_start[lo];
+  const double* A = which == 2 ? M.X2 : M.buf[which];
+  const int64_t lda = which == 0 ? M.ldp : M.n;
+  int32_t* exps = which == 2 ? M.expsX : M.expsP;
+  void* planes = which == 2 ? M.planesX : M.planesP;
+  split_one_row<KIND>(A, r, M.n, M.n, lda, M.s, beta, exps, planes, M.k_pad, M.n_pad * M.k_pad, nullptr);
+}
+
 __global__ void transpose_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
                                  double* __restrict__ At) {
   __shared__ double tile[32][33];
@@ -182,6 +213,16 @@ cudaError_t launch_transpose(const double* A, int64_t m, int64_t n, int64_t lda,
   dim3 grid(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((m + 31) / 32));
   ProfScope prof(DMP_PROF_OTHER, st);
   transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(A, m, n, lda, At);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_grouped(const BatchMat* mats, const int64_t* row_start, int nmats, int64_t total_rows,
+                                 int which, int beta, cudaStream_t st) {
+  if (total_rows <= 0) return cudaSuccess;
+  ProfScope prof(DMP_PROF_SPLIT, st);
+  split_grouped_kernel<3><<<static_cast<unsigned>(total_rows), kSplitThreads, 0, st>>>(mats, row_start, nmats,
+                                                                                       which, beta);
   count_launch();
   return cudaGetLastError();
 }

@@ -321,3 +321,39 @@ def purify_autograd(H, n_occ, mode="int8", slices=7, executor="auto", tol=1e-10,
                     bounds_constant=False):
     """Differentiable purification: P = purify(H), backward through dm_purify_backward."""
     return PurifyFunction.apply(H, n_occ, mode, slices, executor, tol, max_iter, checkpoint_every, bounds_constant)
+
+
+def batched_workspace_bytes(ns, opts: Opts) -> int:
+    arr = (ctypes.c_int64 * len(ns))(*[int(x) for x in ns])
+    b = ctypes.c_size_t(0)
+    _check(lib().dmp_batched_workspace_size(len(ns), arr, ctypes.byref(opts), ctypes.byref(b)),
+           "dmp_batched_workspace_size")
+    return b.value
+
+
+def purify_batched(Hs, n_occs, mode="int8", slices=0, executor="tc", tol=1e-10, energy_tol=0.0, max_iter=100,
+                   Ps=None, ws=None, stream=None, raise_on_error=True):
+    """dm_purify_batched over a list of float64 CUDA tensors (each n x n,
+    contiguous). slices=0 lets the library's autotuner pick s. Returns
+    (list of P, list of info dicts, return code)."""
+    for H in Hs:
+        _require_cuda(H)
+    B = len(Hs)
+    opts = make_opts(mode, slices if slices else 7, executor, tol, energy_tol, max_iter)
+    opts.slices = int(slices)
+    ns = [int(H.shape[0]) for H in Hs]
+    Hs = [H.contiguous() for H in Hs]
+    if Ps is None:
+        Ps = [torch.empty_like(H) for H in Hs]
+    if ws is None:
+        ws = workspace(batched_workspace_bytes(ns, opts), Hs[0].device)
+    Hp = (ctypes.c_void_p * B)(*[H.data_ptr() for H in Hs])
+    Pp = (ctypes.c_void_p * B)(*[P.data_ptr() for P in Ps])
+    na = (ctypes.c_int64 * B)(*ns)
+    oa = (ctypes.c_int64 * B)(*[int(x) for x in n_occs])
+    infos = (Info * B)()
+    code = lib().dm_purify_batched(B, Hp, na, oa, Pp, ctypes.byref(opts), infos, ws.data_ptr(), ws.numel(),
+                                   _stream_ptr(stream))
+    if raise_on_error:
+        _check(code, "dm_purify_batched", allow_status=True)
+    return Ps, [infos[i].as_dict() for i in range(B)], code
