@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--fp64", default="full", choices=["full", "skip"], help="time the FP64 purification once")
     ap.add_argument("--cpu-samples", type=int, default=5, help="oracle samples for cpu_baseline (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--workload", default="purify", choices=["purify", "batch64"],
+                    help="purify: the n=8192 benchmark; batch64: the 64-matrix batched workload")
     ap.add_argument("--gen", default="device", choices=["device", "host"],
                     help="where the QR of the input generator runs (host: numpy, for profiler runs)")
     return ap.parse_args()
@@ -427,10 +429,63 @@ def run_ours(args):
     return 0
 
 
+def run_batch64(args):
+    """64 Hamiltonians, n = 32 U{4..48}, n_occ = n/4, gap 0.2: dm_purify_batched
+    (one graph launch, autotuned s and tile width) against 64 sequential
+    dm_purify calls at the same s. One JSON line; not the benchmark metric."""
+    import numpy as np
+    import torch
+
+    from paper_2407_13299_gb300 import build as _build
+    from paper_2407_13299_gb300 import dmp
+    from synth import batch_sizes, make_hamiltonian
+
+    _build.build()
+    sizes = batch_sizes()
+    hs = [make_hamiltonian(n, o, occ=(-2.0, -0.1), virt=(0.1, 2.0), seed=sd) for n, o, sd in sizes]
+    Hs = [torch.from_numpy(h.H).cuda() for h in hs]
+    occ = [o for _, o, _ in sizes]
+    opts = dmp.make_opts("int8", 7, "tc")
+    opts.slices = 0
+    ws = dmp.workspace(dmp.batched_workspace_bytes([h.n for h in hs], opts))
+    Ps = [torch.empty_like(H) for H in Hs]
+    _, infos, _ = dmp.purify_batched(Hs, occ, slices=0, Ps=Ps, ws=ws)  # tunes and builds the graph
+    s = infos[0]["slices_used"]
+    for _ in range(args.warmup):
+        dmp.purify_batched(Hs, occ, slices=0, Ps=Ps, ws=ws)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        _, infos, _ = dmp.purify_batched(Hs, occ, slices=0, Ps=Ps, ws=ws)
+    b.record()
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(b) / 1e3 / args.steps
+    wss = dmp.workspace(dmp.purify_workspace_bytes(max(h.n for h in hs), dmp.make_opts("int8", s, "tc")))
+    for H, o, P in zip(Hs, occ, Ps):
+        dmp.purify(H, o, mode="int8", slices=s, executor="tc", P=P, ws=wss)
+    torch.cuda.synchronize()
+    a.record()
+    for H, o, P in zip(Hs, occ, Ps):
+        dmp.purify(H, o, mode="int8", slices=s, executor="tc", P=P, ws=wss)
+    b.record()
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b) / 1e3
+    errs = [abs(i["energy"] - float(np.sum(h.e[:h.n_occ]))) / abs(float(np.sum(h.e[:h.n_occ])))
+            for i, h in zip(infos, hs)]
+    print(json.dumps({"workload": "batch64: 64 H, n = 32 U{4..48}, n_occ = n/4, gap 0.2, Ozaki-INT8",
+                      "slices": s, "batched_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
+                      "max_rel_energy_error": max(errs), "iters_max": max(i["iters"] for i in infos),
+                      "steps": args.steps, "warmup": args.warmup}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch64(args)
     return run_ours(args)
 
 

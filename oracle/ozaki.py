@@ -23,9 +23,12 @@ path as well:
   that the diagonal i + j = S + 1 carries.
 * level sums: S_L = sum over i + j = L of D_i^A (D_j^B)^T, exact integers,
   for L = 2 .. S + 1 (these are exactly the kept pairs).
-* recombination: C = 2^(e_r + f_c) * (S_{S+1} 2^-beta(S+1) + ... + S_2 2^-2beta),
-  summed in FP64 from the smallest level (L = S + 1) to the largest, rounding at
-  each addition; each S_L 2^-beta L is exact.
+* recombination: C = 2^(e_r + f_c) * (S_{S+1} 2^-beta(S+1) + ... + S_2 2^-2beta)
+  in FP64. Up to four consecutive levels (beta = 7) are first combined exactly
+  as one integer whose value is an exact float64; these group values are added
+  in FP64 from the smallest group to the largest, rounding at each addition.
+  For S <= 8 there are at most two groups, so C is the correctly rounded value
+  of the exact sum of the kept pairs.
 
 Parity: pinned. The tests check digit reconstruction with exact rationals,
 level sums against Python exact-integer products, the truncation bound against
@@ -129,13 +132,37 @@ def level_sums(DA: np.ndarray, DBt: np.ndarray, beta: int):
     return out
 
 
+def level_groups(s: int, beta: int):
+    """Consecutive levels combined exactly before any rounding: groups of up to
+    four for beta = 7 (four level sums below 2^31 weighted by 1, 2^7, 2^14, 2^21
+    stay below 2^53), single levels for beta = 8. Groups start from the
+    smallest level L = s + 1; each is listed largest L first."""
+    size = 4 if beta == 7 else 1
+    levels = list(range(s + 1, 1, -1))
+    return [levels[i:i + size] for i in range(0, len(levels), size)]
+
+
 def recombine(S: dict, e_row: np.ndarray, f_col: np.ndarray, s: int, beta: int) -> np.ndarray:
-    """FP64 sum of the levels, smallest first, then the power-of-two unscaling."""
+    """FP64 sum of the levels, then the power-of-two unscaling.
+
+    Each group of levels (see level_groups) is first combined exactly as the
+    integer T = sum_L S_L 2^(beta (L_a - L)), L_a the group's largest L, so that
+    its value T 2^(-beta L_a) is an exact float64; the groups are then added in
+    float64 from the smallest to the largest, rounding at each addition. With at
+    most two groups (s <= 8 for beta = 7) the result is the correctly rounded
+    value of the exact sum.
+    """
     m = e_row.shape[0]
     n = f_col.shape[0]
     C = np.zeros((m, n), dtype=np.float64)
-    for L in range(s + 1, 1, -1):
-        C = C + S[L].astype(np.float64) * (2.0 ** (-beta * L))
+    for group in level_groups(s, beta):
+        L_a = group[0]
+        T = np.zeros((m, n), dtype=np.int64)
+        for L in group:
+            T = T + (S[L].astype(np.int64) << (beta * (L_a - L)))
+        if np.max(np.abs(T), initial=0) >= 2 ** 53:
+            raise ValueError("group sum not exact in float64")
+        C = C + T.astype(np.float64) * (2.0 ** (-beta * L_a))
     return np.ldexp(C, e_row[:, None] + f_col[None, :])
 
 

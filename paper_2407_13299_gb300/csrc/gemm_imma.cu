@@ -2,11 +2,12 @@
 //
 // One CTA computes a 128 x 128 output tile. For each level L = s+1 down to 2 it
 // forms S_L = sum_{i+j=L} D_i^A (D_j^B)^T exactly with int8 x int8 -> int32
-// mma.sync (m16n8k32), then folds it into a float64 accumulator held in
-// registers: acc += S_L * 2^(-beta L). Each S_L * 2^(-beta L) is exact and the
-// additions run smallest level first, the same order as the definition, so the
-// float64 result is reproducible bit for bit. After the last level the tile is
-// unscaled by 2^(e_r + f_c) and handed to the epilogue.
+// mma.sync (m16n8k32). Up to four consecutive levels are combined exactly in
+// int64 registers, T = sum S_L 2^(7 (L_a - L)) < 2^53; at the end of each group
+// its exact value T 2^(-7 L_a) is added to a float64 sum kept in shared memory,
+// groups from the smallest to the largest -- the operation sequence of the
+// definition, so the float64 result is reproducible bit for bit. The tile is
+// then unscaled by 2^(e_r + f_c) and handed to the epilogue.
 //
 // Operands are zero-padded digit planes [s][rows_pad][k_pad] (K contiguous).
 // The K loop runs over (level, pair, 64-wide K block) and is fed by a 4-stage
@@ -23,7 +24,8 @@ constexpr int BM = 128, BN = 128, BK = 64;  // BK in int8 elements (= bytes)
 constexpr int STAGES = 4;
 constexpr int THREADS = 256;
 constexpr int TILE_BYTES = BM * BK;  // 8 KiB per operand tile
-constexpr int SMEM_BYTES = STAGES * 2 * TILE_BYTES;
+constexpr int PIPE_BYTES = STAGES * 2 * TILE_BYTES;
+constexpr int SMEM_BYTES = PIPE_BYTES + 64 * THREADS * 8;  // + float64 group sums, [element][thread]
 
 __device__ __forceinline__ uint32_t swz(int row, int chunk) {
   return static_cast<uint32_t>(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
@@ -111,7 +113,8 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_imma_kernel(const Params p) 
   const int total = KT * (s * (s + 1) / 2);
 
   int32_t acc[4][4][4];
-  double acc64[4][4][4];
+  long long accT[4][4][4];  // exact sum of the current group of levels
+  double* dsum = reinterpret_cast<double*>(smem + PIPE_BYTES);  // element e at dsum[e * THREADS + tid]
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_imma_kernel(const Params p) 
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         acc[a][b][q] = 0;
-        acc64[a][b][q] = 0.0;
+        accT[a][b][q] = 0;
       }
 
   auto load_stage = [&](int stage, const Pos& ps) {
@@ -181,9 +184,12 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_imma_kernel(const Params p) 
 #pragma unroll
         for (int ni = 0; ni < 4; ++ni) mma_s8(acc[mi][ni], af[mi], bf[ni]);
     }
-    // end of a level: fold the exact level sum into the float64 accumulator
+    // end of a level: fold the exact level sum into the group sum
     if (cp.kt == KT - 1 && cp.i == min(s, cp.L - 1)) {
-      const double scale = ldexp(1.0, -p.beta * cp.L);
+      const int gpos = (s + 1 - cp.L) & 3;
+      const bool gend = (gpos == 3) && (cp.L != 2);
+      const bool first_group = (s + 1 - cp.L) < 4;
+      const double gscale = ldexp(1.0, -7 * (cp.L + gpos));
       const int g = lane >> 2, tig = lane & 3;
 #pragma unroll
       for (int mi = 0; mi < 4; ++mi)
@@ -197,7 +203,14 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_imma_kernel(const Params p) 
               if (r < p.m && c < p.n)
                 p.epi.levels[static_cast<int64_t>(cp.L - 2) * p.m * p.n + r * p.n + c] = acc[mi][ni][q];
             } else {
-              acc64[mi][ni][q] = fma(static_cast<double>(acc[mi][ni][q]), scale, acc64[mi][ni][q]);
+              const long long T = (gpos > 0 ? accT[mi][ni][q] : 0ll) +
+                                  (static_cast<long long>(acc[mi][ni][q]) << (7 * gpos));
+              if (gend) {
+                const int e = (mi * 4 + ni) * 4 + q;
+                const double gv = static_cast<double>(T) * gscale;
+                dsum[e * THREADS + tid] = first_group ? gv : dsum[e * THREADS + tid] + gv;
+              }
+              accT[mi][ni][q] = T;
             }
             acc[mi][ni][q] = 0;
           }
@@ -221,9 +234,14 @@ __global__ void __launch_bounds__(THREADS, 1) ozaki_imma_kernel(const Params p) 
         if (p.sym && r > c) continue;
         const bool mirror = p.sym && r < c;
         if (r < p.m && c < p.n) {
+          // finish the last group (levels 2 .. L_a) and add the earlier groups
+          const int La = 2 + ((s - 1) & 3);
+          const double gv = static_cast<double>(accT[mi][ni][q]) * ldexp(1.0, -7 * La);
+          const int e = (mi * 4 + ni) * 4 + q;
+          const double acc64 = (s <= 4) ? gv : dsum[e * THREADS + tid] + gv;
           const int32_t er = p.ea[r], ec = p.eb[c];
           const double v = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                            : ldexp(acc64[mi][ni][q], er + ec);
+                                                            : ldexp(acc64, er + ec);
           epi_apply(p.epi, r, c, v, mirror);
         }
       }

@@ -149,6 +149,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Scratch accesses with an L2 evict-last policy: the fold buffers are touched
+// once per level while gigabytes of operand tiles stream through L2.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ long long ld_keep(const void* p, uint64_t pol) {
+  long long v;
+  asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_keep(void* p, long long v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+
+// x 2^e for a finite double: exponent arithmetic when the result stays normal,
+// ldexp otherwise (identical results: scaling by a power of two is exact).
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int E = static_cast<int>((b >> 52) & 0x7ff);
+  const int En = E + e;
+  if (E != 0 && E != 0x7ff && En > 0 && En < 0x7ff) return __longlong_as_double(b + (static_cast<long long>(e) << 52));
+  return ldexp(x, e);
+}
+
 // Shared-memory matrix descriptor: K-major operand tile, rows of 128 bytes,
 // 128-byte swizzle, 8-row groups 1024 bytes apart (tile base 1024-aligned).
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
@@ -452,7 +478,11 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const uint32_t taddr_row = tmem + (static_cast<uint32_t>(32 * q) << 16);
     // this thread's float64 partial sums: element c at scr[32 c] (a warp touches
     // 256 contiguous bytes per column), private to this CTA and L2-resident
-    double* scr = p.scratch + static_cast<int64_t>(blockIdx.x) * (TC_BM * BN) + e * (COLS * 32) + lane;
+    // fold buffers of this thread: the int64 group sum and the float64 sum,
+    // element c at [32 c] (a warp touches 256 contiguous bytes per column)
+    long long* scr_i = reinterpret_cast<long long*>(p.scratch) +
+                       static_cast<int64_t>(blockIdx.x) * (2 * TC_BM * BN) + e * (COLS * 32) + lane;
+    long long* scr_d = scr_i + TC_BM * BN;
 
     int32_t S[COLS];
     int32_t Shi[WIDE ? COLS : 1];
@@ -527,14 +557,59 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
           continue;
         }
-        // ---- fold the exact level sum: acc = S_L 2^(-beta L) + acc (smallest level first)
-        const double scale = ldexp(1.0, -p.beta * L);
-        const bool first_level = (L == s + 1);
+        // ---- fold the exact level sum (groups of levels, smallest first; see the header)
+        {
+          const uint64_t pol = policy_evict_last();
+          if (WIDE) {
+            // beta = 8: every level is its own group: D = S_L 2^(-8L) + D in float64
+            const double scale = ldexp(1.0, -p.beta * L);
+            const bool first_level = (L == s + 1);
 #pragma unroll
-        for (int c = 0; c < COLS; ++c) {
-          const double Sd = WIDE ? static_cast<double>(Shi[c]) * 16777216.0 + static_cast<double>(S[c])
-                                 : static_cast<double>(S[c]);
-          scr[32 * c] = first_level ? Sd * scale : fma(Sd, scale, scr[32 * c]);
+            for (int g = 0; g < COLS / 8; ++g) {
+              long long old[8];
+              if (!first_level) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) old[t] = ld_keep(scr_d + 32 * (8 * g + t), pol);
+              }
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                const int c = 8 * g + t;
+                const double Sd = static_cast<double>(Shi[c]) * 16777216.0 + static_cast<double>(S[c]);
+                const double d = first_level ? Sd * scale : fma(Sd, scale, __longlong_as_double(old[t]));
+                st_keep(scr_d + 32 * c, __double_as_longlong(d), pol);
+              }
+            }
+          } else {
+            // beta = 7: up to four consecutive levels combine exactly in int64,
+            // T = sum S_L 2^(7 (L_a - L)) < 2^53. At the end of a group (other
+            // than the last) its exact value T 2^(-7 L_a) is added to D in
+            // float64; the last group is finished by the output pass below.
+            const int gpos = (s + 1 - L) & 3;
+            const int La = L + gpos;
+            const bool gend = (gpos == 3) && (L != 2);
+            const bool first_group = (s + 1 - L) < 4;
+            const double gscale = ldexp(1.0, -7 * La);
+#pragma unroll
+            for (int g = 0; g < COLS / 8; ++g) {
+              long long told[8];
+              if (gpos > 0) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) told[t] = ld_keep(scr_i + 32 * (8 * g + t), pol);
+              }
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                const int c = 8 * g + t;
+                const long long T = (gpos > 0 ? told[t] : 0ll) + (static_cast<long long>(S[c]) << (7 * gpos));
+                if (!gend) {
+                  st_keep(scr_i + 32 * c, T, pol);
+                } else {
+                  const double gv = static_cast<double>(T) * gscale;
+                  const double d = first_group ? gv : __longlong_as_double(ld_keep(scr_d + 32 * c, pol)) + gv;
+                  st_keep(scr_d + 32 * c, __double_as_longlong(d), pol);
+                }
+              }
+            }
+          }
         }
         if (L != 2) continue;
         // ---- last level: unscale and apply the output step
@@ -552,8 +627,17 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           if (col >= jb.n) break;
           if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
           const int32_t ec = jb.eb[col];
+          double acc;
+          if (WIDE) {
+            acc = __longlong_as_double(scr_d[32 * c]);
+          } else {
+            // last group: levels 2 .. L_a, with L_a = 2 + ((s - 1) & 3); earlier groups are in D
+            const int La = 2 + ((s - 1) & 3);
+            const double gv = static_cast<double>(scr_i[32 * c]) * ldexp(1.0, -7 * La);
+            acc = (s + 1 - 2) < 4 ? gv : __longlong_as_double(scr_d[32 * c]) + gv;
+          }
           double v = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                      : ldexp(scr[32 * c], er + ec);
+                                                      : scale_pow2(acc, er + ec);
           if (upd) {
             // P and P^2 are exactly symmetric: read them at (col, r), coalesced across the warp
             v = wa * jb.epi.P[col * jb.epi.ldp + r] + w2 * jb.epi.X2[col * jb.epi.ldx + r] + w3 * v;
@@ -638,7 +722,7 @@ int tc_max_ctas() {
   return std::min(sms, kTcMaxCtas);
 }
 
-size_t tc_scratch_bytes() { return static_cast<size_t>(kTcMaxCtas) * TC_BM * 256 * sizeof(double); }
+size_t tc_scratch_bytes() { return static_cast<size_t>(kTcMaxCtas) * 2 * TC_BM * 256 * sizeof(double); }
 
 cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, const int32_t* eb, int64_t m,
                             int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int s, int beta, int sym,

@@ -218,18 +218,39 @@ def _exact_product_float(A, B):
     return [[float(v) for v in row] for row in _exact_product(A, B)]
 
 
-def test_recombination_order_smallest_level_first():
-    """The FP64 sum adds levels from L = s+1 down to 2. With a big leading level
-    and two small ones worth 0.375 and 0.25 of its ulp, adding the small ones
-    first rounds up while adding them last leaves the big level unchanged."""
-    s, beta = 3, 7
-    big = 2 ** 53 - 1  # S_2; S_2 2^-14 has ulp 2^-14
-    S = {2: np.array([[big]], dtype=np.int64),
-         3: np.array([[48]], dtype=np.int64),     # 48 2^-21 = 0.375 ulp
-         4: np.array([[4096]], dtype=np.int64)}   # 4096 2^-28 = 0.25 ulp
+def _exact_level_value(S, s, beta, r, c):
+    return sum(Fraction(int(S[L][r, c]), 2 ** (beta * L)) for L in range(2, s + 2))
+
+
+@pytest.mark.parametrize("s", [1, 3, 4, 5, 7, 8])
+def test_recombination_is_correctly_rounded_up_to_two_groups(s):
+    """With at most two exactly combined groups of levels (s <= 8, beta = 7)
+    the float64 result is the correctly rounded exact sum of the level sums."""
+    beta = 7
+    rng = np.random.default_rng(40 + s)
+    S = {L: rng.integers(-(2 ** 30), 2 ** 30, size=(6, 5), dtype=np.int64) for L in range(2, s + 2)}
+    C = oz.recombine(S, np.zeros(6, dtype=np.int64), np.zeros(5, dtype=np.int64), s, beta)
+    for r in range(6):
+        for c in range(5):
+            assert C[r, c] == float(_exact_level_value(S, s, beta, r, c))
+
+
+def test_recombination_three_groups_smallest_first():
+    """s = 10 gives three groups (levels 11..8, 7..4, 3..2), added smallest
+    first. The largest group is (2^37 - 1) 2^-21 with ulp 2^-37; the other two
+    are worth 0.375 and 0.25 of that ulp. Added first, they sum exactly to 0.625
+    ulp and round the result up by one ulp; added last, each would be rounded
+    away."""
+    s, beta = 10, 7
+    S = {L: np.zeros((1, 1), dtype=np.int64) for L in range(2, s + 2)}
+    S[2][0, 0] = 2 ** 30 - 1
+    S[3][0, 0] = 127           # group (3, 2): T = 2^37 - 1, value T 2^-21
+    S[7][0, 0] = 3 * 2 ** 9    # group (7..4): value 3 2^-40 = 0.375 ulp
+    S[8][0, 0] = 2 ** 17       # group (11..8): T = 2^38, value 2^-39 = 0.25 ulp
     C = oz.recombine(S, np.array([0]), np.array([0]), s, beta)
-    assert C[0, 0] == 2.0 ** 39
-    assert C[0, 0] != float(Fraction(big, 2 ** 14))
+    g3 = (2 ** 37 - 1) * 2.0 ** -21
+    assert C[0, 0] == g3 + 2.0 ** -37
+    assert (g3 + 3 * 2.0 ** -40) + 2.0 ** -39 == g3  # the other order would lose both
 
 
 # ----------------------------------------------------------------- planted mistakes
