@@ -621,29 +621,45 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const double wa = upd ? jb.epi.state->alpha : 0.0;
         const double w2 = upd ? jb.epi.state->b2 : 0.0;
         const double w3 = upd ? jb.epi.state->b3 : 0.0;
-#pragma unroll 4
-        for (int c = 0; c < COLS; ++c) {
-          const int64_t col = n0 + cbase + c;
-          if (col >= jb.n) break;
-          if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
-          const int32_t ec = jb.eb[col];
-          double acc;
-          if (WIDE) {
-            acc = __longlong_as_double(scr_d[32 * c]);
-          } else {
-            // last group: levels 2 .. L_a, with L_a = 2 + ((s - 1) & 3); earlier groups are in D
-            const int La = 2 + ((s - 1) & 3);
-            const double gv = static_cast<double>(scr_i[32 * c]) * ldexp(1.0, -7 * La);
-            acc = (s + 1 - 2) < 4 ? gv : __longlong_as_double(scr_d[32 * c]) + gv;
-          }
-          double v = (er == kBadExp || ec == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                      : scale_pow2(acc, er + ec);
-          if (upd) {
+        // last group (levels 2 .. L_a, L_a = 2 + ((s - 1) & 3)); earlier groups are in D
+        const double lscale = ldexp(1.0, -p.beta * (WIDE ? 2 : 2 + ((s - 1) & 3)));
+        const bool has_d = WIDE || s > 4;
+        const uint64_t pol = policy_evict_last();
+        double* Cout = jb.epi.C;
+        const int64_t ldc = jb.epi.ldc;
+        // batches of 8 columns: issue every load of the batch, then compute and store
+        for (int g = 0; g < COLS / 8; ++g) {
+          const int64_t col0 = n0 + cbase + 8 * g;
+          if (col0 >= jb.n) break;
+          long long ti[8], td[8];
+          double pv[8], xv[8];
+          int32_t ecv[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int c = 8 * g + t;
+            const int64_t col = col0 + t;
+            const bool ok = col < jb.n;
+            ti[t] = WIDE ? 0ll : ld_keep(scr_i + 32 * c, pol);
+            td[t] = has_d ? ld_keep(scr_d + 32 * c, pol) : 0ll;
+            ecv[t] = ok ? jb.eb[col] : 0;
             // P and P^2 are exactly symmetric: read them at (col, r), coalesced across the warp
-            v = wa * jb.epi.P[col * jb.epi.ldp + r] + w2 * jb.epi.X2[col * jb.epi.ldx + r] + w3 * v;
+            pv[t] = (upd && ok) ? jb.epi.P[col * jb.epi.ldp + r] : 0.0;
+            xv[t] = (upd && ok) ? jb.epi.X2[col * jb.epi.ldx + r] : 0.0;
           }
-          jb.epi.C[r * jb.epi.ldc + col] = v;
-          if (jb.sym && r < col) jb.epi.C[col * jb.epi.ldc + r] = v;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int64_t col = col0 + t;
+            if (col >= jb.n) break;
+            if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
+            const double acc = WIDE ? __longlong_as_double(td[t])
+                                    : (has_d ? __longlong_as_double(td[t]) + static_cast<double>(ti[t]) * lscale
+                                             : static_cast<double>(ti[t]) * lscale);
+            double v = (er == kBadExp || ecv[t] == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                            : scale_pow2(acc, er + ecv[t]);
+            if (upd) v = wa * pv[t] + w2 * xv[t] + w3 * v;
+            Cout[r * ldc + col] = v;
+            if (jb.sym && r < col) Cout[col * ldc + r] = v;
+          }
         }
       }
     }
