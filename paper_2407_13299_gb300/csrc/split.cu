@@ -5,14 +5,17 @@
 // beta-bit truncated base-2^beta expansion of |x| with the sign of x:
 //   d_i = sign(x) * (floor(|x| 2^(beta i)) mod 2^beta),   |d_i| <= 2^beta - 1.
 // They are read straight off the FP64 significand: with A_rj = m 2^(E-1075)
-// (m the 53-bit significand, E the biased exponent), floor(|x| 2^(beta s)) is
-// m shifted by E - 1075 - e_r + beta s, and digit i is a beta-bit field of it.
-// No floating-point rounding is involved, so the digits are exact.
+// (m the 53-bit significand, E the biased exponent), U = floor(|x| 2^96) is m
+// shifted by E - 1075 - e_r + 96, and digit i is the beta-bit field of U that
+// starts beta i bits below its top (beta s <= 72 < 96). No floating-point
+// rounding is involved, so the digits are exact.
 //
-// One CTA per row: a max-reduction pass over the row, then a pass that emits
-// eight consecutive elements per thread into every plane with one vector store
-// per plane (8 bytes for int8, 16 bytes for 16-bit digits). The row is read
-// twice; the second read is served from L2.
+// One CTA per row. Each thread loads pairs of adjacent entries (16-byte loads,
+// 512 contiguous bytes per warp) and keeps up to 8192 entries of the row in
+// registers, so the row is read from memory once: a max-reduction, then the
+// digits of the same registers go to every plane (4-byte stores of two bf16 or
+// 2-byte stores of two int8 digits per plane). Longer rows take further sweeps
+// that read the rest of the row again.
 
 #include <cuda_bf16.h>
 
@@ -23,135 +26,199 @@ namespace dmp {
 namespace {
 
 constexpr int kSplitThreads = 256;
+constexpr int kPairs = 16;                                          // entry pairs a thread holds
+constexpr int64_t kSweep = 2 * static_cast<int64_t>(kPairs) * kSplitThreads;  // 8192 entries
 
-__device__ __forceinline__ void digits_of(double a, int e_row, int s, int beta, int32_t* d) {
+// U = floor(|a| 2^(96 - e_row)) as w0 (bits 64..95), w1 (32..63), w2 (0..31).
+// |a| < 2^e_row for every finite entry, so U < 2^96; a row holding NaN/Inf has
+// e_row = 0 and its digits are never used (the epilogue writes NaN).
+__device__ __forceinline__ void fix96(double a, int e_row, uint32_t& w0, uint32_t& w1, uint32_t& w2,
+                                      bool& neg) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(a));
-  const bool neg = (bits >> 63) != 0;
+  neg = (bits >> 63) != 0;
   const int E = static_cast<int>((bits >> 52) & 0x7ff);
   const unsigned long long frac = bits & ((1ull << 52) - 1);
   const unsigned long long mant = (E == 0) ? frac : (frac | (1ull << 52));
-  const int ex = (E == 0) ? 1 : E;
-  // |A_rj| 2^(beta s - e_r) = mant 2^shift, below 2^(beta s) <= 2^72
-  const int shift = ex - 1075 - e_row + beta * s;
-  unsigned __int128 T = 0;
-  if (mant != 0) {
-    if (shift >= 0) {
-      T = static_cast<unsigned __int128>(mant) << shift;
-    } else if (shift > -64) {
-      T = static_cast<unsigned __int128>(mant >> (-shift));
-    }
+  const int t = ((E == 0) ? 1 : E) - 1075 - e_row + 96;
+  unsigned long long hi = 0, lo = 0;  // U = hi 2^64 + lo
+  if (t >= 64) {
+    hi = t < 128 ? mant << (t - 64) : 0ull;
+  } else if (t > 0) {
+    hi = mant >> (64 - t);
+    lo = mant << t;
+  } else if (t > -64) {
+    lo = mant >> (-t);
   }
-  const unsigned long long mask = (1ull << beta) - 1;
-#pragma unroll
-  for (int i = 0; i < kMaxSlices; ++i) {
-    if (i < s) {
-      const int v = static_cast<int>(static_cast<unsigned long long>(T >> (beta * (s - 1 - i))) & mask);
-      d[i] = neg ? -v : v;
+  w0 = static_cast<uint32_t>(hi);
+  w1 = static_cast<uint32_t>(lo >> 32);
+  w2 = static_cast<uint32_t>(lo);
+}
+
+// Bits [P, P + BETA) of U (P a compile-time bit position).
+template <int P, int BETA>
+__device__ __forceinline__ uint32_t field(uint32_t w0, uint32_t w1, uint32_t w2) {
+  constexpr uint32_t mask = (1u << BETA) - 1u;
+  if constexpr (P >= 64) {
+    return (w0 >> (P - 64)) & mask;
+  } else if constexpr (P >= 32) {
+    return __funnelshift_r(w1, w0, P - 32) & mask;
+  } else {
+    return __funnelshift_r(w2, w1, P) & mask;
+  }
+}
+
+// bfloat16 bits of sign * v for 0 <= v <= 255, in the upper half of a float:
+// g = 1.5 2^23 + v is exact, and sg g - sg 1.5 2^23 is exactly +v, -v or +0
+// (an exact zero sum rounds to +0), so the float holds sign * v exactly, and
+// sign * v has at most 8 significant bits, so its float bits end in 16 zeros.
+__device__ __forceinline__ uint32_t digit_float_bits(uint32_t v, float sg) {
+  const float g = __uint_as_float(0x4B400000u | v);
+  return __float_as_uint(fmaf(sg, g, -sg * 12582912.0f));
+}
+
+template <int I, int KIND, int BETA>
+__device__ __forceinline__ void store_digit_pair(uint32_t a0, uint32_t a1, uint32_t a2, bool na, uint32_t b0,
+                                                 uint32_t b1, uint32_t b2, bool nb, void* planes, int64_t off) {
+  constexpr int P = 96 - BETA * (I + 1);
+  const uint32_t va = field<P, BETA>(a0, a1, a2);
+  const uint32_t vb = field<P, BETA>(b0, b1, b2);
+  if constexpr (KIND == 1) {
+    const uint32_t da = na ? (0u - va) : va, db = nb ? (0u - vb) : vb;
+    static_cast<uint16_t*>(planes)[off] = static_cast<uint16_t>((da & 0xffu) | ((db & 0xffu) << 8));
+  } else {
+    const uint32_t fa = digit_float_bits(va, na ? -1.0f : 1.0f);
+    const uint32_t fb = digit_float_bits(vb, nb ? -1.0f : 1.0f);
+    static_cast<uint32_t*>(planes)[off] = __byte_perm(fa, fb, 0x7632);  // high halves: (fb.hi << 16) | fa.hi
+  }
+}
+
+template <int I, int KIND, int BETA>
+__device__ __forceinline__ void store_digits(int s, uint32_t a0, uint32_t a1, uint32_t a2, bool na, uint32_t b0,
+                                             uint32_t b1, uint32_t b2, bool nb, char* base, int64_t pair_off,
+                                             int64_t plane_bytes) {
+  if constexpr (I < kMaxSlices) {
+    if (I < s) {
+      store_digit_pair<I, KIND, BETA>(a0, a1, a2, na, b0, b1, b2, nb, base + I * plane_bytes, pair_off);
+      store_digits<I + 1, KIND, BETA>(s, a0, a1, a2, na, b0, b1, b2, nb, base, pair_off, plane_bytes);
     }
   }
 }
 
-// One row r of A (m x k, leading dimension lda) into exps[r] and the s planes;
-// called by one whole CTA of kSplitThreads threads.
-template <int KIND>  // 1: int8, 2: int16, 3: bfloat16 holding the same integers
+// frexp exponent of a nonnegative finite double from its bits (0 for zero):
+// a normal value 1.f 2^(E-1023) is 0.1f 2^(E-1022); a subnormal frac 2^-1074
+// with frac of b bits lies in [2^(b-1075), 2^(b-1074)).
+__device__ __forceinline__ int exponent_of_bits(unsigned long long v) {
+  if (v == 0) return 0;
+  const int E = static_cast<int>(v >> 52);
+  if (E != 0) return E - 1022;
+  return (64 - __clzll(static_cast<long long>(v))) - 1074;
+}
+
+// Entries j, j + 1 of the row (zero past k or for a padding row).
+__device__ __forceinline__ double2 load_pair(const double* __restrict__ row, int64_t j, int64_t k, bool live,
+                                             bool vec) {
+  if (live && vec && j + 1 < k) return *reinterpret_cast<const double2*>(row + j);
+  double2 v;
+  v.x = (live && j < k) ? row[j] : 0.0;
+  v.y = (live && j + 1 < k) ? row[j + 1] : 0.0;
+  return v;
+}
+
+__device__ __forceinline__ void max_bits(double a, unsigned long long& mx, bool& bad) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a)) & 0x7fffffffffffffffull;
+  bad |= (b >> 52) == 0x7ff;
+  mx = b > mx ? b : mx;  // bit patterns of nonnegative doubles order like their values
+}
+
+// One row r of A (m x k, leading dimension lda) into exps[r] and the s planes
+// (row length k_pad, plane_stride elements apart); one whole CTA per row.
+template <int KIND, int BETA>  // KIND 1: int8 digits, 3: bfloat16 holding the same integers
 __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int64_t r, int64_t m, int64_t k,
-                                              int64_t lda, int s, int beta, int32_t* __restrict__ exps,
+                                              int64_t lda, int s, int32_t* __restrict__ exps,
                                               void* __restrict__ planes, int64_t k_pad, int64_t plane_stride,
                                               int* flag) {
   const int tid = threadIdx.x;
   __shared__ unsigned long long red[kSplitThreads / 32];
-  __shared__ int e_sh;
+  __shared__ int red_bad[kSplitThreads / 32];
+  const bool live = r < m;
+  const double* row = A + (live ? r * lda : 0);
+  const bool vec = (reinterpret_cast<uintptr_t>(row) & 15) == 0;
 
+  double2 v[kPairs];
+#pragma unroll
+  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, 2 * (tid + static_cast<int64_t>(kSplitThreads) * q), k, live, vec);
   unsigned long long mx = 0;
   bool bad = false;
-  if (r < m) {
-    const double* row = A + r * lda;
-    for (int64_t j = tid; j < k; j += kSplitThreads) {
-      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(row[j])) & 0x7fffffffffffffffull;
-      bad |= (b >> 52) == 0x7ff;
-      mx = b > mx ? b : mx;  // bit patterns of nonnegative doubles order like their values
-    }
+#pragma unroll
+  for (int q = 0; q < kPairs; ++q) {
+    max_bits(v[q].x, mx, bad);
+    max_bits(v[q].y, mx, bad);
+  }
+  if (live) {
+    for (int64_t j = kSweep + tid; j < k; j += kSplitThreads) max_bits(row[j], mx, bad);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
-    mx = v > mx ? v : mx;
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = u > mx ? u : mx;
   }
-  if ((tid & 31) == 0) red[tid >> 5] = mx;
-  if (bad && flag != nullptr) atomicExch(flag, 1);
-  __shared__ int bad_sh;
-  if (tid == 0) bad_sh = 0;
+  bad = __any_sync(0xffffffffu, bad);
+  if ((tid & 31) == 0) {
+    red[tid >> 5] = mx;
+    red_bad[tid >> 5] = bad ? 1 : 0;
+  }
   __syncthreads();
-  if (bad) atomicExch(&bad_sh, 1);
-  __syncthreads();
+  mx = 0;
+  int any_bad = 0;
+#pragma unroll
+  for (int w = 0; w < kSplitThreads / 32; ++w) {
+    mx = red[w] > mx ? red[w] : mx;
+    any_bad |= red_bad[w];
+  }
+  const int e_row = any_bad ? 0 : exponent_of_bits(mx);
   if (tid == 0) {
-    unsigned long long v = 0;
-    for (int w = 0; w < kSplitThreads / 32; ++w) v = red[w] > v ? red[w] : v;
-    int e = 0;
-    if (v != 0 && !bad_sh) frexp(__longlong_as_double(static_cast<long long>(v)), &e);
-    e_sh = e;
     // a row holding NaN/Inf is marked; the product epilogue then writes NaN
-    exps[r] = bad_sh ? kBadExp : e;
+    exps[r] = any_bad ? kBadExp : e_row;
+    if (any_bad && flag != nullptr) atomicExch(flag, 1);
   }
-  __syncthreads();
-  const int e_row = e_sh;
 
-  const double* row = A + r * lda;
-  for (int64_t j0 = static_cast<int64_t>(tid) * 8; j0 < k_pad; j0 += kSplitThreads * 8) {
-    uint32_t pk[kMaxSlices][4];
+  constexpr int kElemBytes = KIND == 1 ? 1 : 2;
+  char* base = static_cast<char*>(planes) + r * k_pad * kElemBytes;
+  const int64_t plane_bytes = plane_stride * kElemBytes;
+  for (int64_t c0 = 0;;) {
 #pragma unroll
-    for (int i = 0; i < kMaxSlices; ++i) pk[i][0] = pk[i][1] = pk[i][2] = pk[i][3] = 0u;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int64_t j = j0 + q;
-      const double a = (r < m && j < k) ? row[j] : 0.0;
-      int32_t d[kMaxSlices];
-      digits_of(a, e_row, s, beta, d);
-#pragma unroll
-      for (int i = 0; i < kMaxSlices; ++i) {
-        if (i < s) {
-          if (KIND == 1) {
-            pk[i][q >> 2] |= (static_cast<uint32_t>(d[i]) & 0xffu) << (8 * (q & 3));
-          } else if (KIND == 2) {
-            pk[i][q >> 1] |= (static_cast<uint32_t>(d[i]) & 0xffffu) << (16 * (q & 1));
-          } else {
-            const __nv_bfloat16 h = __float2bfloat16_rn(static_cast<float>(d[i]));  // exact: |d| <= 255
-            const uint32_t hb = static_cast<uint32_t>(__bfloat16_as_ushort(h));
-            pk[i][q >> 1] |= hb << (16 * (q & 1));
-          }
-        }
+    for (int q = 0; q < kPairs; ++q) {
+      const int64_t j = c0 + 2 * (tid + static_cast<int64_t>(kSplitThreads) * q);
+      if (j < k_pad) {
+        uint32_t a0, a1, a2, b0, b1, b2;
+        bool na, nb;
+        fix96(v[q].x, e_row, a0, a1, a2, na);
+        fix96(v[q].y, e_row, b0, b1, b2, nb);
+        store_digits<0, KIND, BETA>(s, a0, a1, a2, na, b0, b1, b2, nb, base, j >> 1, plane_bytes);
       }
     }
+    c0 += kSweep;
+    if (c0 >= k_pad) break;
 #pragma unroll
-    for (int i = 0; i < kMaxSlices; ++i) {
-      if (i < s) {
-        if (KIND == 1) {
-          int8_t* dst = static_cast<int8_t*>(planes) + i * plane_stride + r * k_pad + j0;
-          *reinterpret_cast<uint2*>(dst) = make_uint2(pk[i][0], pk[i][1]);
-        } else {
-          int16_t* dst = static_cast<int16_t*>(planes) + i * plane_stride + r * k_pad + j0;
-          *reinterpret_cast<uint4*>(dst) = make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
-        }
-      }
-    }
+    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, c0 + 2 * (tid + static_cast<int64_t>(kSplitThreads) * q), k, live, vec);
   }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(kSplitThreads)
-split_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda, int s, int beta,
+template <int KIND, int BETA>
+__global__ void __launch_bounds__(kSplitThreads, 2)
+split_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda, int s,
                   int32_t* __restrict__ exps, void* __restrict__ planes, int64_t k_pad,
                   int64_t plane_stride, int* flag, const int* done) {
   if (done != nullptr && *done) return;
-  split_one_row<KIND>(A, blockIdx.x, m, k, lda, s, beta, exps, planes, k_pad, plane_stride, flag);
+  split_one_row<KIND, BETA>(A, blockIdx.x, m, k, lda, s, exps, planes, k_pad, plane_stride, flag);
 }
 
 // Grouped: CTA x covers row x - row_start[b] of matrix b (row_start ascending,
 // row_start[nmats] = total padded rows). Finished matrices are skipped.
-template <int KIND>
-__global__ void __launch_bounds__(kSplitThreads)
+template <int BETA>
+__global__ void __launch_bounds__(kSplitThreads, 2)
 split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restrict__ row_start, int nmats,
-                     int which, int beta) {
+                     int which) {
   const int64_t x = blockIdx.x;
   int lo = 0, hi = nmats - 1;
   while (lo < hi) {
@@ -165,7 +232,7 @@ split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restric
   const int64_t lda = which == 0 ? M.ldp : M.n;
   int32_t* exps = which == 2 ? M.expsX : M.expsP;
   void* planes = which == 2 ? M.planesX : M.planesP;
-  split_one_row<KIND>(A, r, M.n, M.n, lda, M.s, beta, exps, planes, M.k_pad, M.n_pad * M.k_pad, nullptr);
+  split_one_row<3, BETA>(A, r, M.n, M.n, lda, M.s, exps, planes, M.k_pad, M.n_pad * M.k_pad, nullptr);
 }
 
 __global__ void transpose_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
@@ -193,15 +260,17 @@ cudaError_t launch_split_rows(const double* A, int64_t m, int64_t k, int64_t lda
   const int64_t plane_stride = m_pad * k_pad;
   dim3 grid(static_cast<unsigned>(m_pad));
   ProfScope prof(DMP_PROF_SPLIT, st);
-  if (elem_kind == 1) {
-    split_rows_kernel<1><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, beta, exps, planes, k_pad,
-                                                         plane_stride, flag, done);
-  } else if (elem_kind == 2) {
-    split_rows_kernel<2><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, beta, exps, planes, k_pad,
-                                                         plane_stride, flag, done);
+  if (elem_kind == 1 && beta == 7) {
+    split_rows_kernel<1, 7><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
+                                                            flag, done);
+  } else if (elem_kind == 3 && beta == 7) {
+    split_rows_kernel<3, 7><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
+                                                            flag, done);
+  } else if (elem_kind == 3 && beta == 8) {
+    split_rows_kernel<3, 8><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
+                                                            flag, done);
   } else {
-    split_rows_kernel<3><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, beta, exps, planes, k_pad,
-                                                         plane_stride, flag, done);
+    return cudaErrorInvalidValue;
   }
   count_launch();
   return cudaGetLastError();
@@ -221,8 +290,15 @@ cudaError_t launch_split_grouped(const BatchMat* mats, const int64_t* row_start,
                                  int which, int beta, cudaStream_t st) {
   if (total_rows <= 0) return cudaSuccess;
   ProfScope prof(DMP_PROF_SPLIT, st);
-  split_grouped_kernel<3><<<static_cast<unsigned>(total_rows), kSplitThreads, 0, st>>>(mats, row_start, nmats,
-                                                                                       which, beta);
+  if (beta == 7) {
+    split_grouped_kernel<7><<<static_cast<unsigned>(total_rows), kSplitThreads, 0, st>>>(mats, row_start, nmats,
+                                                                                         which);
+  } else if (beta == 8) {
+    split_grouped_kernel<8><<<static_cast<unsigned>(total_rows), kSplitThreads, 0, st>>>(mats, row_start, nmats,
+                                                                                         which);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   count_launch();
   return cudaGetLastError();
 }
