@@ -27,31 +27,33 @@ namespace {
 
 constexpr int kSplitThreads = 256;
 constexpr int kPairs = 16;                                          // entry pairs a thread holds
-constexpr int64_t kSweep = 2 * static_cast<int64_t>(kPairs) * kSplitThreads;  // 8192 entries
+constexpr int kSweep = 2 * kPairs * kSplitThreads;  // 8192 entries
+constexpr int64_t kMaxRow = (int64_t{1} << 31) - 1 - kSweep;     // in-row offsets stay below 2^31
 
 // U = floor(|a| 2^(96 - e_row)) as w0 (bits 64..95), w1 (32..63), w2 (0..31).
 // |a| < 2^e_row for every finite entry, so U < 2^96; a row holding NaN/Inf has
-// e_row = 0 and its digits are never used (the epilogue writes NaN).
-__device__ __forceinline__ void fix96(double a, int e_row, uint32_t& w0, uint32_t& w1, uint32_t& w2,
-                                      bool& neg) {
-  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(a));
-  neg = (bits >> 63) != 0;
-  const int E = static_cast<int>((bits >> 52) & 0x7ff);
-  const unsigned long long frac = bits & ((1ull << 52) - 1);
-  const unsigned long long mant = (E == 0) ? frac : (frac | (1ull << 52));
-  const int t = ((E == 0) ? 1 : E) - 1075 - e_row + 96;
-  unsigned long long hi = 0, lo = 0;  // U = hi 2^64 + lo
-  if (t >= 64) {
-    hi = t < 128 ? mant << (t - 64) : 0ull;
-  } else if (t > 0) {
-    hi = mant >> (64 - t);
-    lo = mant << t;
-  } else if (t > -64) {
-    lo = mant >> (-t);
-  }
-  w0 = static_cast<uint32_t>(hi);
-  w1 = static_cast<uint32_t>(lo >> 32);
-  w2 = static_cast<uint32_t>(lo);
+// e_row = 0 and its digits are never used (the epilogue writes NaN). With
+// m = mh 2^32 + ml the significand, U = m 2^t, t = E - 1075 - e_row + 96: word
+// i of U is the funnel shift by t mod 32 of words i - floor(t/32) - 1 and
+// i - floor(t/32) of m. Only 32-bit integer operations are used (64-bit integer
+// arithmetic is slow on this GPU).
+__device__ __forceinline__ void fix96(double a, int c_row, uint32_t& w0, uint32_t& w1, uint32_t& w2, bool& neg) {
+  const uint32_t hi = static_cast<uint32_t>(__double2hiint(a));
+  const uint32_t lo = static_cast<uint32_t>(__double2loint(a));
+  neg = (hi >> 31) != 0;
+  const int E = static_cast<int>((hi >> 20) & 0x7ffu);
+  const uint32_t mh = (hi & 0xfffffu) | (E != 0 ? 0x100000u : 0u);
+  const int t = (E == 0 ? 1 : E) - c_row;  // c_row = 1075 + e_row - 96
+  const int z = -(t >> 5);                 // word i of U reads words i + z - 1, i + z of m
+  const uint32_t bs = static_cast<uint32_t>(t) & 31u;
+  // word z + d of m for d = -1 .. 2 (m has words 0 = lo and 1 = mh)
+  const uint32_t m_m1 = (z == 1) ? lo : ((z == 2) ? mh : 0u);
+  const uint32_t m_0 = (z == 0) ? lo : ((z == 1) ? mh : 0u);
+  const uint32_t m_1 = (z == -1) ? lo : ((z == 0) ? mh : 0u);
+  const uint32_t m_2 = (z == -2) ? lo : ((z == -1) ? mh : 0u);
+  w2 = __funnelshift_l(m_m1, m_0, bs);
+  w1 = __funnelshift_l(m_0, m_1, bs);
+  w0 = __funnelshift_l(m_1, m_2, bs);
 }
 
 // Bits [P, P + BETA) of U (P a compile-time bit position).
@@ -78,7 +80,7 @@ __device__ __forceinline__ uint32_t digit_float_bits(uint32_t v, float sg) {
 
 template <int I, int KIND, int BETA>
 __device__ __forceinline__ void store_digit_pair(uint32_t a0, uint32_t a1, uint32_t a2, bool na, uint32_t b0,
-                                                 uint32_t b1, uint32_t b2, bool nb, void* planes, int64_t off) {
+                                                 uint32_t b1, uint32_t b2, bool nb, void* planes, int off) {
   constexpr int P = 96 - BETA * (I + 1);
   const uint32_t va = field<P, BETA>(a0, a1, a2);
   const uint32_t vb = field<P, BETA>(b0, b1, b2);
@@ -94,7 +96,7 @@ __device__ __forceinline__ void store_digit_pair(uint32_t a0, uint32_t a1, uint3
 
 template <int I, int KIND, int BETA>
 __device__ __forceinline__ void store_digits(int s, uint32_t a0, uint32_t a1, uint32_t a2, bool na, uint32_t b0,
-                                             uint32_t b1, uint32_t b2, bool nb, char* base, int64_t pair_off,
+                                             uint32_t b1, uint32_t b2, bool nb, char* base, int pair_off,
                                              int64_t plane_bytes) {
   if constexpr (I < kMaxSlices) {
     if (I < s) {
@@ -104,19 +106,24 @@ __device__ __forceinline__ void store_digits(int s, uint32_t a0, uint32_t a1, ui
   }
 }
 
-// frexp exponent of a nonnegative finite double from its bits (0 for zero):
-// a normal value 1.f 2^(E-1023) is 0.1f 2^(E-1022); a subnormal frac 2^-1074
-// with frac of b bits lies in [2^(b-1075), 2^(b-1074)).
-__device__ __forceinline__ int exponent_of_bits(unsigned long long v) {
-  if (v == 0) return 0;
-  const int E = static_cast<int>(v >> 52);
-  if (E != 0) return E - 1022;
-  return (64 - __clzll(static_cast<long long>(v))) - 1074;
+// frexp exponent of the row maximum from the maxima of the high words (sign
+// cleared) and of the low words of its entries (0 for a zero row): a normal
+// value 1.f 2^(E-1023) is 0.1f 2^(E-1022); a subnormal frac 2^-1074 with frac of
+// b bits lies in [2^(b-1075), 2^(b-1074)). The largest entry has the largest
+// high word; if every high word is zero, the largest low word is the largest
+// subnormal.
+__device__ __forceinline__ int row_exponent(uint32_t mxh, uint32_t mxl) {
+  if (mxh != 0) {
+    const int E = static_cast<int>(mxh >> 20);
+    if (E != 0) return E - 1022;
+    return (64 - __clz(static_cast<int>(mxh))) - 1074;
+  }
+  if (mxl != 0) return (32 - __clz(static_cast<int>(mxl))) - 1074;
+  return 0;
 }
 
 // Entries j, j + 1 of the row (zero past k or for a padding row).
-__device__ __forceinline__ double2 load_pair(const double* __restrict__ row, int64_t j, int64_t k, bool live,
-                                             bool vec) {
+__device__ __forceinline__ double2 load_pair(const double* __restrict__ row, int j, int k, bool live, bool vec) {
   if (live && vec && j + 1 < k) return *reinterpret_cast<const double2*>(row + j);
   double2 v;
   v.x = (live && j < k) ? row[j] : 0.0;
@@ -124,21 +131,23 @@ __device__ __forceinline__ double2 load_pair(const double* __restrict__ row, int
   return v;
 }
 
-__device__ __forceinline__ void max_bits(double a, unsigned long long& mx, bool& bad) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(a)) & 0x7fffffffffffffffull;
-  bad |= (b >> 52) == 0x7ff;
-  mx = b > mx ? b : mx;  // bit patterns of nonnegative doubles order like their values
+__device__ __forceinline__ void max_bits(double a, uint32_t& mxh, uint32_t& mxl, bool& bad) {
+  const uint32_t h = static_cast<uint32_t>(__double2hiint(a)) & 0x7fffffffu;
+  bad |= h >= 0x7ff00000u;
+  mxh = max(mxh, h);
+  mxl = max(mxl, static_cast<uint32_t>(__double2loint(a)));
 }
 
 // One row r of A (m x k, leading dimension lda) into exps[r] and the s planes
 // (row length k_pad, plane_stride elements apart); one whole CTA per row.
+// Offsets within a row are 32-bit (k_pad < 2^31, checked by the launcher).
 template <int KIND, int BETA>  // KIND 1: int8 digits, 3: bfloat16 holding the same integers
-__device__ __forceinline__ void split_one_row(const double* __restrict__ A, int64_t r, int64_t m, int64_t k,
+__device__ __forceinline__ void split_one_row(const double* __restrict__ A, int64_t r, int64_t m, int k,
                                               int64_t lda, int s, int32_t* __restrict__ exps,
-                                              void* __restrict__ planes, int64_t k_pad, int64_t plane_stride,
+                                              void* __restrict__ planes, int k_pad, int64_t plane_stride,
                                               int* flag) {
   const int tid = threadIdx.x;
-  __shared__ unsigned long long red[kSplitThreads / 32];
+  __shared__ uint32_t red_h[kSplitThreads / 32], red_l[kSplitThreads / 32];
   __shared__ int red_bad[kSplitThreads / 32];
   const bool live = r < m;
   const double* row = A + (live ? r * lda : 0);
@@ -146,61 +155,63 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
 
   double2 v[kPairs];
 #pragma unroll
-  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, 2 * (tid + static_cast<int64_t>(kSplitThreads) * q), k, live, vec);
-  unsigned long long mx = 0;
+  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, 2 * (tid + kSplitThreads * q), k, live, vec);
+  uint32_t mxh = 0, mxl = 0;
   bool bad = false;
 #pragma unroll
   for (int q = 0; q < kPairs; ++q) {
-    max_bits(v[q].x, mx, bad);
-    max_bits(v[q].y, mx, bad);
+    max_bits(v[q].x, mxh, mxl, bad);
+    max_bits(v[q].y, mxh, mxl, bad);
   }
   if (live) {
-    for (int64_t j = kSweep + tid; j < k; j += kSplitThreads) max_bits(row[j], mx, bad);
+    for (int j = kSweep + tid; j < k; j += kSplitThreads) max_bits(row[j], mxh, mxl, bad);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long u = __shfl_xor_sync(0xffffffffu, mx, o);
-    mx = u > mx ? u : mx;
+    mxh = max(mxh, __shfl_xor_sync(0xffffffffu, mxh, o));
+    mxl = max(mxl, __shfl_xor_sync(0xffffffffu, mxl, o));
   }
   bad = __any_sync(0xffffffffu, bad);
   if ((tid & 31) == 0) {
-    red[tid >> 5] = mx;
+    red_h[tid >> 5] = mxh;
+    red_l[tid >> 5] = mxl;
     red_bad[tid >> 5] = bad ? 1 : 0;
   }
   __syncthreads();
-  mx = 0;
   int any_bad = 0;
 #pragma unroll
   for (int w = 0; w < kSplitThreads / 32; ++w) {
-    mx = red[w] > mx ? red[w] : mx;
+    mxh = max(mxh, red_h[w]);
+    mxl = max(mxl, red_l[w]);
     any_bad |= red_bad[w];
   }
-  const int e_row = any_bad ? 0 : exponent_of_bits(mx);
+  const int e_row = any_bad ? 0 : row_exponent(mxh, mxl);
   if (tid == 0) {
     // a row holding NaN/Inf is marked; the product epilogue then writes NaN
     exps[r] = any_bad ? kBadExp : e_row;
     if (any_bad && flag != nullptr) atomicExch(flag, 1);
   }
+  const int c_row = 1075 + e_row - 96;
 
   constexpr int kElemBytes = KIND == 1 ? 1 : 2;
   char* base = static_cast<char*>(planes) + r * k_pad * kElemBytes;
   const int64_t plane_bytes = plane_stride * kElemBytes;
-  for (int64_t c0 = 0;;) {
+  for (int c0 = 0;;) {
 #pragma unroll
     for (int q = 0; q < kPairs; ++q) {
-      const int64_t j = c0 + 2 * (tid + static_cast<int64_t>(kSplitThreads) * q);
+      const int j = c0 + 2 * (tid + kSplitThreads * q);
       if (j < k_pad) {
         uint32_t a0, a1, a2, b0, b1, b2;
         bool na, nb;
-        fix96(v[q].x, e_row, a0, a1, a2, na);
-        fix96(v[q].y, e_row, b0, b1, b2, nb);
+        fix96(v[q].x, c_row, a0, a1, a2, na);
+        fix96(v[q].y, c_row, b0, b1, b2, nb);
         store_digits<0, KIND, BETA>(s, a0, a1, a2, na, b0, b1, b2, nb, base, j >> 1, plane_bytes);
       }
     }
+    if (k_pad - c0 <= kSweep) break;
     c0 += kSweep;
-    if (c0 >= k_pad) break;
 #pragma unroll
-    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, c0 + 2 * (tid + static_cast<int64_t>(kSplitThreads) * q), k, live, vec);
+    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, c0 + 2 * (tid + kSplitThreads * q), k, live, vec);
   }
 }
 
@@ -210,7 +221,8 @@ split_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t ld
                   int32_t* __restrict__ exps, void* __restrict__ planes, int64_t k_pad,
                   int64_t plane_stride, int* flag, const int* done) {
   if (done != nullptr && *done) return;
-  split_one_row<KIND, BETA>(A, blockIdx.x, m, k, lda, s, exps, planes, k_pad, plane_stride, flag);
+  split_one_row<KIND, BETA>(A, blockIdx.x, m, static_cast<int>(k), lda, s, exps, planes, static_cast<int>(k_pad),
+                            plane_stride, flag);
 }
 
 // Grouped: CTA x covers row x - row_start[b] of matrix b (row_start ascending,
@@ -232,7 +244,8 @@ split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restric
   const int64_t lda = which == 0 ? M.ldp : M.n;
   int32_t* exps = which == 2 ? M.expsX : M.expsP;
   void* planes = which == 2 ? M.planesX : M.planesP;
-  split_one_row<3, BETA>(A, r, M.n, M.n, lda, M.s, exps, planes, M.k_pad, M.n_pad * M.k_pad, nullptr);
+  split_one_row<3, BETA>(A, r, M.n, static_cast<int>(M.n), lda, M.s, exps, planes, static_cast<int>(M.k_pad),
+                         M.n_pad * M.k_pad, nullptr);
 }
 
 __global__ void transpose_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
@@ -257,6 +270,7 @@ cudaError_t launch_split_rows(const double* A, int64_t m, int64_t k, int64_t lda
                               int32_t* exps, void* planes, int64_t m_pad, int64_t k_pad,
                               int elem_kind, int* flag, const int* done, cudaStream_t st) {
   if (m_pad <= 0 || k_pad <= 0) return cudaSuccess;
+  if (k > k_pad || k_pad > kMaxRow) return cudaErrorInvalidValue;
   const int64_t plane_stride = m_pad * k_pad;
   dim3 grid(static_cast<unsigned>(m_pad));
   ProfScope prof(DMP_PROF_SPLIT, st);
@@ -289,7 +303,7 @@ cudaError_t launch_transpose(const double* A, int64_t m, int64_t n, int64_t lda,
 cudaError_t launch_split_grouped(const BatchMat* mats, const int64_t* row_start, int nmats, int64_t total_rows,
                                  int which, int beta, cudaStream_t st) {
   if (total_rows <= 0) return cudaSuccess;
-  ProfScope prof(DMP_PROF_SPLIT, st);
+  ProfScope prof(DMP_PROF_SPLIT, st);  // batch rows are at most a few thousand long (k_pad << kMaxRow)
   if (beta == 7) {
     split_grouped_kernel<7><<<static_cast<unsigned>(total_rows), kSplitThreads, 0, st>>>(mats, row_start, nmats,
                                                                                          which);
