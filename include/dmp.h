@@ -271,6 +271,15 @@ long long dmp_launch_count(void);
 /* Library version string. */
 const char* dmp_version(void);
 
+/* Whether DMP_EXEC_TC products with beta = 7 run on CTA pairs: clusters of two
+ * CTAs on neighbouring SMs that compute 256 x 256 output tiles with the 2-SM
+ * tensor-core MMA (each SM stages its own 128 rows of A and half of B). On by
+ * default; off runs one CTA per 128 x 256 tile. Both give bit-identical
+ * results (the same exact integer level sums). Process-wide, read at each
+ * launch; returns the previous setting. A performance knob with no
+ * counterpart in the paper. */
+int dmp_set_tc_pairing(int enable);
+
 #ifdef __cplusplus
 }
 #endif

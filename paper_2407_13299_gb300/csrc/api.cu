@@ -207,6 +207,8 @@ const char* dmp_version(void) { return "dmp 0.1 (sm_103a)"; }
 
 long long dmp_launch_count(void) { return g_launches.load(); }
 
+int dmp_set_tc_pairing(int enable) { return set_tc_pairing(enable); }
+
 const char* dmp_status_str(int code) {
   switch (code) {
     case DMP_OK: return "DMP_OK";

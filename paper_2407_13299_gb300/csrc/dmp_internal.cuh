@@ -15,7 +15,8 @@ namespace dmp {
 constexpr int kMaxSlices = 10;   // beta = 7: 70 bits; beta = 8 is limited to 9 (72 bits)
 constexpr int kTileM = 128;      // output tile rows of the slice-pair GEMMs
 constexpr int kTileN = 128;      // output tile columns
-constexpr int kPadK = 64;        // digit planes are padded to a multiple of this along K
+constexpr int kPadK = 128;       // digit planes are padded to a multiple of this along K (two
+                                 // 64-element swizzle atoms: the paired tcgen05 kernel stages 128)
 constexpr int32_t kBadExp = 0x7fffffff;  // row exponent of a row holding NaN/Inf
 
 inline int beta_of(int mode) { return mode == DMP_OZAKI_BF16 ? 8 : 7; }
@@ -94,6 +95,8 @@ cudaError_t launch_ozaki_imma(const int8_t* A, const int8_t* B, const int32_t* e
 // at most kTcMaxCtas CTAs, one per SM).
 constexpr int kTcMaxCtas = 160;
 size_t tc_scratch_bytes();
+// beta = 7 single-matrix products on CTA pairs (2-SM MMA); returns the previous setting
+int set_tc_pairing(int enable);
 cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, const int32_t* eb, int64_t m,
                             int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int s, int beta, int sym,
                             const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st);

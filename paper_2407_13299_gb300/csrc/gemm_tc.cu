@@ -45,12 +45,21 @@ constexpr int TC_BK = 64;  // bf16 elements per K block: one 128-byte swizzle ro
 constexpr int TC_THREADS = 320;
 constexpr int TC_EPI_WARPS = 8;
 
-template <int BN>
+// PAIR: a cluster of two CTAs computes a 256 x BN tile with tcgen05.mma.cta_group::2;
+// each CTA stages its own 128 rows of A and half of the BN rows of B, and its
+// TMEM receives its 128 output rows with all BN columns.
+// A PAIR stage holds two 64-element K atoms of each operand (8 MMAs per stage
+// barrier round: with 4 the per-stage wait and commit left the tensor pipe
+// idle about a third of the time).
+template <int BN, bool PAIR = false>
 struct TcCfg {
-  static constexpr int A_BYTES = TC_BM * TC_BK * 2;
-  static constexpr int B_BYTES = BN * TC_BK * 2;
+  static constexpr int KSUB = PAIR ? 2 : 1;  // 64-element K atoms per stage
+  static constexpr int A_ATOM = TC_BM * TC_BK * 2;
+  static constexpr int B_ATOM = (PAIR ? BN / 2 : BN) * TC_BK * 2;
+  static constexpr int A_BYTES = KSUB * A_ATOM;
+  static constexpr int B_BYTES = KSUB * B_ATOM;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int STAGES = BN == 256 ? 4 : 6;
+  static constexpr int STAGES = PAIR ? 3 : (BN == 128 ? 6 : 4);
   static constexpr int TMEM_COLS = 2 * BN;      // two fp32 chunk accumulators
   static constexpr int COLS = BN / 2;           // columns per epilogue thread
   static constexpr int BAR_BYTES = 256;
@@ -140,6 +149,71 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+
+// ---- the CTA pair (cluster of two, cta_group::2)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// the shared::cluster address of the same object in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_to_cta(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, "
+      "p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// arrive on a barrier of either CTA of the pair (a shared::cluster address)
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// TMA load into this CTA's shared memory that signals `bar`, which may be the peer's
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(dst),
+      "l"(tm), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// one MMA of the 256-row pair tile: A rows from both CTAs, B halves from both
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on `bar` in both CTAs of the pair when the MMAs issued so far complete
+__device__ __forceinline__ void umma_commit_pair_both(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(static_cast<unsigned short>(3))
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair_self(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -192,13 +266,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
-// bounded wait; false on timeout or when another role aborted
+// bounded wait; false on timeout or when another role aborted. CLUSTER: the
+// barrier also receives arrivals from the peer CTA (acquire at cluster scope).
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                          const TcParams& p) {
-  if (mbar_try_wait(bar, parity)) return true;
+  auto try_once = [&]() { return CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
+  if (try_once()) return true;
   const uint64_t deadline = globaltimer() + p.timeout_ns;
   for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (try_once()) return true;
     if ((it & 255u) == 0) {
       if (*abort_flag) return false;
       if (globaltimer() > deadline) {
@@ -212,7 +289,8 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
 
 __device__ __forceinline__ int npairs_of(int L, int s) { return min(s, L - 1) - max(1, L - s) + 1; }
 
-template <int BN>
+// Row block bi (BM rows: 128, or 256 for a CTA pair) and column block bj of tile idx.
+template <int BN, int BM>
 __device__ __forceinline__ void tile_of(const TcParams& p, int idx, int& bi, int& bj) {
   if (!p.sym) {
     bj = idx / p.tiles_m;  // column-block major: CTAs running together share B blocks
@@ -221,7 +299,7 @@ __device__ __forceinline__ void tile_of(const TcParams& p, int idx, int& bi, int
   }
   bj = 0;
   for (;;) {
-    const int cnt = min(p.tiles_m, (BN * (bj + 1)) / TC_BM);
+    const int cnt = min(p.tiles_m, (BN * (bj + 1)) / BM);
     if (idx < cnt) break;
     idx -= cnt;
     ++bj;
@@ -241,15 +319,18 @@ struct Job {
   EpiArgs epi;
 };
 
-template <int BN>
-__device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, int tile) {
+// PAIR: tile is a 256-row pair tile and this CTA (rank 0 or 1) takes rows
+// 128 rank .. 128 rank + 127 of it.
+template <int BN, bool PAIR = false>
+__device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, int tile,
+                                      uint32_t rank = 0) {
   Job j;
-  if (p.mats == nullptr) {
+  if (PAIR || p.mats == nullptr) {
     int bi, bj;
-    tile_of<BN>(p, tile, bi, bj);
+    tile_of<BN, PAIR ? 2 * TC_BM : TC_BM>(p, tile, bi, bj);
     j.ta = tmA;
     j.tb = tmB;
-    j.m0 = static_cast<int64_t>(bi) * TC_BM;
+    j.m0 = static_cast<int64_t>(bi) * (PAIR ? 2 * TC_BM : TC_BM) + TC_BM * static_cast<int64_t>(rank);
     j.n0 = static_cast<int64_t>(bj) * BN;
     j.rows_a = p.rows_a;
     j.rows_b = p.rows_b;
@@ -307,11 +388,17 @@ __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA,
 // Persistent: one CTA per SM walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // The three roles keep their ring and buffer phases across tiles, so the next
 // tile's loads and MMAs overlap the current tile's last fold and output.
-template <int BN, bool WIDE>
+//
+// PAIR (launched as clusters of two CTAs): the cluster walks 256-row pair
+// tiles. Each CTA loads its A rows and its half of the B rows, signalling the
+// leader's (rank 0) full barrier; the leader alone issues the cta_group::2
+// MMAs and its commits arrive on the stage and accumulator barriers of both
+// CTAs; both epilogues release a TMEM buffer on the leader's barrier.
+template <int BN, bool WIDE, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const TcParams p) {
-  using Cfg = TcCfg<BN>;
+  using Cfg = TcCfg<BN, PAIR>;
   if (p.done != nullptr && *p.done) return;  // uniform: the whole CTA leaves before any setup
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -328,6 +415,11 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  // CTA (or CTA pair) index and count for the persistent tile walk
+  const int cta_id = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int cta_stride = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
 
   if (threadIdx.x == 0) {
     for (int st = 0; st < Cfg::STAGES; ++st) {
@@ -336,7 +428,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accfull_bar(b), 1);
-      mbar_init(accempty_bar(b), TC_EPI_WARPS);
+      mbar_init(accempty_bar(b), PAIR ? 2 * TC_EPI_WARPS : TC_EPI_WARPS);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -347,11 +439,17 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     tma_prefetch(&tmB);
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
-    tmem_relinquish();
+    if (PAIR) {
+      tmem_alloc_pair(smem_u32(tmem_slot), Cfg::TMEM_COLS);  // both CTAs, the same columns
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // barriers of both CTAs initialised before any remote use
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -364,8 +462,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       uint32_t phase = 0;
       bool ok = true;
       uint32_t armed = 0;  // stages armed in the current ring pass (for the abort drain)
-      for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-        const Job jb = job_of<BN>(p, &tmA, &tmB, tile);
+      // PAIR: both CTAs' copies complete on the leader's full barrier, which expects both
+      const uint32_t full_target0 = PAIR ? map_to_cta(full_bar(0), 0) : full_bar(0);
+      const uint32_t expect_bytes = PAIR ? 2u * Cfg::STAGE_BYTES : static_cast<uint32_t>(Cfg::STAGE_BYTES);
+      const int b_off = PAIR ? static_cast<int>(rank) * (BN / 2) : 0;  // this CTA's half of the B rows
+      for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
+        const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
         if (jb.skip) continue;
         const int s = jb.s;
         for (int L = s + 1; L >= 2 && ok; --L) {
@@ -373,16 +475,26 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           for (int i = i_lo; i <= i_hi && ok; ++i) {
             const int j = L - i;
             const int ya = static_cast<int>((i - 1) * jb.rows_a + jb.m0);
-            const int yb = static_cast<int>((j - 1) * jb.rows_b + jb.n0);
-            for (int kt = 0; kt < jb.KT; ++kt) {
-              if (!wait_bar(empty_bar(stage), phase ^ 1u, abort_flag, p)) {
+            const int yb = static_cast<int>((j - 1) * jb.rows_b + jb.n0) + b_off;
+            for (int kt = 0; kt < jb.KT; kt += Cfg::KSUB) {
+              if (!wait_bar<PAIR>(empty_bar(stage), phase ^ 1u, abort_flag, p)) {
                 ok = false;
                 break;
               }
               const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
-              mbar_arrive_expect_tx(full_bar(stage), Cfg::STAGE_BYTES);
-              tma_load_2d(sa, jb.ta, full_bar(stage), kt * TC_BK, ya);
-              tma_load_2d(sa + Cfg::A_BYTES, jb.tb, full_bar(stage), kt * TC_BK, yb);
+              if (PAIR) {
+                const uint32_t fb = full_target0 + 8u * stage;
+                if (leader) mbar_arrive_expect_tx(full_bar(stage), expect_bytes);
+#pragma unroll
+                for (int u = 0; u < Cfg::KSUB; ++u) {
+                  tma_load_2d_pair(sa + u * Cfg::A_ATOM, jb.ta, fb, (kt + u) * TC_BK, ya);
+                  tma_load_2d_pair(sa + Cfg::A_BYTES + u * Cfg::B_ATOM, jb.tb, fb, (kt + u) * TC_BK, yb);
+                }
+              } else {
+                mbar_arrive_expect_tx(full_bar(stage), expect_bytes);
+                tma_load_2d(sa, jb.ta, full_bar(stage), kt * TC_BK, ya);
+                tma_load_2d(sa + Cfg::A_BYTES, jb.tb, full_bar(stage), kt * TC_BK, yb);
+              }
               armed |= 1u << stage;
               if (++stage == Cfg::STAGES) {
                 stage = 0;
@@ -393,8 +505,9 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
         }
       }
-      if (!ok) {
-        // let copies already issued land before shared memory is released
+      if (!ok && leader) {
+        // let copies already issued land before shared memory is released (the
+        // leader's full barriers count both CTAs' copies)
         for (int st = 0; st < Cfg::STAGES; ++st) {
           if (armed & (1u << st)) {
             const uint64_t dl = globaltimer() + 100000000ull;
@@ -403,52 +516,81 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
         }
       }
+      if (PAIR && ok) {
+        // the leader's commits arrive on this CTA's empty barriers: wait until
+        // every stage is released, so no arrival is left in flight at exit
+        for (int i = 0; i < Cfg::STAGES && ok; ++i) {
+          ok = wait_bar<PAIR>(empty_bar(stage), phase ^ 1u, abort_flag, p);
+          if (++stage == Cfg::STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+    if (lane == 0 && leader) {
+      constexpr uint32_t idesc = idesc_bf16(PAIR ? 2 * TC_BM : TC_BM, BN);
       int stage = 0;
       uint32_t phase = 0;
       int buf = 0;
       uint32_t aph[2] = {0u, 0u};
       bool ok = true;
       bool issued = false;
-      for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-        const Job jb = job_of<BN>(p, &tmA, &tmB, tile);
+      for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
+        const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
         if (jb.skip) continue;
         const int s = jb.s;
+        // stages per level and per fp32 chunk (KT and CH are multiples of KSUB)
+        const int CHS = CH / Cfg::KSUB;
         for (int L = s + 1; L >= 2 && ok; --L) {
-          const int nkb = npairs_of(L, s) * jb.KT;
+          const int nkb = npairs_of(L, s) * (jb.KT / Cfg::KSUB);
           for (int kb = 0; kb < nkb; ++kb) {
-            const int kc = kb % CH;
+            const int kc = kb % CHS;
             const bool first = kc == 0;
-            const bool last = (kc == CH - 1) || (kb == nkb - 1);
+            const bool last = (kc == CHS - 1) || (kb == nkb - 1);
             if (first) {
-              if (!wait_bar(accempty_bar(buf), aph[buf] ^ 1u, abort_flag, p)) {
+              if (!wait_bar<PAIR>(accempty_bar(buf), aph[buf] ^ 1u, abort_flag, p)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
             }
-            if (!wait_bar(full_bar(stage), phase, abort_flag, p)) {
+            if (!wait_bar<PAIR>(full_bar(stage), phase, abort_flag, p)) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
-            const uint64_t ad = sdesc_sw128(sa);
-            const uint64_t bd = sdesc_sw128(sa + Cfg::A_BYTES);
             const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
 #pragma unroll
-            for (int ks = 0; ks < TC_BK / 16; ++ks) {
-              // advance 16 bf16 = 32 bytes along K inside the swizzled row
-              umma_bf16(d, ad + 2ull * ks, bd + 2ull * ks, idesc, (first && ks == 0) ? 0u : 1u);
+            for (int u = 0; u < Cfg::KSUB; ++u) {
+              const uint64_t ad = sdesc_sw128(sa + u * Cfg::A_ATOM);
+              const uint64_t bd = sdesc_sw128(sa + Cfg::A_BYTES + u * Cfg::B_ATOM);
+#pragma unroll
+              for (int ks = 0; ks < TC_BK / 16; ++ks) {
+                // advance 16 bf16 = 32 bytes along K inside the swizzled row
+                const uint32_t acc = (first && u == 0 && ks == 0) ? 0u : 1u;
+                if (PAIR) {
+                  umma_bf16_pair(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
+                } else {
+                  umma_bf16(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
+                }
+              }
             }
             issued = true;
-            umma_commit(empty_bar(stage));
+            if (PAIR) {
+              umma_commit_pair_both(empty_bar(stage));
+            } else {
+              umma_commit(empty_bar(stage));
+            }
             if (last) {
-              umma_commit(accfull_bar(buf));
+              if (PAIR) {
+                umma_commit_pair_both(accfull_bar(buf));
+              } else {
+                umma_commit(accfull_bar(buf));
+              }
               aph[buf] ^= 1u;
               buf ^= 1;
             }
@@ -461,10 +603,19 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       }
       if (!ok && issued) {
         // wait for the MMAs in flight before TMEM is released
-        umma_commit(drain_bar);
+        if (PAIR) {
+          umma_commit_pair_self(drain_bar);
+        } else {
+          umma_commit(drain_bar);
+        }
         const uint64_t dl = globaltimer() + 100000000ull;
         while (!mbar_try_wait(drain_bar, 0) && globaltimer() < dl) {
         }
+      }
+      if (PAIR && ok) {
+        // both epilogues arrive on this CTA's accumulator barriers: wait for
+        // their last releases, so no arrival is left in flight at exit
+        for (int b = 0; b < 2 && ok; ++b) ok = wait_bar<PAIR>(accempty_bar(b), aph[b] ^ 1u, abort_flag, p);
       }
     }
   } else {
@@ -489,12 +640,14 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int buf = 0;
     uint32_t aph[2] = {0u, 0u};
     bool ok = true;
-    for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+    // PAIR: TMEM buffers are released on the leader's barrier
+    const uint32_t accempty_target0 = PAIR ? map_to_cta(accempty_bar(0), 0) : accempty_bar(0);
+    for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
       int64_t m0, n0;
       int s, KT;
       bool skip;
       {
-        const Job jb = job_of<BN>(p, &tmA, &tmB, tile);
+        const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
         m0 = jb.m0;
         n0 = jb.n0;
         s = jb.s;
@@ -512,7 +665,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const int nch = (nkb + CH - 1) / CH;
         for (int ch = 0; ch < nch; ++ch) {
           // the whole warp takes the same branch: tcgen05.ld below is warp-collective
-          const bool got = wait_bar(accfull_bar(buf), aph[buf], abort_flag, p);
+          const bool got = wait_bar<PAIR>(accfull_bar(buf), aph[buf], abort_flag, p);
           if (!__all_sync(0xffffffffu, got)) {
             ok = false;
             break;
@@ -528,7 +681,13 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(accempty_bar(buf));
+          if (lane == 0) {
+            if (PAIR) {
+              mbar_arrive_cluster(accempty_target0 + 8u * buf);
+            } else {
+              mbar_arrive(accempty_bar(buf));
+            }
+          }
           aph[buf] ^= 1u;
           buf ^= 1;
           if (WIDE && ((ch & 63) == 63 || ch == nch - 1)) {
@@ -613,7 +772,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         }
         if (L != 2) continue;
         // ---- last level: unscale and apply the output step
-        const Job jb = job_of<BN>(p, &tmA, &tmB, tile);
+        const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
         const int64_t r = m0 + row;
         if (r >= jb.m) continue;
         const int32_t er = jb.ea[r];
@@ -668,9 +827,14 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   // ------------------------------------------------------------ teardown
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // neither CTA leaves while the other may still use its barriers or TMEM
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, Cfg::TMEM_COLS);
+    if (PAIR) {
+      tmem_dealloc_pair(tmem, Cfg::TMEM_COLS);
+    } else {
+      tmem_dealloc(tmem, Cfg::TMEM_COLS);
+    }
   }
 }
 
@@ -709,23 +873,83 @@ bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int6
 
 namespace {
 
-template <int BN, bool WIDE>
-cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& p, int ntiles,
-                           cudaStream_t st) {
-  using Cfg = TcCfg<BN>;
+template <int BN, bool WIDE, bool PAIR>
+cudaError_t set_smem_attr() {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_tc_kernel<BN, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(ozaki_tc_kernel<BN, WIDE, PAIR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, PAIR>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  ozaki_tc_kernel<BN, WIDE><<<ntiles, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
+  return cudaSuccess;
+}
+
+template <int BN, bool WIDE, bool PAIR = false>
+cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& p, int grid,
+                           cudaStream_t st) {
+  using Cfg = TcCfg<BN, PAIR>;
+  cudaError_t e = set_smem_attr<BN, WIDE, PAIR>();
+  if (e != cudaSuccess) return e;
+  if (PAIR) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = Cfg::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, WIDE, PAIR>, ta, tb, p);
+    if (e != cudaSuccess) return e;
+  } else {
+    ozaki_tc_kernel<BN, WIDE, PAIR><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
+  }
   count_launch();
   return cudaGetLastError();
 }
 
+bool g_pairing = true;
+
+// CTA pairs of the PAIR kernel that can be resident at once (0: none)
+int tc_max_pairs() {
+  static int pairs = -1;
+  if (pairs < 0) {
+    pairs = 0;
+    if (set_smem_attr<256, false, true>() == cudaSuccess) {
+      cudaLaunchConfig_t cfg;
+      std::memset(&cfg, 0, sizeof(cfg));
+      cfg.gridDim = dim3(2);
+      cfg.blockDim = dim3(TC_THREADS);
+      cfg.dynamicSmemBytes = TcCfg<256, true>::SMEM;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int c = 0;
+      if (cudaOccupancyMaxActiveClusters(&c, ozaki_tc_kernel<256, false, true>, &cfg) == cudaSuccess) pairs = c;
+    }
+    (void)cudaGetLastError();
+    pairs = std::min(pairs, kTcMaxCtas / 2);
+  }
+  return pairs;
+}
+
 }  // namespace
+
+int set_tc_pairing(int enable) {
+  const int prev = g_pairing ? 1 : 0;
+  g_pairing = enable != 0;
+  return prev;
+}
 
 int tc_max_ctas() {
   static int sms = 0;
@@ -747,9 +971,14 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   const bool wide = beta == 8;
   const int BN = wide ? 128 : 256;
   if (rows_a % TC_BM != 0 || rows_b % BN != 0 || k_pad % TC_BK != 0) return cudaErrorInvalidValue;
+  // beta = 7 products run on CTA pairs (256 x 256 tiles, 2-SM MMA) when rows allow
+  const bool pair = !wide && g_pairing && rows_a % (2 * TC_BM) == 0 && k_pad % (2 * TC_BK) == 0 &&
+                    tc_max_pairs() > 0;
+  const int BM = pair ? 2 * TC_BM : TC_BM;
   CUtensorMap ta, tb;
   if (!make_plane_map(&ta, A, k_pad, static_cast<int64_t>(s) * rows_a, TC_BM)) return cudaErrorInvalidValue;
-  if (!make_plane_map(&tb, B, k_pad, static_cast<int64_t>(s) * rows_b, BN)) return cudaErrorInvalidValue;
+  if (!make_plane_map(&tb, B, k_pad, static_cast<int64_t>(s) * rows_b, pair ? BN / 2 : BN))
+    return cudaErrorInvalidValue;
   TcParams p;
   p.mats = nullptr;
   p.tiles = nullptr;
@@ -764,7 +993,7 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   p.rows_a = rows_a;
   p.rows_b = rows_b;
   p.sym = sym;
-  p.tiles_m = static_cast<int>(rows_a / TC_BM);
+  p.tiles_m = static_cast<int>(rows_a / BM);
   p.tiles_n = static_cast<int>(rows_b / BN);
   p.ea = ea;
   p.eb = eb;
@@ -774,14 +1003,15 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   p.timeout_ns = 5000000000ull;
   int ntiles = 0;
   if (sym) {
-    for (int bj = 0; bj < p.tiles_n; ++bj) ntiles += std::min(p.tiles_m, (BN * (bj + 1)) / TC_BM);
+    for (int bj = 0; bj < p.tiles_n; ++bj) ntiles += std::min(p.tiles_m, (BN * (bj + 1)) / BM);
   } else {
     ntiles = p.tiles_m * p.tiles_n;
   }
   p.ntiles = ntiles;
   p.scratch = scratch;
-  const int grid = std::min(ntiles, tc_max_ctas());
   ProfScope prof(DMP_PROF_PRODUCT, st);
+  if (pair) return launch_tc_impl<256, false, true>(ta, tb, p, 2 * std::min(ntiles, tc_max_pairs()), st);
+  const int grid = std::min(ntiles, tc_max_ctas());
   return wide ? launch_tc_impl<128, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
 }
 

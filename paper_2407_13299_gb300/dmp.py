@@ -81,6 +81,7 @@ SIGNATURES = {
     "dmp_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "dmp_launch_count": (ctypes.c_longlong, []),
     "dmp_version": (ctypes.c_char_p, []),
+    "dmp_set_tc_pairing": (ctypes.c_int, [ctypes.c_int]),
 }
 
 
@@ -109,6 +110,12 @@ def status_str(code: int) -> str:
 def launch_count() -> int:
     """Kernels launched by libdmp in this process so far."""
     return int(lib().dmp_launch_count())
+
+
+def set_tc_pairing(enable: bool) -> bool:
+    """Run tcgen05 beta = 7 products on CTA pairs (2-SM MMA, the default) or on
+    single CTAs (dmp_set_tc_pairing). Returns the previous setting."""
+    return bool(lib().dmp_set_tc_pairing(1 if enable else 0))
 
 
 PROF_PRODUCT, PROF_SPLIT, PROF_MEASURE, PROF_INIT, PROF_OTHER = 0, 1, 2, 3, 4
