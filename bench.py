@@ -350,7 +350,8 @@ def run_ours(args):
     peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
     traffic = kernel_traffic("gemm_tc.cu", "ozaki_tc_kernel_n8192.md") if args.executor == "tc" else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "ozaki_tc_kernel<256,false>" if args.executor == "tc" else
+                "traffic": traffic,
+                "kernel": "ozaki_tc_kernel<256,false,true> (CTA pairs, 2-SM MMA)" if args.executor == "tc" else
                 "ozaki_imma_kernel",
                 "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)",
                 "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
@@ -412,7 +413,8 @@ def run_ours(args):
             "config": {"workload": workload_name(w), "mode": "ozaki-int8", "slices": s, "executor": args.executor,
                        "iters": info["iters"], "status": dmp.status_str(info["status"]),
                        "rel_energy_error": rel_energy, "idempotency": info["idem"],
-                       "l2": "inputs larger than L2 (H 512 MiB, digit planes 1.8 GiB)", "slice_tuning": tune,
+                       "l2": (f"inputs larger than L2 (H {n * n * 8 / 2**20:.0f} MiB, digit planes "
+                              f"{2 * s * n * n * 2 / 2**30:.2f} GiB)"), "slice_tuning": tune,
                        "replicas": world},
             "roofline": roofline,
             "cpu_baseline": cpu,
