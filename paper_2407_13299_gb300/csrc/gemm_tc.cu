@@ -32,6 +32,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cmath>
 #include <cstring>
 
 #include "dmp_internal.cuh"
@@ -72,6 +73,10 @@ struct TcParams {
   int64_t m, n;
   int64_t rows_a, rows_b;  // padded rows per digit plane
   int sym, tiles_m, tiles_n;
+  // tile order: bands of band_w column blocks, each cut into groups of group_h
+  // row blocks, so the tiles in flight together form a near-square block and
+  // share their operand panels in L2 (band_w = 0: column-major order)
+  int band_w, group_h;
   const int32_t* ea;
   const int32_t* eb;
   EpiArgs epi;
@@ -289,9 +294,36 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
 
 __device__ __forceinline__ int npairs_of(int L, int s) { return min(s, L - 1) - max(1, L - s) + 1; }
 
+// Row blocks of column block c that hold tiles (symmetric: some element with row <= column).
+template <int BN, int BM>
+__device__ __forceinline__ int rows_of_col(const TcParams& p, int c) {
+  return p.sym ? min(p.tiles_m, (BN * (c + 1)) / BM) : p.tiles_m;
+}
+
 // Row block bi (BM rows: 128, or 256 for a CTA pair) and column block bj of tile idx.
 template <int BN, int BM>
 __device__ __forceinline__ void tile_of(const TcParams& p, int idx, int& bi, int& bj) {
+  if (p.band_w > 0) {
+    const int W = p.band_w, H = p.group_h;
+    for (int c0 = 0; c0 < p.tiles_n; c0 += W) {
+      const int c1 = min(p.tiles_n, c0 + W);
+      const int rmax = rows_of_col<BN, BM>(p, c1 - 1);  // nondecreasing in the column
+      for (int r0 = 0; r0 < rmax; r0 += H) {
+        const int r1 = min(rmax, r0 + H);
+        for (int c = c0; c < c1; ++c) {
+          const int k = max(0, min(rows_of_col<BN, BM>(p, c), r1) - r0);
+          if (idx < k) {
+            bi = r0 + idx;
+            bj = c;
+            return;
+          }
+          idx -= k;
+        }
+      }
+    }
+    bi = bj = 0;  // not reached for idx < ntiles
+    return;
+  }
   if (!p.sym) {
     bj = idx / p.tiles_m;  // column-block major: CTAs running together share B blocks
     bi = idx % p.tiles_m;
@@ -995,6 +1027,14 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   p.sym = sym;
   p.tiles_m = static_cast<int>(rows_a / BM);
   p.tiles_n = static_cast<int>(rows_b / BN);
+  {
+    // blocks of about as many tiles as run at once, near-square in elements
+    const int units = pair ? tc_max_pairs() : tc_max_ctas();
+    int w = static_cast<int>(std::lround(std::sqrt(static_cast<double>(units) * BM / BN)));
+    w = std::max(1, std::min(w, p.tiles_n));
+    p.band_w = w;
+    p.group_h = std::max(1, units / w);
+  }
   p.ea = ea;
   p.eb = eb;
   p.epi = epi;
