@@ -142,9 +142,13 @@ int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int
  * (Sec. "Ozaki Scheme"): A scaled per row and B per column by powers of two,
  * split into `slices` digit planes of beta bits (mode DMP_OZAKI_INT8: beta 7;
  * DMP_OZAKI_BF16: beta 8), level sums S_L = sum_{i+j=L} A_i B_j formed exactly
- * for L = 2..s+1, and C = 2^(e_r+f_c) * sum_L S_L 2^(-beta L) added in float64
- * from L = s+1 down to 2. The result is bit-for-bit the same for every
- * executor. mode DMP_FP64 computes a plain float64 product instead.
+ * for L = 2..s+1, and C = 2^(e_r+f_c) * sum_L S_L 2^(-beta L) in float64:
+ * groups of up to four consecutive levels (beta 7; single levels for beta 8)
+ * are first combined exactly in 64-bit integers, then the groups are added in
+ * float64 from the L = s+1 end to L = 2. For beta 7 and s <= 8 this is the
+ * correctly rounded value of the exact sum of the kept pairs. The result is
+ * bit-for-bit the same for every executor. mode DMP_FP64 computes a plain
+ * float64 product instead.
  * A row of A or column of B holding NaN/Inf gives a NaN row/column of C.
  * Limits: s * k * (2^beta - 1)^2 < 2^31 (exact s32 level sums).
  */
