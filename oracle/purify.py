@@ -34,6 +34,14 @@ Stopping rules (readings; the paper runs TRS4 with an energy-change test, Sec.
      difference has sunk into rounding noise          -> C_OUT_OF_RANGE
 The rules are tested in this order on each iterate, before the update.
 
+Refinement (Sec. "Precision Requirements Sweep"): after the loop has
+stopped, one McWeeny step P' = 3 P^2 - 2 P^3 taken in full precision (the
+paper's mixed-precision recommendation when the energy matters). Reading: the
+step's two products use the `refine_product` passed in (FP64, or an Ozaki
+product with enough slices to reach FP64 accuracy); the returned P, energy and
+band energy are those of P', and the unrefined values are kept. The step is
+the update above with c = 1/2, but is written here as printed.
+
 Energies: tr(P H) is reported as `energy`; the paper's band energy
 Tr(H K) = 2 tr(P H) is reported as `band_energy` (Sec. "Error Evaluation
 Criteria"), as are the RMSD of P and the commutator norm ||H K - K H||_F.
@@ -121,8 +129,18 @@ def pm_update(P, X2, X3, c):
     return alpha * P + b2 * X2 + b3 * X3
 
 
+def mcweeny_step(P, product=None):
+    """One McWeeny step P' = 3 P^2 - 2 P^3 (the equation printed in Sec.
+    "Precision Requirements Sweep"), with P^2 = P P and P^3 = P P^2 formed by
+    `product` (FP64 by default)."""
+    product = fp64_product if product is None else product
+    X2 = product(P, P)
+    X3 = product(P, X2)
+    return 3.0 * X2 - 2.0 * X3
+
+
 def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
-           energy_tol: float = 0.0, record: bool = False):
+           energy_tol: float = 0.0, record: bool = False, refine_product=None):
     """Canonical purification of H with the stopping rules of the module header.
 
     `product(A, B)` forms every matrix product (FP64 by default; pass a partial
@@ -130,6 +148,11 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
     status, iters (number of updates applied), energy = tr(PH), band_energy,
     idem = ||P^2 - P||_F, trace, the per-iteration histories, the initial-guess
     scalars and, with record=True, every iterate P_0 .. P_iters.
+
+    With `refine_product` set, the stopped iterate gets one McWeeny step whose
+    products use it (the refinement of the module header); P, energy and
+    band_energy then describe the refined matrix, energy_unrefined the one
+    before, and idem stays that of the unrefined iterate.
     """
     product = fp64_product if product is None else product
     H = np.asarray(H, dtype=np.float64)
@@ -180,8 +203,14 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
         if record:
             iterates.append(P.copy())
         k += 1
+    energy_unrefined = 0.5 * band[-1]
+    energy = energy_unrefined
+    if refine_product is not None:
+        P = mcweeny_step(P, refine_product)
+        energy = float(np.sum(P * H))
     out = dict(P=P, status=status, status_name=STATUS_NAMES[status], iters=k,
-               energy=0.5 * band[-1], band_energy=band[-1], idem=idems[-1], trace=traces[-1],
+               energy=energy, band_energy=2.0 * energy, energy_unrefined=energy_unrefined,
+               refined=refine_product is not None, idem=idems[-1], trace=traces[-1],
                band_history=band, idem_history=idems, trace_history=traces, c_history=cs,
                branch_history=branches, init=init)
     if record:

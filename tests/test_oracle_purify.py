@@ -8,6 +8,7 @@ canonical update, Gershgorin's theorem, and the stopping rules.
 
 import json
 import os
+from fractions import Fraction
 from functools import partial
 
 import numpy as np
@@ -206,3 +207,65 @@ def test_spectral_loop_matches_matrix_loop():
     assert np.allclose(np.sort(sp["x"]), w, atol=1e-10)
     P0, _ = pu.initial_guess(h.H, 20)
     assert np.allclose(np.sort(np.linalg.eigvalsh(P0)), np.sort(x0), atol=1e-13)
+
+
+# ---- refinement: one McWeeny step after the loop (Sec. "Precision Requirements Sweep")
+
+def test_mcweeny_step_matches_printed_polynomial_exactly_on_diagonals():
+    """P = diag(l): P' = diag(3 l^2 - 2 l^3) of the printed equation, checked
+    against exact rationals (the FP64 products of diagonal matrices are exact,
+    so only the last multiply-adds round)."""
+    rng = np.random.default_rng(3)
+    lam = np.concatenate([rng.uniform(-0.2, 1.2, 40), [0.0, 1.0, 0.5, -1e-9, 1.0 + 1e-9]])
+    got = pu.mcweeny_step(np.diag(lam))
+    assert np.count_nonzero(got - np.diag(np.diag(got))) == 0
+    for x, g in zip(lam, np.diag(got)):
+        q = Fraction(float(x))
+        exact = 3 * q * q - 2 * q * q * q
+        assert abs(Fraction(float(g)) - exact) <= Fraction(1, 2 ** 50) * max(1, abs(exact))
+
+
+def test_mcweeny_step_maps_eigenvalues_of_a_rotated_matrix():
+    rng = np.random.default_rng(4)
+    n = 60
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = rng.uniform(-0.1, 1.1, n)
+    P = (Q * lam) @ Q.T
+    P = 0.5 * (P + P.T)
+    got = np.linalg.eigvalsh(pu.mcweeny_step(P))
+    want = np.sort(3 * lam ** 2 - 2 * lam ** 3)
+    assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_refinement_squares_the_distance_to_a_projector():
+    """Eigenvalues 0 + d and 1 - d move to 3 d^2 - 2 d^3 and 1 - (3 d^2 - 2 d^3):
+    the idempotency error goes from O(d) to O(d^2)."""
+    rng = np.random.default_rng(5)
+    n, n_occ = 80, 20
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    d = rng.uniform(1e-5, 1e-4, n)
+    lam = np.where(np.arange(n) < n_occ, 1.0 - d, d)
+    P = (Q * lam) @ Q.T
+    P = 0.5 * (P + P.T)
+    R = pu.mcweeny_step(P)
+    lam_r = np.where(np.arange(n) < n_occ, 1.0 - (3 * d ** 2 - 2 * d ** 3), 3 * d ** 2 - 2 * d ** 3)
+    idem_r = np.sqrt(np.sum((lam_r ** 2 - lam_r) ** 2))
+    assert abs(np.linalg.norm(R @ R - R) - idem_r) <= 1e-3 * idem_r + 1e-13
+    assert np.linalg.norm(R @ R - R) < 1e-3 * np.linalg.norm(P @ P - P)
+
+
+def test_refinement_fixes_the_energy_of_a_low_slice_purification():
+    """The paper's observation: one full-precision McWeeny step after a
+    low-precision purification cuts the energy error by orders of magnitude.
+    Here Ozaki-INT8 products with s = 4, refined with FP64 and with s = 9
+    Ozaki products (FP64 level)."""
+    h = make_hamiltonian(128, 32, occ=(-1.5, -0.01), virt=(0.01, 1.5), seed=61)
+    E_star = float(np.sum(np.sort(h.e)[:32]))
+    low = partial(oz.ozaki_gemm, s=4, beta=7)
+    r64 = pu.purify(h.H, 32, tol=1e-10, product=low, refine_product=pu.fp64_product)
+    r9 = pu.purify(h.H, 32, tol=1e-10, product=low, refine_product=partial(oz.ozaki_gemm, s=9, beta=7))
+    before = abs(r64["energy_unrefined"] - E_star) / abs(E_star)
+    after = abs(r64["energy"] - E_star) / abs(E_star)
+    assert r64["refined"] and after < 1e-2 * before and after < 1e-9
+    assert np.max(np.abs(r9["P"] - r64["P"])) < 1e-13
+    assert r64["iters"] == r9["iters"] and r64["band_energy"] == 2.0 * r64["energy"]
