@@ -84,6 +84,9 @@ typedef struct {
   int32_t flags;            /* DMP_FLAG_* bits                                       */
   double tol;               /* ||P^2 - P||_F threshold; 0 -> 1e-10                   */
   double energy_tol;        /* optional |change of Tr(HK)| threshold; 0 = off        */
+  int32_t refine_slices;    /* refinement after the loop (see dm_purify): 0 off,
+                               -1 FP64 products, s_r > 0 Ozaki products of s_r slices */
+  int32_t reserved;         /* 0 */
 } dmp_opts;
 
 /* Per-run report, filled when the host pointer is non-NULL (the call then
@@ -99,6 +102,9 @@ typedef struct {
   double trace;        /* tr(P)                                                  */
   double c_last;       /* last purification coefficient                          */
   double h_min, h_max; /* Gershgorin bounds used for the initial guess          */
+  double energy_unrefined; /* tr(P H) before the refinement step (= energy if none) */
+  int32_t refined;     /* 1 if the refinement step was applied                   */
+  int32_t reserved;
 } dmp_info;
 
 /* Bytes of workspace dm_purify needs for this n and these options. */
@@ -118,7 +124,14 @@ int dmp_tape_size(int64_t n, const dmp_opts* opts, size_t* bytes);
  * iterate P_k: ||P_k^2 - P_k||_F < tol (DMP_OK); the paper's energy halt rule
  * (DMP_STALLED); |change of band energy| < energy_tol if set (DMP_OK);
  * k == max_iter (DMP_NOT_CONVERGED); tr(P - P^2) <= 0 or c outside [0, 1]
- * (DMP_C_OUT_OF_RANGE). The returned P is that P_k.
+ * (DMP_C_OUT_OF_RANGE). The returned P is that P_k, or, with
+ * opts->refine_slices != 0 and a status >= 0, its refinement: one McWeeny step
+ * P' = 3 P_k^2 - 2 P_k^3 in full precision (Sec. "Precision Requirements
+ * Sweep": the paper's mixed-precision recommendation when the energy matters),
+ * with FP64 products (refine_slices = -1) or Ozaki products of refine_slices
+ * slices (9 reaches FP64 accuracy; the level-sum limit below applies to it).
+ * info->energy then describes P' and info->energy_unrefined P_k; info->idem
+ * stays that of P_k. Refinement with a tape is DMP_ERR_UNSUPPORTED.
  *   H      n x n, leading dimension ldh. Only the upper triangle is read; the
  *          lower triangle is taken as its mirror.
  *   P      n x n output, leading dimension ldp (may not alias H).

@@ -33,6 +33,7 @@ struct Carver {
 struct Opts {
   int mode, s, beta, executor, max_iter, every;
   double tol, energy_tol;
+  int refine;  // 0 off, -1 FP64 products, > 0 Ozaki slices of the refinement step
 };
 
 int normalize(const dmp_opts* o, Opts& out) {
@@ -61,6 +62,9 @@ int normalize(const dmp_opts* o, Opts& out) {
   out.tol = o->tol == 0.0 ? 1e-10 : o->tol;
   out.energy_tol = o->energy_tol;
   if (!(out.tol >= 0.0) || !(out.energy_tol >= 0.0)) return DMP_ERR_INVALID_ARG;
+  out.refine = o->refine_slices;
+  if (out.refine != 0 && out.mode == DMP_FP64) out.refine = -1;
+  if (out.refine < -1 || out.refine > (out.beta == 8 ? 9 : 10)) return DMP_ERR_INVALID_ARG;
   return DMP_OK;
 }
 
@@ -106,7 +110,9 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
   L.Palt = c.take(static_cast<size_t>(n) * n * sizeof(double));
   L.X2 = c.take(static_cast<size_t>(n) * n * sizeof(double));
   if (o.mode != DMP_FP64) {
-    const size_t plane = static_cast<size_t>(o.s) * L.n_pad * L.k_pad * elem_bytes(o.executor);
+    // room for the refinement step's slices too
+    const int smax = std::max(o.s, o.refine);
+    const size_t plane = static_cast<size_t>(smax) * L.n_pad * L.k_pad * elem_bytes(o.executor);
     L.planesP = c.take(plane);
     L.planesX = c.take(plane);
   } else {
@@ -253,6 +259,9 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   if (n < 2 || ldh < n || ldp < n || n_occ <= 0 || n_occ >= n) return DMP_ERR_INVALID_ARG;
   if (o.mode != DMP_FP64 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.s, o.beta))
     return DMP_ERR_UNSUPPORTED;
+  if (o.refine > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.refine, o.beta))
+    return DMP_ERR_UNSUPPORTED;
+  if (o.refine != 0 && tape != nullptr) return DMP_ERR_UNSUPPORTED;
   const PurifyLayout L = purify_layout(n, o);
   if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
   TapeLayout TL{};
@@ -340,13 +349,59 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     std::swap(cur, alt);
     std::swap(ldcur, ldalt);
   }
+  // ---- refinement (Sec. "Precision Requirements Sweep"): one McWeeny step in
+  // full precision, P' = 3 P^2 - 2 P^3, run as the update with the weights of c = 1/2
+  bool refined = false;
+  if (o.refine != 0) {
+    int32_t status_now = 0;
+    DMP_CUDA(cudaMemcpyAsync(&status_now, &state->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DMP_CUDA(cudaStreamSynchronize(st));
+    if (status_now >= 0) {
+      DMP_CUDA(launch_refine_weights(state, st));
+      EpiArgs r2{};
+      r2.kind = EPI_SYM_STORE;
+      r2.C = X2;
+      r2.ldc = n;
+      EpiArgs r3{};
+      r3.kind = EPI_PM_UPDATE;
+      r3.C = alt;
+      r3.ldc = ldalt;
+      r3.P = cur;
+      r3.ldp = ldcur;
+      r3.X2 = X2;
+      r3.ldx = n;
+      r3.state = state;
+      if (o.refine < 0) {
+        DMP_CUDA(launch_gemm_f64(cur, ldcur, cur, ldcur, n, n, n, 1, r2, nullptr, st));
+        DMP_CUDA(launch_gemm_f64(cur, ldcur, X2, n, n, n, n, 1, r3, nullptr, st));
+      } else {
+        Opts orr = o;
+        orr.s = o.refine;
+        DMP_CUDA(launch_split_rows(cur, n, n, ldcur, orr.s, orr.beta, expsP, planesP, L.n_pad, L.k_pad,
+                                   elem_kind(o.executor), nullptr, nullptr, st));
+        DMP_CUDA(launch_product(orr, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, r2, nullptr,
+                                err, scratch, st));
+        DMP_CUDA(launch_split_rows(X2, n, n, n, orr.s, orr.beta, expsX, planesX, L.n_pad, L.k_pad,
+                                   elem_kind(o.executor), nullptr, nullptr, st));
+        DMP_CUDA(launch_product(orr, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, r3, nullptr,
+                                err, scratch, st));
+      }
+      std::swap(cur, alt);
+      std::swap(ldcur, ldalt);
+      DMP_CUDA(launch_energy(cur, ldcur, H, ldh, n, partials, state, st));
+      refined = true;
+    }
+  }
   if (cur != P) {
     DMP_CUDA(cudaMemcpy2DAsync(P, ldp * sizeof(double), cur, ldcur * sizeof(double), n * sizeof(double), n,
                                cudaMemcpyDeviceToDevice, st));
   }
   PurifyState fin;
+  int32_t err_end = 0;
   DMP_CUDA(cudaMemcpyAsync(&fin, state, sizeof(fin), cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaMemcpyAsync(&err_end, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DMP_CUDA(cudaStreamSynchronize(st));
+  if (err_end) return DMP_ERR_TIMEOUT;
   if (tape != nullptr) {
     TapeHeader h;
     std::memset(&h, 0, sizeof(h));
@@ -374,8 +429,10 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     info->iters = fin.iter;
     info->slices_used = o.s;
     info->executor_used = o.executor;
-    info->energy = fin.energy;
-    info->band_energy = 2.0 * fin.energy;
+    info->energy = refined ? fin.energy_refined : fin.energy;
+    info->band_energy = 2.0 * info->energy;
+    info->energy_unrefined = fin.energy;
+    info->refined = refined ? 1 : 0;
     info->idem = std::sqrt(fin.idem2);
     info->trace = fin.t1;
     info->c_last = fin.c;

@@ -250,6 +250,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     return DMP_ERR_INVALID_ARG;
   if (opts->mode != DMP_OZAKI_INT8 && opts->mode != DMP_OZAKI_BF16) return DMP_ERR_UNSUPPORTED;
   if (opts->executor != DMP_EXEC_AUTO && opts->executor != DMP_EXEC_TC) return DMP_ERR_UNSUPPORTED;
+  if (opts->refine_slices != 0) return DMP_ERR_UNSUPPORTED;  // no batched refinement step
   const int beta = opts->mode == DMP_OZAKI_BF16 ? 8 : 7;
   const int smax_mode = beta == 8 ? 9 : 10;
   if (opts->slices < 0 || opts->slices > smax_mode) return DMP_ERR_INVALID_ARG;
@@ -504,6 +505,8 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       I.c_last = f.c;
       I.h_min = f.h_min;
       I.h_max = f.h_max;
+      I.energy_unrefined = f.energy;
+      I.refined = 0;
     }
     worst = std::max(worst, f.status);
   }

@@ -44,6 +44,8 @@ struct PurifyState {
   int32_t done;     // nonzero once a stopping rule fired (kernels then skip work)
   int32_t nonfinite;
   int32_t branch;   // 1: c >= 1/2, 2: c < 1/2
+  // tr(P' H) of the refined matrix (refinement step only)
+  double energy_refined;
   // options copied for the device
   double tol, energy_tol;
   int32_t max_iter;
@@ -111,13 +113,18 @@ cudaError_t launch_gershgorin_init(const double* H, int64_t n, int64_t ldh, int6
                                    double* rowbuf, PurifyState* state, double* P, int64_t ldp,
                                    cudaStream_t st);
 size_t gershgorin_rowbuf_bytes(int64_t n);
+// Refinement step: the update weights of c = 1/2 (P' = 3 P^2 - 2 P^3), and
+// state->energy_refined = tr(P H) (deterministic, from the upper triangles).
+cudaError_t launch_refine_weights(PurifyState* state, cudaStream_t st);
+cudaError_t launch_energy(const double* P, int64_t ldp, const double* H, int64_t ldh, int64_t n, double* partials,
+                          PurifyState* state, cudaStream_t st);
 cudaError_t launch_measure(const double* P, int64_t ldp, const double* X2, int64_t ldx,
                            const double* H, int64_t ldh, int64_t n, double* partials,
                            PurifyState* state, cudaStream_t st);
 cudaError_t launch_copy_matrix(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t m,
                                int64_t n, cudaStream_t st);
 
-constexpr int kMeasureBlocks = 304;  // 2 x 152 SMs; fixed so sums are reproducible
+constexpr int kMeasureBlocks = 608;  // 4 x 152 SMs; fixed so sums are reproducible
 
 }  // namespace dmp
 

@@ -178,8 +178,11 @@ measure_kernel(const double* __restrict__ P, int64_t ldp, const double* __restri
                const double* __restrict__ H, int64_t ldh, int64_t n, double* __restrict__ part,
                const PurifyState* st) {
   if (st->done) return;
-  double u_px = 0.0, u_id = 0.0, u_ph = 0.0;
+  // four independent accumulator sets (entries j, j + 256, j + 512, j + 768 of
+  // a step) keep twelve loads in flight per thread; combined in order below
+  double a_px[4] = {0.0, 0.0, 0.0, 0.0}, a_id[4] = {0.0, 0.0, 0.0, 0.0}, a_ph[4] = {0.0, 0.0, 0.0, 0.0};
   double d_p = 0.0, d_x = 0.0, d_px = 0.0, d_id = 0.0, d_ph = 0.0;
+  const int64_t B = blockDim.x;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const double* pr = P + i * ldp;
     const double* xr = X2 + i * ldx;
@@ -192,13 +195,32 @@ measure_kernel(const double* __restrict__ P, int64_t ldp, const double* __restri
       d_id += (x - p) * (x - p);
       d_ph += p * h;
     }
-    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+    int64_t j = i + 1 + threadIdx.x;
+    for (; j + 3 * B < n; j += 4 * B) {
+      double p[4], x[4], h[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        p[u] = pr[j + u * B];
+        x[u] = xr[j + u * B];
+        h[u] = hr[j + u * B];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a_px[u] += p[u] * x[u];
+        a_id[u] += (x[u] - p[u]) * (x[u] - p[u]);
+        a_ph[u] += p[u] * h[u];
+      }
+    }
+    for (; j < n; j += B) {
       const double p = pr[j], x = xr[j], h = hr[j];
-      u_px += p * x;
-      u_id += (x - p) * (x - p);
-      u_ph += p * h;
+      a_px[0] += p * x;
+      a_id[0] += (x - p) * (x - p);
+      a_ph[0] += p * h;
     }
   }
+  const double u_px = (a_px[0] + a_px[1]) + (a_px[2] + a_px[3]);
+  const double u_id = (a_id[0] + a_id[1]) + (a_id[2] + a_id[3]);
+  const double u_ph = (a_ph[0] + a_ph[1]) + (a_ph[2] + a_ph[3]);
   __shared__ double red[8][8];
   double v[8] = {d_p, d_x, d_px, u_px, d_id, u_id, d_ph, u_ph};
 #pragma unroll
@@ -228,7 +250,65 @@ __global__ void measure_final_kernel(const double* __restrict__ part, int nblock
   if (threadIdx.x == 0) pm_decide(st, tot);
 }
 
+// The update weights of a McWeeny step (c = 1/2): alpha = 0, b2 = 3, b3 = -2.
+__global__ void refine_weights_kernel(PurifyState* st) {
+  st->alpha = 0.0;
+  st->b2 = 3.0;
+  st->b3 = -2.0;
+}
+
+// Per-block partial sums of tr(P H) over the upper triangle: [0] diagonal, [1] strictly upper.
+__global__ void __launch_bounds__(256)
+energy_kernel(const double* __restrict__ P, int64_t ldp, const double* __restrict__ H, int64_t ldh, int64_t n,
+              double* __restrict__ part) {
+  double d = 0.0, u = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double* pr = P + i * ldp;
+    const double* hr = H + i * ldh;
+    if (threadIdx.x == 0) d += pr[i] * hr[i];
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) u += pr[j] * hr[j];
+  }
+  d = warp_sum(d);
+  u = warp_sum(u);
+  __shared__ double red[8][2];
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = d;
+    red[threadIdx.x >> 5][1] = u;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+    part[static_cast<int64_t>(blockIdx.x) * 2 + threadIdx.x] = t;
+  }
+}
+
+__global__ void energy_final_kernel(const double* __restrict__ part, int nblocks, PurifyState* st) {
+  double d = 0.0, u = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    d += part[2 * b];
+    u += part[2 * b + 1];
+  }
+  st->energy_refined = d + 2.0 * u;
+}
+
 }  // namespace
+
+cudaError_t launch_refine_weights(PurifyState* state, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_OTHER, st);
+  refine_weights_kernel<<<1, 1, 0, st>>>(state);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const double* P, int64_t ldp, const double* H, int64_t ldh, int64_t n, double* partials,
+                          PurifyState* state, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_MEASURE, st);
+  energy_kernel<<<kMeasureBlocks, 256, 0, st>>>(P, ldp, H, ldh, n, partials);
+  energy_final_kernel<<<1, 1, 0, st>>>(partials, kMeasureBlocks, state);
+  count_launch(2);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gershgorin_init(const double* H, int64_t n, int64_t ldh, int64_t n_occ,
                                    double* rowbuf, PurifyState* state, double* P, int64_t ldp,

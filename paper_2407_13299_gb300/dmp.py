@@ -33,17 +33,19 @@ class DmpError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("slices", ctypes.c_int32), ("executor", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("tol", ctypes.c_double), ("energy_tol", ctypes.c_double)]
+                ("flags", ctypes.c_int32), ("tol", ctypes.c_double), ("energy_tol", ctypes.c_double),
+                ("refine_slices", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("slices_used", ctypes.c_int32),
                 ("executor_used", ctypes.c_int32), ("energy", ctypes.c_double),
                 ("band_energy", ctypes.c_double), ("idem", ctypes.c_double), ("trace", ctypes.c_double),
-                ("c_last", ctypes.c_double), ("h_min", ctypes.c_double), ("h_max", ctypes.c_double)]
+                ("c_last", ctypes.c_double), ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
+                ("energy_unrefined", ctypes.c_double), ("refined", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
 _lib = None
@@ -156,9 +158,11 @@ def _require_cuda(*ts):
 
 
 def make_opts(mode="int8", slices=7, executor="auto", tol=1e-10, energy_tol=0.0, max_iter=100,
-              checkpoint_every=8) -> Opts:
+              checkpoint_every=8, refine=0) -> Opts:
+    """refine: 0 none, -1 a McWeeny refinement step with FP64 products, s_r > 0
+    one with Ozaki products of s_r slices (see dm_purify)."""
     return Opts(MODES[mode], int(slices) if mode != "fp64" else 0, EXECUTORS[executor], int(max_iter),
-                int(checkpoint_every), 0, float(tol), float(energy_tol))
+                int(checkpoint_every), 0, float(tol), float(energy_tol), int(refine), 0)
 
 
 def workspace(nbytes: int, device=None) -> torch.Tensor:
@@ -178,15 +182,16 @@ def tape_bytes(n: int, opts: Opts) -> int:
 
 
 def purify(H: torch.Tensor, n_occ: int, mode="int8", slices=7, executor="auto", tol=1e-10,
-           energy_tol=0.0, max_iter=100, P=None, ws=None, tape=None, stream=None, checkpoint_every=8):
+           energy_tol=0.0, max_iter=100, P=None, ws=None, tape=None, stream=None, checkpoint_every=8, refine=0):
     """dm_purify on a float64 CUDA tensor H. Returns (P, info dict).
 
     `ws`, `P` and `tape` may be passed preallocated (see purify_workspace_bytes,
-    tape_bytes) so that repeated calls allocate nothing.
+    tape_bytes) so that repeated calls allocate nothing. `refine` adds the
+    McWeeny refinement step (make_opts).
     """
     _require_cuda(H)
     n = H.shape[0]
-    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every)
+    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every, refine)
     if P is None:
         P = torch.empty_like(H)
     if ws is None:

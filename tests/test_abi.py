@@ -4,6 +4,7 @@ include/dmp.h declares. No compute call is made here."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -46,11 +47,27 @@ def test_binding_covers_the_header(built):
     assert dmp.status_str(-5) == "DMP_ERR_UNSUPPORTED"
 
 
-def test_struct_layouts_match_header(built):
+def test_struct_layouts_match_header(built, tmp_path):
+    """Every field offset and the size of dmp_opts and dmp_info, as a C compiler
+    lays them out from include/dmp.h, equal the binding's ctypes layout."""
     from paper_2407_13299_gb300 import dmp
 
-    assert ctypes.sizeof(dmp.Opts) == 6 * 4 + 2 * 8
-    assert ctypes.sizeof(dmp.Info) == 4 * 4 + 7 * 8
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dmp.h"', "int main(void) {"]
+    for cname, cls in (("dmp_opts", dmp.Opts), ("dmp_info", dmp.Info)):
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                            check=True).stdout.splitlines())
+    for cname, cls in (("dmp_opts", dmp.Opts), ("dmp_info", dmp.Info)):
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(cls)
+        for field, _ in cls._fields_:
+            assert int(got[f"{cname} {field}"]) == getattr(cls, field).offset, (cname, field)
 
 
 def test_workspace_sizes_are_host_side(built):
