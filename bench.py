@@ -39,7 +39,7 @@ UNIT = "s"
 REL_ENERGY_TARGET = 1e-8
 # (loop slices, refinement-step slices) the GPU arm selects on the default
 # workload; the reference arm times the oracle in the same configuration
-REFERENCE_CONFIG = (5, 9)
+REFERENCE_CONFIG = (5, 8)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -89,9 +89,11 @@ def load_peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
-def kernel_traffic(kernel_file, summary):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current source of the kernel (matching sha256 prefix); else None."""
+def kernel_traffic(kernel_file, summary, mix):
+    """DRAM bytes per launch of the product kernel from a committed ncu summary
+    taken on the current source of the kernel (matching sha256 prefix), averaged
+    over `mix` = {slice count: launches}; None if the summary is stale or lacks
+    a slice count of the mix."""
     src = os.path.join(ROOT, "paper_2407_13299_gb300", "csrc", kernel_file)
     path = os.path.join(ROOT, "profiles", summary)
     if not (os.path.exists(src) and os.path.exists(path)):
@@ -99,15 +101,16 @@ def kernel_traffic(kernel_file, summary):
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256")):
+        if ":" in line and line.strip().lstrip("- ").startswith(("traffic_bytes_per_launch", "source_sha256")):
             k, v = line.split(":", 1)
             vals[k.strip().lstrip("- ")] = v.strip().split()[0]
     if vals.get("source_sha256") != digest:
         return None
     try:
-        return float(vals["traffic_bytes_per_launch"])
+        total = sum(cnt * float(vals[f"traffic_bytes_per_launch_s{s}"]) for s, cnt in mix.items())
     except (KeyError, ValueError):
         return None
+    return total / max(sum(mix.values()), 1)
 
 
 class ClockSampler:
@@ -308,8 +311,9 @@ def run_ours(args):
     # ---- configuration (untimed): the cheapest Ozaki-INT8 setting whose band energy
     # meets the target. Candidates in order of product work: s slices in the loop,
     # with or without the paper's refinement step (one McWeeny step after the loop,
-    # Sec. "Precision Requirements Sweep", with FP64-level products of 9 slices).
-    REFINE_SLICES = 9
+    # Sec. "Precision Requirements Sweep", in full double precision: products of 8
+    # slices, 56 digit bits >= the 53 of FP64).
+    REFINE_SLICES = 8
     fixed_refine = None if args.refine in ("auto", "off") else int(args.refine)
     if args.slices:
         cands = [(args.slices, fixed_refine or 0)]
@@ -393,7 +397,11 @@ def run_ours(args):
     avg_launch_s = (prod_ms / 1e3) / max(prod_n, 1)
     achieved = flops_per_launch / avg_launch_s / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
-    traffic = kernel_traffic("gemm_tc.cu", "ozaki_tc_kernel_n8192.md") if args.executor == "tc" else None
+    mix = {s: 2 * info["iters"] + 1}
+    if refined and refine > 0:
+        mix[refine] = mix.get(refine, 0) + 2
+    traffic = kernel_traffic("gemm_tc.cu", "ozaki_tc_kernel_n8192.md", mix) \
+        if args.executor == "tc" and n == 8192 else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "kernel": "ozaki_tc_kernel<256,false,true> (CTA pairs, 2-SM MMA)" if args.executor == "tc" else

@@ -237,13 +237,29 @@ measure_kernel(const double* __restrict__ P, int64_t ldp, const double* __restri
   }
 }
 
-// Sum the partials in fixed order and apply the stopping rules; one CTA.
-__global__ void measure_final_kernel(const double* __restrict__ part, int nblocks, PurifyState* st) {
+// Sum the partials in a fixed order and apply the stopping rules; one CTA of
+// 256 threads: thread t sums blocks t, t + 256, ... of all eight measures,
+// then warp trees and the eight warps in order.
+__global__ void __launch_bounds__(256)
+measure_final_kernel(const double* __restrict__ part, int nblocks, PurifyState* st) {
   if (st->done) return;
+  double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] += part[static_cast<int64_t>(b) * 8 + q];
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = warp_sum(v[q]);
+  __shared__ double red[8][8];
   __shared__ double tot[8];
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[threadIdx.x >> 5][q] = v[q];
+  }
+  __syncthreads();
   if (threadIdx.x < 8) {
     double t = 0.0;
-    for (int b = 0; b < nblocks; ++b) t += part[static_cast<int64_t>(b) * 8 + threadIdx.x];
+    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
     tot[threadIdx.x] = t;
   }
   __syncthreads();
@@ -283,13 +299,29 @@ energy_kernel(const double* __restrict__ P, int64_t ldp, const double* __restric
   }
 }
 
-__global__ void energy_final_kernel(const double* __restrict__ part, int nblocks, PurifyState* st) {
+__global__ void __launch_bounds__(256)
+energy_final_kernel(const double* __restrict__ part, int nblocks, PurifyState* st) {
   double d = 0.0, u = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
     d += part[2 * b];
     u += part[2 * b + 1];
   }
-  st->energy_refined = d + 2.0 * u;
+  d = warp_sum(d);
+  u = warp_sum(u);
+  __shared__ double red[8][2];
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5][0] = d;
+    red[threadIdx.x >> 5][1] = u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double td = 0.0, tu = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      td += red[w][0];
+      tu += red[w][1];
+    }
+    st->energy_refined = td + 2.0 * tu;
+  }
 }
 
 }  // namespace
@@ -305,7 +337,7 @@ cudaError_t launch_energy(const double* P, int64_t ldp, const double* H, int64_t
                           PurifyState* state, cudaStream_t st) {
   ProfScope prof(DMP_PROF_MEASURE, st);
   energy_kernel<<<kMeasureBlocks, 256, 0, st>>>(P, ldp, H, ldh, n, partials);
-  energy_final_kernel<<<1, 1, 0, st>>>(partials, kMeasureBlocks, state);
+  energy_final_kernel<<<1, 256, 0, st>>>(partials, kMeasureBlocks, state);
   count_launch(2);
   return cudaGetLastError();
 }
@@ -339,7 +371,7 @@ cudaError_t launch_measure(const double* P, int64_t ldp, const double* X2, int64
                            PurifyState* state, cudaStream_t st) {
   ProfScope prof(DMP_PROF_MEASURE, st);
   measure_kernel<<<kMeasureBlocks, 256, 0, st>>>(P, ldp, X2, ldx, H, ldh, n, partials, state);
-  measure_final_kernel<<<1, 32, 0, st>>>(partials, kMeasureBlocks, state);
+  measure_final_kernel<<<1, 256, 0, st>>>(partials, kMeasureBlocks, state);
   count_launch(2);
   return cudaGetLastError();
 }
