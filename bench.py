@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--fp64", default="full", choices=["full", "skip"], help="time the FP64 purification once")
     ap.add_argument("--cpu-samples", type=int, default=5, help="oracle samples for cpu_baseline (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--targets", choices=("on", "off"), default="on",
+                    help="also time INT8 and BF16 at 1e-5 and 1e-8 (untimed search, 2 timed runs each)")
     ap.add_argument("--refine", default="auto",
                     help="refinement step after the loop: auto (pick the cheapest setting meeting the target, "
                          "with or without it), off, or the slice count of its products (-1: FP64)")
@@ -326,8 +328,8 @@ def run_ours(args):
                  (8, 0), (9, 0)]
     s, refine = cands[-1]
     tune = []
-    ws = dmp.workspace(dmp.purify_workspace_bytes(n, dmp.make_opts("int8", 9, args.executor, refine=REFINE_SLICES)),
-                       dev)
+    ws = dmp.workspace(max(dmp.purify_workspace_bytes(n, dmp.make_opts("int8", 9, args.executor, refine=9)),
+                           dmp.purify_workspace_bytes(n, dmp.make_opts("bf16", 9, args.executor, refine=9))), dev)
     P = torch.empty_like(H)
     for cs, cr in cands:
         _, info = dmp.purify(H, n_occ, mode="int8", slices=cs, executor=args.executor, refine=cr, P=P, ws=ws)
@@ -457,6 +459,34 @@ def run_ours(args):
         plain = {"slices": cs, "value": a.elapsed_time(b) / 2e3, "unit": UNIT, "rel_energy_error": prel,
                  "iters": pi["iters"]}
 
+    # ---- the other targets of this workload: Ozaki-INT8 and Ozaki-BF16 at 1e-5
+    # and 1e-8 relative band-energy error, each with its cheapest setting
+    # (candidates by product work: 101 loop products of p(s) pairs, plus about 72
+    # pair-products for the refinement; refinement products of 56 digit bits)
+    targets = []
+    if args.targets == "on" and not args.slices:
+        for mode, beta in (("int8", 7), ("bf16", 8)):
+            r_s = 8 if beta == 7 else 7
+            cand = sorted(((cs, cr) for cs in range(3, 10 if beta == 7 else 9) for cr in (0, r_s)),
+                          key=lambda c: 101 * c[0] * (c[0] + 1) // 2 + (72 if c[1] else 0))
+            for target in (1e-5, 1e-8):
+                for cs, cr in cand:
+                    _, ti = dmp.purify(H, n_occ, mode=mode, slices=cs, executor=args.executor, refine=cr, P=P, ws=ws)
+                    trel = abs(ti["energy"] - E_star) / abs(E_star)
+                    if trel <= target:
+                        break
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(2):
+                    dmp.purify(H, n_occ, mode=mode, slices=cs, executor=args.executor, refine=cr, P=P, ws=ws)
+                b.record(stream)
+                torch.cuda.synchronize()
+                targets.append({"mode": f"ozaki-{mode}", "target": target, "slices": cs, "refine_slices": cr,
+                                "value": a.elapsed_time(b) / 2e3, "unit": UNIT, "rel_energy_error": trel,
+                                "iters": ti["iters"]})
+
     # ---- FP64 purification on the same GPU (once)
     fp64 = None
     if args.fp64 == "full":
@@ -503,7 +533,7 @@ def run_ours(args):
                        "iters": info["iters"], "status": dmp.status_str(info["status"]),
                        "rel_energy_error": rel_energy, "rel_energy_error_unrefined":
                            abs(info["energy_unrefined"] - E_star) / abs(E_star),
-                       "idempotency": info["idem"], "without_refinement": plain,
+                       "idempotency": info["idem"], "without_refinement": plain, "targets": targets,
                        "l2": (f"inputs larger than L2 (H {n * n * 8 / 2**20:.0f} MiB, digit planes "
                               f"{2 * s * n * n * 2 / 2**30:.2f} GiB)"), "slice_tuning": tune,
                        "replicas": world},
