@@ -347,6 +347,29 @@ def run_ours(args):
         _, info = step()
     torch.cuda.synchronize()
 
+    # ---- end to end through the public API with host buffers
+    H_host = H.to("cpu").pin_memory()
+    P_host = torch.empty_like(H_host).pin_memory()
+    e2e_times = []
+    # (measured after the warm-up steps and before the timed region, so that both
+    # run in the same warm state of the GPU; the first call through the host path,
+    # whose device copy of H comes from torch's caching allocator, is untimed)
+    dmp.purify_host(H_host, n_occ, out=P_host, mode="int8", slices=s, executor=args.executor, ws=ws, P=P,
+                    refine=refine)
+    torch.cuda.synchronize()
+    for _ in range(max(args.e2e_steps, 1)):
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dmp.purify_host(H_host, n_occ, out=P_host, mode="int8", slices=s, executor=args.executor, ws=ws, P=P,
+                        refine=refine)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    te = torch.tensor([statistics.median(e2e_times)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": float(te.item()), "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8}
+
     # ---- timed region: K full purifications, H resident in HBM (512 MiB > L2)
     dmp.profile_enable(True)
     dmp.profile_reset()
@@ -414,30 +437,6 @@ def run_ours(args):
                 "launch_mix": f"{2 * info['iters'] + 1} x s={s}" + (f" + 2 x s={refine}" if refined else "") +
                               " per purification"}
 
-    # ---- end to end through the public API with host buffers
-    H_host = H.to("cpu").pin_memory()
-    P_host = torch.empty_like(H_host).pin_memory()
-    e2e_times = []
-    # untimed warm-up after the host work above (pinning 1 GiB of host buffers):
-    # two device-resident calls, then one call through the host path, whose
-    # device copy of H comes from torch's caching allocator (a one-time cudaMalloc)
-    for _ in range(2):
-        step()
-    dmp.purify_host(H_host, n_occ, out=P_host, mode="int8", slices=s, executor=args.executor, ws=ws, P=P,
-                    refine=refine)
-    torch.cuda.synchronize()
-    for _ in range(max(args.e2e_steps, 1)):
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dmp.purify_host(H_host, n_occ, out=P_host, mode="int8", slices=s, executor=args.executor, ws=ws, P=P,
-                        refine=refine)
-        torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-    te = torch.tensor([statistics.median(e2e_times)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": float(te.item()), "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8}
 
     # ---- the cheapest setting without the refinement step, timed the same way (2 steps)
     plain = None
