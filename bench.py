@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=8192, help="matrix size (8192 is the benchmark workload)")
+    ap.add_argument("--n", "--size", dest="n", type=int, default=8192, help="matrix size (8192 is the benchmark workload)")
     ap.add_argument("--slices", type=int, default=0, help="0: smallest s >= 6 meeting the energy target")
     ap.add_argument("--executor", default="tc", choices=["tc", "imma"])
     ap.add_argument("--fp64", default="full", choices=["full", "skip"], help="time the FP64 purification once")
@@ -68,6 +68,19 @@ def parse_args():
 
 
 # ---------------------------------------------------------------- helpers
+def max_over_ranks(x, device=None):
+    """The largest of x over all ranks (x on a single process). One replica
+    per GPU, so the job's time per step is that of its slowest rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_params(n):
     if n == 8192:
         from synth import CONFIGS
@@ -365,10 +378,8 @@ def run_ours(args):
                         refine=refine)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-    te = torch.tensor([statistics.median(e2e_times)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": float(te.item()), "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8}
+    e2e = {"value": max_over_ranks(statistics.median(e2e_times), dev), "unit": UNIT,
+           "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8}
 
     # ---- timed region: K full purifications, H resident in HBM (512 MiB > L2)
     dmp.profile_enable(True)
@@ -393,11 +404,7 @@ def run_ours(args):
     launches = dmp.launch_count() - launches0
     clk = clocks.stop() if clocks else None
     dmp.profile_enable(False)
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dev)
     per_step = elapsed / args.steps
     prod_ms, prod_n = dmp.profile_read(dmp.PROF_PRODUCT)
     split_ms, split_n = dmp.profile_read(dmp.PROF_SPLIT)
