@@ -19,8 +19,10 @@ Modules
               Purification", "Implementation Details", "Error Evaluation
               Criteria")
   adjoint  -- reverse mode through the purification iterations
+  variants -- SP2 and TRS4 purification (TRS4 is the algorithm the paper runs
+              through NTPoly, Sec. "Implementation Details")
 
 Parity status per function is stated in each module header.
 """
 
-from . import adjoint, ozaki, purify  # noqa: F401
+from . import adjoint, ozaki, purify, variants  # noqa: F401
