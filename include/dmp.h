@@ -74,6 +74,26 @@ enum {
  * because the converged projector does not depend on P_0. */
 enum { DMP_FLAG_BOUNDS_CONSTANT = 1 };
 
+/*
+ * Purification method (dmp_opts.method).
+ * DMP_METHOD_PM    canonical purification (Palser-Manolopoulos; the default).
+ * DMP_METHOD_TRS4  trace-resetting fourth-order purification, the recursion the
+ *                  paper runs through NTPoly (Sec. "Implementation Details"):
+ *                  X_0 = (h_max I - H)/(h_max - h_min); gamma = (n_occ - tr F)
+ *                  / tr G with F = X^2 (4X - 3X^2), G = X^2 (I - X)^2; X' =
+ *                  F + gamma G = X^2 Z, Z = gamma I + (4 - 2 gamma) X +
+ *                  (gamma - 3) X^2, for gamma in [0, 6], else an SP2 step
+ *                  (2X - X^2 above 6, X^2 below 0). Two products per step.
+ * DMP_METHOD_SP2   second-order spectral projection: X' = X^2 or 2X - X^2,
+ *                  whichever brings tr X' closer to n_occ. One product per step.
+ * For TRS4 and SP2, tr G is taken as ||X^2 - X||_F^2 and the stopping rules
+ * are: ||X^2 - X||_F < tol (DMP_OK); k >= 2, the value two steps earlier
+ * below 1 and not above the current one (the rounding floor,
+ * DMP_C_OUT_OF_RANGE); k == max_iter (DMP_NOT_CONVERGED). No energy rules.
+ * They take no tape and are not offered in the batched call.
+ */
+enum { DMP_METHOD_PM = 0, DMP_METHOD_TRS4 = 1, DMP_METHOD_SP2 = 2 };
+
 /* Options. Zero-initialise and set what you need; zeros select defaults. */
 typedef struct {
   int32_t mode;             /* DMP_FP64 / DMP_OZAKI_INT8 / DMP_OZAKI_BF16           */
@@ -86,7 +106,7 @@ typedef struct {
   double energy_tol;        /* optional |change of Tr(HK)| threshold; 0 = off        */
   int32_t refine_slices;    /* refinement after the loop (see dm_purify): 0 off,
                                -1 FP64 products, s_r > 0 Ozaki products of s_r slices */
-  int32_t reserved;         /* 0 */
+  int32_t method;           /* DMP_METHOD_* (0: canonical purification)              */
 } dmp_opts;
 
 /* Per-run report, filled when the host pointer is non-NULL (the call then
@@ -100,7 +120,8 @@ typedef struct {
   double band_energy;  /* Tr(H K) = 2 tr(P H), the paper's energy                */
   double idem;         /* ||P^2 - P||_F of the returned P                        */
   double trace;        /* tr(P)                                                  */
-  double c_last;       /* last purification coefficient                          */
+  double c_last;       /* last coefficient: c (canonical), gamma (TRS4), 1 or 0 for a
+                          squaring or a 2X - X^2 step (SP2)                       */
   double h_min, h_max; /* Gershgorin bounds used for the initial guess          */
   double energy_unrefined; /* tr(P H) before the refinement step (= energy if none) */
   int32_t refined;     /* 1 if the refinement step was applied                   */

@@ -34,6 +34,7 @@ struct Opts {
   int mode, s, beta, executor, max_iter, every;
   double tol, energy_tol;
   int refine;  // 0 off, -1 FP64 products, > 0 Ozaki slices of the refinement step
+  int method;  // DMP_METHOD_*
 };
 
 int normalize(const dmp_opts* o, Opts& out) {
@@ -62,6 +63,8 @@ int normalize(const dmp_opts* o, Opts& out) {
   out.tol = o->tol == 0.0 ? 1e-10 : o->tol;
   out.energy_tol = o->energy_tol;
   if (!(out.tol >= 0.0) || !(out.energy_tol >= 0.0)) return DMP_ERR_INVALID_ARG;
+  out.method = o->method;
+  if (out.method < DMP_METHOD_PM || out.method > DMP_METHOD_SP2) return DMP_ERR_INVALID_ARG;
   out.refine = o->refine_slices;
   if (out.refine != 0 && out.mode == DMP_FP64) out.refine = -1;
   if (out.refine < -1 || out.refine > (out.beta == 8 ? 9 : 10)) return DMP_ERR_INVALID_ARG;
@@ -102,7 +105,7 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
   L.n_pad = round_up(n, o.mode == DMP_FP64 ? kTileM : row_pad(o.executor));
   L.k_pad = round_up(n, kPadK);
   L.state = c.take(sizeof(PurifyState));
-  L.partials = c.take(static_cast<size_t>(kMeasureBlocks) * 8 * sizeof(double));
+  L.partials = c.take(static_cast<size_t>(kMeasureBlocks) * 10 * sizeof(double));  // 8 measures, 10 for SP2 / TRS4
   L.rowbuf = c.take(gershgorin_rowbuf_bytes(n));
   L.expsP = c.take(static_cast<size_t>(L.n_pad) * sizeof(int32_t));
   L.expsX = c.take(static_cast<size_t>(L.n_pad) * sizeof(int32_t));
@@ -261,7 +264,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     return DMP_ERR_UNSUPPORTED;
   if (o.refine > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.refine, o.beta))
     return DMP_ERR_UNSUPPORTED;
-  if (o.refine != 0 && tape != nullptr) return DMP_ERR_UNSUPPORTED;
+  if ((o.refine != 0 || o.method != DMP_METHOD_PM) && tape != nullptr) return DMP_ERR_UNSUPPORTED;
   const PurifyLayout L = purify_layout(n, o);
   if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
   TapeLayout TL{};
@@ -290,6 +293,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   init.energy_tol = o.energy_tol;
   init.max_iter = o.max_iter;
   init.status = DMP_NOT_CONVERGED;
+  init.method = o.method;
   DMP_CUDA(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st));
   DMP_CUDA(launch_gershgorin_init(H, n, ldh, n_occ, rowbuf, state, P, ldp, st));
 
@@ -319,13 +323,44 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
       DMP_CUDA(launch_product(o, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e2, done,
                               err, scratch, st));
     }
-    DMP_CUDA(launch_measure(cur, ldcur, X2, n, H, ldh, n, partials, state, st));
-    int32_t flags[2] = {0, 0};
+    if (o.method == DMP_METHOD_PM) {
+      DMP_CUDA(launch_measure(cur, ldcur, X2, n, H, ldh, n, partials, state, st));
+    } else {
+      DMP_CUDA(launch_measure_variant(cur, ldcur, X2, n, H, ldh, n, partials, state, st));
+    }
+    int32_t flags[3] = {0, 0, 0};
     DMP_CUDA(cudaMemcpyAsync(&flags[0], &state->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     DMP_CUDA(cudaMemcpyAsync(&flags[1], err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DMP_CUDA(cudaMemcpyAsync(&flags[2], &state->step_kind, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     DMP_CUDA(cudaStreamSynchronize(st));
     if (flags[1]) return DMP_ERR_TIMEOUT;
     if (flags[0]) break;
+    if (o.method != DMP_METHOD_PM) {
+      // SP2 / TRS4 step (the weights are on the device)
+      if (flags[2] == 0) {
+        DMP_CUDA(launch_axpby(cur, ldcur, X2, n, alt, ldalt, n, state, st));
+        std::swap(cur, alt);
+        std::swap(ldcur, ldalt);
+      } else {
+        // X' = X2 Z: Z into alt, then the symmetric product written over X
+        DMP_CUDA(launch_trs4_z(cur, ldcur, X2, n, alt, ldalt, n, state, st));
+        EpiArgs ez{};
+        ez.kind = EPI_SYM_STORE;
+        ez.C = cur;
+        ez.ldc = ldcur;
+        if (o.mode == DMP_FP64) {
+          DMP_CUDA(launch_gemm_f64(X2, n, alt, ldalt, n, n, n, 1, ez, done, st));
+        } else {
+          DMP_CUDA(launch_split_rows(X2, n, n, n, o.s, o.beta, expsX, planesX, L.n_pad, L.k_pad,
+                                     elem_kind(o.executor), nullptr, done, st));
+          DMP_CUDA(launch_split_rows(alt, n, n, ldalt, o.s, o.beta, expsP, planesP, L.n_pad, L.k_pad,
+                                     elem_kind(o.executor), nullptr, done, st));
+          DMP_CUDA(launch_product(o, planesX, planesP, expsX, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, ez, done,
+                                  err, scratch, st));
+        }
+      }
+      continue;
+    }
     if (tape != nullptr) {
       DMP_CUDA(cudaMemcpyAsync(tape_c + k, &state->c, sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
@@ -598,6 +633,7 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
   Opts o;
   int rc = normalize(opts, o);
   if (rc != DMP_OK) return rc;
+  if (o.method != DMP_METHOD_PM || o.refine != 0) return DMP_ERR_UNSUPPORTED;  // the tape is canonical only
   if (H == nullptr || tape == nullptr || dLdP == nullptr || dLdH == nullptr || ws == nullptr)
     return DMP_ERR_INVALID_ARG;
   if (n < 2 || n_occ <= 0 || n_occ >= n) return DMP_ERR_INVALID_ARG;

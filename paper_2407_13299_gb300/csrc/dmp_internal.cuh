@@ -46,6 +46,14 @@ struct PurifyState {
   int32_t branch;   // 1: c >= 1/2, 2: c < 1/2
   // tr(P' H) of the refined matrix (refinement step only)
   double energy_refined;
+  // method (DMP_METHOD_*) and the per-step data of SP2 / TRS4
+  int32_t method;
+  int32_t step_kind;      // 0: X' = alpha X + b2 X2 (elementwise); 1: X' = X2 Z (TRS4 product)
+  double t4;              // tr X^4 = ||X2||_F^2
+  double idem_hist[3];    // ||X2 - X||_F of the last three iterates, newest first
+  double zd, zx, zx2;     // TRS4: Z = zd I + zx X + zx2 X2
+  double n_occ_d;         // n_occ
+  double p0_scale, p0_shift;  // initial guess -p0_scale H + p0_shift I (canonical: built as in the method)
   // options copied for the device
   double tol, energy_tol;
   int32_t max_iter;
@@ -118,6 +126,15 @@ size_t gershgorin_rowbuf_bytes(int64_t n);
 cudaError_t launch_refine_weights(PurifyState* state, cudaStream_t st);
 cudaError_t launch_energy(const double* P, int64_t ldp, const double* H, int64_t ldh, int64_t n, double* partials,
                           PurifyState* state, cudaStream_t st);
+// SP2 / TRS4: measures with tr X^4 and variant_decide; the elementwise step
+// Out = alpha X + b2 X2; the TRS4 factor Z = zd I + zx X + zx2 X2 (weights from
+// the state; full n x n, so the results are exactly symmetric as X and X2 are).
+cudaError_t launch_measure_variant(const double* X, int64_t ldx, const double* X2, int64_t ldx2, const double* H,
+                                   int64_t ldh, int64_t n, double* partials, PurifyState* state, cudaStream_t st);
+cudaError_t launch_axpby(const double* X, int64_t ldx, const double* X2, int64_t ldx2, double* out, int64_t ldo,
+                         int64_t n, const PurifyState* state, cudaStream_t st);
+cudaError_t launch_trs4_z(const double* X, int64_t ldx, const double* X2, int64_t ldx2, double* out, int64_t ldo,
+                          int64_t n, const PurifyState* state, cudaStream_t st);
 cudaError_t launch_measure(const double* P, int64_t ldp, const double* X2, int64_t ldx,
                            const double* H, int64_t ldh, int64_t n, double* partials,
                            PurifyState* state, cudaStream_t st);
@@ -244,6 +261,7 @@ namespace dmp {
 // the measures of the current iterate (diagonal/strict-upper partial sums:
 // tot = {tr P, tr X2, diag PX2, upper PX2, diag (X2-P)^2, upper (X2-P)^2,
 // diag PH, upper PH}). Sets status/done, or c and the update weights.
+// (SP2 / TRS4 use variant_decide below.)
 __device__ __forceinline__ void pm_decide(PurifyState* st, const double* tot) {
   const double t1 = tot[0], t2 = tot[1];
   const double t3 = tot[2] + 2.0 * tot[3];
@@ -309,6 +327,80 @@ __device__ __forceinline__ void pm_decide(PurifyState* st, const double* tot) {
     st->b2 = (1.0 + c) / (1.0 - c);
     st->b3 = -1.0 / (1.0 - c);
     st->branch = 2;
+  }
+  st->iter = k + 1;
+}
+
+// SP2 / TRS4 stopping rules and step (the cited recursions; readings as in the
+// oracle): tot as for pm_decide plus {diag X2^2, upper X2^2}. Rules on X_k:
+// ||X2 - X|| < tol -> DMP_OK; k >= 2, the value two steps earlier below 1 and
+// not above the current one -> DMP_C_OUT_OF_RANGE (rounding floor); k ==
+// max_iter -> DMP_NOT_CONVERGED. Else the step: SP2 squares or takes 2X - X2,
+// whichever brings the trace closer to n_occ; TRS4 takes gamma = (n_occ - tr F)
+// / tr G with tr F = 4 tr X^3 - 3 tr X^4 and tr G = ||X2 - X||^2, SP2 steps for
+// gamma outside [0, 6], else X' = X2 Z. c is gamma (TRS4) or 1 / 0 for a
+// squaring / 2X - X2 step (SP2).
+__device__ __forceinline__ void variant_decide(PurifyState* st, const double* tot) {
+  const double t1 = tot[0], t2 = tot[1];
+  const double t3 = tot[2] + 2.0 * tot[3];
+  const double idem2 = tot[4] + 2.0 * tot[5];
+  const double energy = tot[6] + 2.0 * tot[7];
+  const double t4 = tot[8] + 2.0 * tot[9];
+  st->t1 = t1;
+  st->t2 = t2;
+  st->t3 = t3;
+  st->t4 = t4;
+  st->idem2 = idem2;
+  st->energy = energy;
+  if (!isfinite(t1) || !isfinite(t2) || !isfinite(t3) || !isfinite(t4) || !isfinite(idem2) ||
+      !isfinite(energy)) {
+    st->nonfinite = 1;
+    st->status = DMP_ERR_NONFINITE;
+    st->done = 1;
+    return;
+  }
+  const int k = st->iter;
+  const double idem = sqrt(idem2);
+  st->idem_hist[2] = st->idem_hist[1];
+  st->idem_hist[1] = st->idem_hist[0];
+  st->idem_hist[0] = idem;
+  if (idem < st->tol) {
+    st->status = DMP_OK;
+    st->done = 1;
+    return;
+  }
+  if (k >= 2 && st->idem_hist[2] < 1.0 && idem >= st->idem_hist[2]) {
+    st->status = DMP_C_OUT_OF_RANGE;
+    st->done = 1;
+    return;
+  }
+  if (k >= st->max_iter) {
+    st->status = DMP_NOT_CONVERGED;
+    st->done = 1;
+    return;
+  }
+  const double N = st->n_occ_d;
+  st->step_kind = 0;
+  if (st->method == DMP_METHOD_SP2) {
+    const bool sq = fabs(t2 - N) <= fabs(2.0 * t1 - t2 - N);
+    st->alpha = sq ? 0.0 : 2.0;
+    st->b2 = sq ? 1.0 : -1.0;
+    st->c = sq ? 1.0 : 0.0;
+  } else {
+    const double gamma = (N - (4.0 * t3 - 3.0 * t4)) / idem2;
+    st->c = gamma;
+    if (gamma > 6.0) {
+      st->alpha = 2.0;
+      st->b2 = -1.0;
+    } else if (gamma < 0.0) {
+      st->alpha = 0.0;
+      st->b2 = 1.0;
+    } else {
+      st->step_kind = 1;
+      st->zd = gamma;
+      st->zx = 4.0 - 2.0 * gamma;
+      st->zx2 = gamma - 3.0;
+    }
   }
   st->iter = k + 1;
 }

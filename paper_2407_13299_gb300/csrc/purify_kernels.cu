@@ -9,6 +9,8 @@
 //
 // Reductions are deterministic: fixed grid, fixed per-thread order, fixed tree.
 
+#include <algorithm>
+
 #include "dmp_internal.cuh"
 
 namespace dmp {
@@ -122,6 +124,7 @@ gersh_final_kernel(int64_t n, int64_t n_occ, const double* __restrict__ U, const
       st->lam = 0.0;
       return;
     }
+    st->n_occ_d = static_cast<double>(n_occ);
     const double lam1 = static_cast<double>(n_occ) / (s_hi[0] - mu);
     const double lam2 = static_cast<double>(n - n_occ) / (mu - s_lo[0]);
     st->lam_branch = lam1 <= lam2 ? 1 : 2;
@@ -137,6 +140,9 @@ __global__ void p0_kernel(const double* __restrict__ H, int64_t n, int64_t ldh, 
   upper_tile(blockIdx.x, T, bi, bj);
   const double dn = static_cast<double>(n);
   const double a = st->lam / dn, mu = st->mu, occ = static_cast<double>(n_occ) / dn;
+  // SP2 / TRS4: X_0 = (h_max I - H) / (h_max - h_min)
+  const bool var = st->method != DMP_METHOD_PM;
+  const double hmax = st->h_max, width = st->h_max - st->h_min;
   const int64_t r0 = static_cast<int64_t>(bi) * 32, c0 = static_cast<int64_t>(bj) * 32;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
     const int64_t r = r0 + y, c = c0 + threadIdx.x;
@@ -151,9 +157,13 @@ __global__ void p0_kernel(const double* __restrict__ H, int64_t n, int64_t ldh, 
       if (bi == bj) {
         // on the diagonal tile the lower half takes the mirror of the upper half
         const double h = (y <= x) ? tile[y][x] : tile[x][y];
-        v = (r == c) ? a * (mu - h) + occ : -a * h;
+        if (var) {
+          v = (r == c) ? (hmax - h) / width : -h / width;
+        } else {
+          v = (r == c) ? a * (mu - h) + occ : -a * h;
+        }
       } else {
-        v = -a * tile[y][x];
+        v = var ? -tile[y][x] / width : -a * tile[y][x];
       }
       P[r * ldp + c] = v;
     }
@@ -162,7 +172,7 @@ __global__ void p0_kernel(const double* __restrict__ H, int64_t n, int64_t ldh, 
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
       // write the transposed tile: P[c0 + y][r0 + x] = -a H[r0 + x][c0 + y]
       const int64_t r = c0 + y, c = r0 + threadIdx.x;
-      if (r < n && c < n) P[r * ldp + c] = -a * tile[threadIdx.x][y];
+      if (r < n && c < n) P[r * ldp + c] = var ? -tile[threadIdx.x][y] / width : -a * tile[threadIdx.x][y];
     }
   }
 }
@@ -173,11 +183,14 @@ __global__ void p0_kernel(const double* __restrict__ H, int64_t n, int64_t ldh, 
 //   2: diag P X2     3: upper P X2
 //   4: diag (X2-P)^2 5: upper (X2-P)^2
 //   6: diag P H      7: upper P H
+//   8: diag X2^2      9: upper X2^2      (NQ = 10: SP2 / TRS4)
+template <int NQ>
 __global__ void __launch_bounds__(256)
 measure_kernel(const double* __restrict__ P, int64_t ldp, const double* __restrict__ X2, int64_t ldx,
                const double* __restrict__ H, int64_t ldh, int64_t n, double* __restrict__ part,
                const PurifyState* st) {
   if (st->done) return;
+  double d_xx = 0.0, a_xx[4] = {0.0, 0.0, 0.0, 0.0};
   // four independent accumulator sets (entries j, j + 256, j + 512, j + 768 of
   // a step) keep twelve loads in flight per thread; combined in order below
   double a_px[4] = {0.0, 0.0, 0.0, 0.0}, a_id[4] = {0.0, 0.0, 0.0, 0.0}, a_ph[4] = {0.0, 0.0, 0.0, 0.0};
@@ -194,6 +207,7 @@ measure_kernel(const double* __restrict__ P, int64_t ldp, const double* __restri
       d_px += p * x;
       d_id += (x - p) * (x - p);
       d_ph += p * h;
+      if (NQ == 10) d_xx += x * x;
     }
     int64_t j = i + 1 + threadIdx.x;
     for (; j + 3 * B < n; j += 4 * B) {
@@ -209,6 +223,7 @@ measure_kernel(const double* __restrict__ P, int64_t ldp, const double* __restri
         a_px[u] += p[u] * x[u];
         a_id[u] += (x[u] - p[u]) * (x[u] - p[u]);
         a_ph[u] += p[u] * h[u];
+        if (NQ == 10) a_xx[u] += x[u] * x[u];
       }
     }
     for (; j < n; j += B) {
@@ -216,54 +231,91 @@ measure_kernel(const double* __restrict__ P, int64_t ldp, const double* __restri
       a_px[0] += p * x;
       a_id[0] += (x - p) * (x - p);
       a_ph[0] += p * h;
+      if (NQ == 10) a_xx[0] += x * x;
     }
   }
   const double u_px = (a_px[0] + a_px[1]) + (a_px[2] + a_px[3]);
   const double u_id = (a_id[0] + a_id[1]) + (a_id[2] + a_id[3]);
   const double u_ph = (a_ph[0] + a_ph[1]) + (a_ph[2] + a_ph[3]);
-  __shared__ double red[8][8];
-  double v[8] = {d_p, d_x, d_px, u_px, d_id, u_id, d_ph, u_ph};
+  const double u_xx = (a_xx[0] + a_xx[1]) + (a_xx[2] + a_xx[3]);
+  __shared__ double red[8][NQ];
+  double v[NQ];
+  v[0] = d_p, v[1] = d_x, v[2] = d_px, v[3] = u_px, v[4] = d_id, v[5] = u_id, v[6] = d_ph, v[7] = u_ph;
+  if (NQ == 10) v[NQ - 2] = d_xx, v[NQ - 1] = u_xx;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = warp_sum(v[q]);
+  for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) red[w][q] = v[q];
+    for (int q = 0; q < NQ; ++q) red[w][q] = v[q];
   __syncthreads();
-  if (threadIdx.x < 8) {
+  if (threadIdx.x < NQ) {
     double t = 0.0;
     for (int ww = 0; ww < 8; ++ww) t += red[ww][threadIdx.x];
-    part[static_cast<int64_t>(blockIdx.x) * 8 + threadIdx.x] = t;
+    part[static_cast<int64_t>(blockIdx.x) * NQ + threadIdx.x] = t;
   }
 }
 
 // Sum the partials in a fixed order and apply the stopping rules; one CTA of
-// 256 threads: thread t sums blocks t, t + 256, ... of all eight measures,
-// then warp trees and the eight warps in order.
+// 256 threads: thread t sums blocks t, t + 256, ... of all NQ measures, then
+// warp trees and the eight warps in order. NQ = 8: canonical purification
+// (pm_decide); NQ = 10: SP2 / TRS4 (variant_decide).
+template <int NQ>
 __global__ void __launch_bounds__(256)
 measure_final_kernel(const double* __restrict__ part, int nblocks, PurifyState* st) {
   if (st->done) return;
-  double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] += part[static_cast<int64_t>(b) * 8 + q];
+    for (int q = 0; q < NQ; ++q) v[q] += part[static_cast<int64_t>(b) * NQ + q];
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = warp_sum(v[q]);
-  __shared__ double red[8][8];
-  __shared__ double tot[8];
+  for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+  __shared__ double red[8][NQ];
+  __shared__ double tot[NQ];
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) red[threadIdx.x >> 5][q] = v[q];
+    for (int q = 0; q < NQ; ++q) red[threadIdx.x >> 5][q] = v[q];
   }
   __syncthreads();
-  if (threadIdx.x < 8) {
+  if (threadIdx.x < NQ) {
     double t = 0.0;
     for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
     tot[threadIdx.x] = t;
   }
   __syncthreads();
-  if (threadIdx.x == 0) pm_decide(st, tot);
+  if (threadIdx.x == 0) {
+    if (NQ == 8) {
+      pm_decide(st, tot);
+    } else {
+      variant_decide(st, tot);
+    }
+  }
+}
+
+// Out = alpha X + b2 X2 (SP2 steps), over the full n x n (grid-stride, rows of 256 threads)
+__global__ void __launch_bounds__(256)
+axpby_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2, int64_t ldx2,
+             double* __restrict__ out, int64_t ldo, int64_t n, const PurifyState* st) {
+  const double a = st->alpha, b = st->b2;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) out[i * ldo + j] = a * X[i * ldx + j] + b * X2[i * ldx2 + j];
+  }
+}
+
+// Z = zd I + zx X + zx2 X2 (the TRS4 factor with F + gamma G = X2 Z)
+__global__ void __launch_bounds__(256)
+trs4_z_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2, int64_t ldx2,
+              double* __restrict__ out, int64_t ldo, int64_t n, const PurifyState* st) {
+  const double zd = st->zd, zx = st->zx, zx2 = st->zx2;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const double v = zx * X[i * ldx + j] + zx2 * X2[i * ldx2 + j];
+      out[i * ldo + j] = j == i ? v + zd : v;
+    }
+  }
 }
 
 // The update weights of a McWeeny step (c = 1/2): alpha = 0, b2 = 3, b3 = -2.
@@ -326,6 +378,33 @@ energy_final_kernel(const double* __restrict__ part, int nblocks, PurifyState* s
 
 }  // namespace
 
+cudaError_t launch_measure_variant(const double* X, int64_t ldx, const double* X2, int64_t ldx2, const double* H,
+                                   int64_t ldh, int64_t n, double* partials, PurifyState* state, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_MEASURE, st);
+  measure_kernel<10><<<kMeasureBlocks, 256, 0, st>>>(X, ldx, X2, ldx2, H, ldh, n, partials, state);
+  measure_final_kernel<10><<<1, 256, 0, st>>>(partials, kMeasureBlocks, state);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(const double* X, int64_t ldx, const double* X2, int64_t ldx2, double* out, int64_t ldo,
+                         int64_t n, const PurifyState* state, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_OTHER, st);
+  axpby_kernel<<<static_cast<unsigned>(std::min<int64_t>(n, 4 * 152)), 256, 0, st>>>(X, ldx, X2, ldx2, out, ldo, n,
+                                                                                     state);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trs4_z(const double* X, int64_t ldx, const double* X2, int64_t ldx2, double* out, int64_t ldo,
+                          int64_t n, const PurifyState* state, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_OTHER, st);
+  trs4_z_kernel<<<static_cast<unsigned>(std::min<int64_t>(n, 4 * 152)), 256, 0, st>>>(X, ldx, X2, ldx2, out, ldo,
+                                                                                      n, state);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_refine_weights(PurifyState* state, cudaStream_t st) {
   ProfScope prof(DMP_PROF_OTHER, st);
   refine_weights_kernel<<<1, 1, 0, st>>>(state);
@@ -370,8 +449,8 @@ cudaError_t launch_measure(const double* P, int64_t ldp, const double* X2, int64
                            const double* H, int64_t ldh, int64_t n, double* partials,
                            PurifyState* state, cudaStream_t st) {
   ProfScope prof(DMP_PROF_MEASURE, st);
-  measure_kernel<<<kMeasureBlocks, 256, 0, st>>>(P, ldp, X2, ldx, H, ldh, n, partials, state);
-  measure_final_kernel<<<1, 256, 0, st>>>(partials, kMeasureBlocks, state);
+  measure_kernel<8><<<kMeasureBlocks, 256, 0, st>>>(P, ldp, X2, ldx, H, ldh, n, partials, state);
+  measure_final_kernel<8><<<1, 256, 0, st>>>(partials, kMeasureBlocks, state);
   count_launch(2);
   return cudaGetLastError();
 }

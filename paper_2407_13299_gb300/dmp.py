@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdmp.so")
 
 MODES = {"fp64": 0, "int8": 1, "bf16": 2}
+METHODS = {"pm": 0, "trs4": 1, "sp2": 2}
 EXECUTORS = {"auto": 0, "imma": 1, "tc": 2}
 BETA = {"int8": 7, "bf16": 8}
 
@@ -34,7 +35,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("slices", ctypes.c_int32), ("executor", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("tol", ctypes.c_double), ("energy_tol", ctypes.c_double),
-                ("refine_slices", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("refine_slices", ctypes.c_int32), ("method", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -158,11 +159,12 @@ def _require_cuda(*ts):
 
 
 def make_opts(mode="int8", slices=7, executor="auto", tol=1e-10, energy_tol=0.0, max_iter=100,
-              checkpoint_every=8, refine=0) -> Opts:
+              checkpoint_every=8, refine=0, method="pm") -> Opts:
     """refine: 0 none, -1 a McWeeny refinement step with FP64 products, s_r > 0
-    one with Ozaki products of s_r slices (see dm_purify)."""
+    one with Ozaki products of s_r slices (see dm_purify). method: "pm"
+    (canonical purification), "trs4" or "sp2" (DMP_METHOD_*)."""
     return Opts(MODES[mode], int(slices) if mode != "fp64" else 0, EXECUTORS[executor], int(max_iter),
-                int(checkpoint_every), 0, float(tol), float(energy_tol), int(refine), 0)
+                int(checkpoint_every), 0, float(tol), float(energy_tol), int(refine), METHODS[method])
 
 
 def workspace(nbytes: int, device=None) -> torch.Tensor:
@@ -182,16 +184,18 @@ def tape_bytes(n: int, opts: Opts) -> int:
 
 
 def purify(H: torch.Tensor, n_occ: int, mode="int8", slices=7, executor="auto", tol=1e-10,
-           energy_tol=0.0, max_iter=100, P=None, ws=None, tape=None, stream=None, checkpoint_every=8, refine=0):
+           energy_tol=0.0, max_iter=100, P=None, ws=None, tape=None, stream=None, checkpoint_every=8, refine=0,
+           method="pm"):
     """dm_purify on a float64 CUDA tensor H. Returns (P, info dict).
 
     `ws`, `P` and `tape` may be passed preallocated (see purify_workspace_bytes,
     tape_bytes) so that repeated calls allocate nothing. `refine` adds the
-    McWeeny refinement step (make_opts).
+    McWeeny refinement step, `method` picks canonical purification, TRS4 or
+    SP2 (make_opts).
     """
     _require_cuda(H)
     n = H.shape[0]
-    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every, refine)
+    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every, refine, method)
     if P is None:
         P = torch.empty_like(H)
     if ws is None:
