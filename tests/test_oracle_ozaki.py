@@ -297,3 +297,177 @@ def test_planted_wrong_digit_sign_fails_reconstruction():
     A = _mixed_matrix(4, 6, seed=61)
     with pytest.raises(AssertionError):
         _check_split(split_abs, A, 3, 7)
+
+
+# ----------------------------------------------------------------- nearest digits (E4M3 mode)
+
+def _e4m3_values():
+    """Every finite value of the FP8 format E4M3 (sign, 4 exponent bits with
+    bias 7, 3 fraction bits; exponent field 0 is subnormal; S.1111.111 is NaN)."""
+    vals = set()
+    for code in range(256):
+        sign = -1 if code & 0x80 else 1
+        ex = (code >> 3) & 0xF
+        fr = code & 0x7
+        if ex == 0xF and fr == 0x7:
+            continue
+        v = Fraction(fr, 8) * Fraction(2) ** -6 if ex == 0 else (1 + Fraction(fr, 8)) * Fraction(2) ** (ex - 7)
+        vals.add(sign * v)
+    return vals
+
+
+def test_nearest_digits_are_exact_in_e4m3():
+    """Sec. "Ozaki Scheme": slices must multiply without error on the hardware;
+    every nearest digit of beta = 5 (|d| <= 16) is an E4M3 value, 17 is not."""
+    vals = _e4m3_values()
+    assert oz.max_digit(oz.BETA["e4m3"], oz.ROUNDING["e4m3"]) == 16
+    assert all(Fraction(d) in vals for d in range(-16, 17))
+    assert Fraction(17) not in vals
+
+
+def _tie_matrix():
+    """Rows whose scaled entries hit the digit rule's edges: ties (y = k + 1/2
+    of both signs, even and odd k) and a first digit of 16. Row max 1.96875:
+    e = 2, x = a / 4, y = 32 x = 8 a."""
+    A = np.array([
+        [1.96875, 0.4375, -0.4375, 0.3125, -0.3125, 0.0625, 2.0 ** -40],
+        [1.5, -1.96875 + 2.0 ** -30, 0.1875, -0.1875, 1.0 / 3.0, -2.0 / 7.0, 0.0],
+    ])
+    return A
+
+
+def _check_nearest_split(split_rows, A, s, beta):
+    e, D, res = split_rows(A, s, beta, "nearest")
+    m, k = A.shape
+    half = Fraction(1, 2)
+    for r in range(m):
+        rowmax = max(abs(Fraction(float(v))) for v in A[r])
+        if rowmax == 0:
+            assert e[r] == 0
+        else:
+            assert 2 * rowmax < Fraction(2) ** int(e[r]) <= 4 * rowmax
+        for c in range(k):
+            x = Fraction(float(A[r, c])) / Fraction(2) ** int(e[r])
+            assert -half < x < half
+            for i in range(s):
+                y = x * 2 ** beta
+                d = int(D[i, r, c])
+                # d = floor(y + 1/2) is the one integer with y - d in [-1/2, 1/2)
+                assert -half <= y - d < half, (r, c, i, y, d)
+                assert abs(d) <= 2 ** (beta - 1)
+                x = y - d
+            assert Fraction(float(res[r, c])) == x
+            recon = sum(Fraction(int(D[i, r, c])) / Fraction(2) ** (beta * (i + 1)) for i in range(s))
+            recon += x / Fraction(2) ** (beta * s)
+            assert recon * Fraction(2) ** int(e[r]) == Fraction(float(A[r, c]))
+
+
+@pytest.mark.parametrize("s", [1, 3, 7, 12])
+def test_nearest_split_matches_digit_rule(s):
+    _check_nearest_split(oz.split_rows, _mixed_matrix(5, 9, seed=70 + s), s, 5)
+    _check_nearest_split(oz.split_rows, _tie_matrix(), s, 5)
+
+
+def test_nearest_tie_and_edge_digits():
+    """The tie matrix's first digits, worked by hand: y = 8 a."""
+    e, D, _ = oz.split_rows(_tie_matrix(), 2, 5, "nearest")
+    assert list(e) == [2, 2]
+    # 1.96875 -> y = 15.75 -> 16; +-0.4375 -> y = +-3.5 -> 4 and -3 (ties upward);
+    # +-0.3125 -> y = +-2.5 -> 3 and -2; 0.0625 -> 0.5 -> 1; 2^-40 -> 0
+    assert list(D[0, 0]) == [16, 4, -3, 3, -2, 1, 0]
+    # second digits: 15.75 - 16 = -1/4 -> -8; 3.5 - 4 = -1/2 -> -16; -3.5 + 3 = -1/2 -> -16
+    assert list(D[1, 0, :3]) == [-8, -16, -16]
+
+
+@pytest.mark.parametrize("s", [2, 5, 7])
+def test_nearest_level_sums_equal_exact_integer_products(s):
+    A = _mixed_matrix(5, 7, seed=81)
+    B = _mixed_matrix(7, 4, seed=82)
+    _, DA, _ = oz.split_rows(A, s, 5, "nearest")
+    _, DBt, _ = oz.split_cols(B, s, 5, "nearest")
+    got = oz.level_sums(DA, DBt, 5, "nearest")
+    want = _brute_levels(DA, DBt)
+    for L in want:
+        assert np.array_equal(got[L], np.array(want[L], dtype=np.int64)), L
+
+
+@pytest.mark.parametrize("s", [2, 4, 7, 9])
+def test_nearest_error_within_bound(s):
+    A = _mixed_matrix(6, 8, seed=91)
+    B = _mixed_matrix(8, 5, seed=92)
+    C, parts = oz.ozaki_gemm(A, B, s, 5, return_parts=True, rounding="nearest")
+    exact = _exact_product(A, B)
+    bound = oz.truncation_bound(parts["e"], parts["f"], A.shape[1], s, 5, rounding="nearest")
+    for r in range(A.shape[0]):
+        for c in range(B.shape[1]):
+            assert abs(Fraction(float(C[r, c])) - exact[r][c]) <= Fraction(float(bound[r, c])), (r, c)
+
+
+def test_nearest_small_integers_need_one_slice():
+    """Integer entries in [-15, 15] with a row (column) maximum of at least 8:
+    e = 5, so y = a is its own single digit and the one-slice product is exact."""
+    rng = _rng(95)
+    A = rng.integers(-15, 16, size=(7, 9)).astype(np.float64)
+    B = rng.integers(-15, 16, size=(9, 6)).astype(np.float64)
+    A[:, 0] = -9.0
+    B[0, :] = 12.0
+    want = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    for s in (1, 3):
+        assert np.array_equal(oz.ozaki_gemm(A, B, s, 5, rounding="nearest"), want)
+
+
+def test_nearest_full_coverage_is_correctly_rounded():
+    """beta s = 60 on nonnegative inputs: within 2 ulp of the correctly rounded product."""
+    rng = _rng(96)
+    A = rng.random((6, 10))
+    B = rng.random((10, 5))
+    C = oz.ozaki_gemm(A, B, 12, 5, rounding="nearest")
+    exact = _exact_product(A, B)
+    for r in range(6):
+        for c in range(5):
+            ref = float(exact[r][c])
+            assert abs(C[r, c] - ref) <= 2 * np.spacing(ref), (r, c)
+
+
+def test_nearest_matches_truncated_accuracy_per_bit():
+    """Seven nearest digits of 5 bits (34 bits below the row maximum) and five
+    truncated digits of 7 bits (35 bits) give errors of the same order."""
+    rng = _rng(97)
+    A = rng.standard_normal((24, 96))
+    B = rng.standard_normal((96, 20))
+    ref = np.array(_exact_product_float(A, B))
+    e_near = np.abs(oz.ozaki_gemm(A, B, 7, 5, rounding="nearest") - ref).max()
+    e_trunc = np.abs(oz.ozaki_gemm(A, B, 5, 7) - ref).max()
+    assert 0.1 < e_near / e_trunc < 10.0
+
+
+def test_planted_half_even_rounding_fails_the_digit_rule():
+    def split_half_even(A, s, beta, rounding):
+        e = oz.row_exponents(A, "nearest")
+        x = np.ldexp(np.asarray(A, dtype=np.float64), -e[:, None])
+        D = np.zeros((s,) + A.shape, dtype=np.int64)
+        for i in range(s):
+            y = x * 2.0 ** beta
+            d = np.round(y)  # ties to even
+            x = y - d
+            D[i] = d.astype(np.int64)
+        return e, D, x
+
+    with pytest.raises(AssertionError):
+        _check_nearest_split(split_half_even, _tie_matrix(), 2, 5)
+
+
+def test_planted_truncated_digits_fail_the_nearest_rule():
+    def split_trunc_digits(A, s, beta, rounding):
+        e = oz.row_exponents(A, "nearest")
+        x = np.ldexp(np.asarray(A, dtype=np.float64), -e[:, None])
+        D = np.zeros((s,) + A.shape, dtype=np.int64)
+        for i in range(s):
+            y = x * 2.0 ** beta
+            d = np.trunc(y)
+            x = y - d
+            D[i] = d.astype(np.int64)
+        return e, D, x
+
+    with pytest.raises(AssertionError):
+        _check_nearest_split(split_trunc_digits, _mixed_matrix(4, 6, seed=98), 3, 5)

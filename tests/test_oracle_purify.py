@@ -181,6 +181,22 @@ def test_ozaki_mode_converges_towards_projector():
     assert errs[2] < 1e-9
 
 
+def test_nearest_digit_mode_converges_towards_projector():
+    """The same with nearest 5-bit digits (the E4M3 mode): the error falls with
+    the slice count, and 7 such slices land near 5 truncated 7-bit ones."""
+    h = make_hamiltonian(96, 24, seed=7)
+    P_star = _projector(h.Q, 24)
+    errs = []
+    for s in (4, 7, 10):
+        r = pu.purify(h.H, 24, tol=1e-10, product=partial(oz.ozaki_gemm, s=s, beta=5, rounding="nearest"))
+        errs.append(np.max(np.abs(r["P"] - P_star)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-9
+    r5 = pu.purify(h.H, 24, tol=1e-10, product=partial(oz.ozaki_gemm, s=5, beta=7))
+    ratio = errs[1] / np.max(np.abs(r5["P"] - P_star))
+    assert 0.05 < ratio < 20.0
+
+
 def test_error_metrics_paper_conventions():
     h = make_hamiltonian(40, 10, seed=8)
     P = _projector(h.Q, 10)
