@@ -42,14 +42,25 @@ extern "C" {
  *                 int8 range): exact s32 accumulation of the level sums.
  * DMP_OZAKI_BF16  Ozaki products with beta = 8 digit slices (|d| <= 255, the
  *                 integers bfloat16 holds exactly), bf16 tensor cores only.
+ * DMP_OZAKI_E4M3  Ozaki products with beta = 5 digit slices rounded to nearest
+ *                 (the extraction of the original Ozaki scheme): the row
+ *                 exponent is one larger (max_j |A_rj| < 2^(e_r - 1)) and
+ *                 d_i = floor(y + 1/2) for y = 2^5 x, so |d| <= 16, integers
+ *                 the FP8 format E4M3 holds exactly. Products run on the
+ *                 tcgen05 kind::f8f6f4 tensor cores (fp32 accumulation in
+ *                 tensor memory, exact while every partial sum stays below
+ *                 2^24: a whole K of up to 65536 digits). s in [1, 12];
+ *                 seven slices (34 bits below the row maximum) match five
+ *                 INT8 slices (34). Tensor-core executor only.
  */
-enum { DMP_FP64 = 0, DMP_OZAKI_INT8 = 1, DMP_OZAKI_BF16 = 2 };
+enum { DMP_FP64 = 0, DMP_OZAKI_INT8 = 1, DMP_OZAKI_BF16 = 2, DMP_OZAKI_E4M3 = 3 };
 
 /* ---- executors for the slice-pair products ---------------------------------
  * DMP_EXEC_IMMA  int8 x int8 -> int32 warp-level tensor-core MMA.
- * DMP_EXEC_TC    digits carried in bfloat16 on the 5th-generation tensor cores
- *                (tcgen05), fp32 accumulation in tensor memory, drained to
- *                exact integers every K chunk that keeps partial sums < 2^24.
+ * DMP_EXEC_TC    digits carried in bfloat16 (E4M3 for DMP_OZAKI_E4M3) on the
+ *                5th-generation tensor cores (tcgen05), fp32 accumulation in
+ *                tensor memory, drained to exact integers every K chunk that
+ *                keeps partial sums < 2^24.
  * Both give bit-identical level sums; DMP_EXEC_AUTO picks the faster.
  */
 enum { DMP_EXEC_AUTO = 0, DMP_EXEC_IMMA = 1, DMP_EXEC_TC = 2 };
@@ -96,8 +107,9 @@ enum { DMP_METHOD_PM = 0, DMP_METHOD_TRS4 = 1, DMP_METHOD_SP2 = 2 };
 
 /* Options. Zero-initialise and set what you need; zeros select defaults. */
 typedef struct {
-  int32_t mode;             /* DMP_FP64 / DMP_OZAKI_INT8 / DMP_OZAKI_BF16           */
-  int32_t slices;           /* s in [1, 10] (beta 7) or [1, 9] (beta 8); 0 -> 7      */
+  int32_t mode;             /* DMP_FP64 / DMP_OZAKI_INT8 / DMP_OZAKI_BF16 / _E4M3   */
+  int32_t slices;           /* s in [1, 10] (beta 7), [1, 9] (beta 8) or [1, 12]
+                               (E4M3); 0 -> 7                                        */
   int32_t executor;         /* DMP_EXEC_*                                            */
   int32_t max_iter;         /* 0 -> 100 (the paper's cap)                            */
   int32_t checkpoint_every; /* forward iterates kept every k steps for the adjoint; 0 -> 8 */
@@ -175,16 +187,18 @@ int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int
  * ozaki_gemm: C = A B, m x k times k x n, through the Ozaki scheme
  * (Sec. "Ozaki Scheme"): A scaled per row and B per column by powers of two,
  * split into `slices` digit planes of beta bits (mode DMP_OZAKI_INT8: beta 7;
- * DMP_OZAKI_BF16: beta 8), level sums S_L = sum_{i+j=L} A_i B_j formed exactly
- * for L = 2..s+1, and C = 2^(e_r+f_c) * sum_L S_L 2^(-beta L) in float64:
- * groups of up to four consecutive levels (beta 7; single levels for beta 8)
- * are first combined exactly in 64-bit integers, then the groups are added in
- * float64 from the L = s+1 end to L = 2. For beta 7 and s <= 8 this is the
- * correctly rounded value of the exact sum of the kept pairs. The result is
- * bit-for-bit the same for every executor. mode DMP_FP64 computes a plain
- * float64 product instead.
+ * DMP_OZAKI_BF16: beta 8; DMP_OZAKI_E4M3: beta 5, nearest digits), level sums
+ * S_L = sum_{i+j=L} A_i B_j formed exactly for L = 2..s+1, and
+ * C = 2^(e_r+f_c) * sum_L S_L 2^(-beta L) in float64: groups of up to four
+ * consecutive levels (beta 7 and 5; single levels for beta 8) are first
+ * combined exactly in 64-bit integers, then the groups are added in float64
+ * from the L = s+1 end to L = 2. With at most two groups (s <= 8 for beta 7
+ * and 5) this is the correctly rounded value of the exact sum of the kept
+ * pairs. The result is bit-for-bit the same for every executor. mode DMP_FP64
+ * computes a plain float64 product instead.
  * A row of A or column of B holding NaN/Inf gives a NaN row/column of C.
- * Limits: s * k * (2^beta - 1)^2 < 2^31 (exact s32 level sums).
+ * Limits: s * k * dmax^2 < 2^31 (exact s32 level sums; dmax = 2^beta - 1, or
+ * 16 for E4M3).
  */
 int ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                int64_t ldb, double* C, int64_t ldc, int32_t mode, int32_t slices, int32_t executor,
@@ -233,11 +247,14 @@ int ozaki_level_sums(int64_t m, int64_t n, int64_t k, const double* A, int64_t l
 /*
  * ozaki_split: the row scaling and digit planes of A (m x k), the first step
  * of the scheme, exactly as the product kernels consume them. exps[m] receives
- * e_r (max_j |A_rj| < 2^e_r; 0 for a zero row; INT32_MAX for a row holding NaN
- * or Inf, whose products are then NaN). digits receives s planes of m x k
- * (plane-major, leading dimension k) of the beta-bit truncated digits,
- * |d| <= 2^beta - 1: int8 for executor DMP_EXEC_IMMA, bfloat16 bit patterns
- * for DMP_EXEC_TC. Workspace as for ozaki_gemm(m, 1, k, ...).
+ * e_r (max_j |A_rj| < 2^e_r, or < 2^(e_r - 1) for DMP_OZAKI_E4M3; 0 for a
+ * zero row; INT32_MAX for a row holding NaN or Inf, whose products are then
+ * NaN). digits receives s planes of m x k (plane-major, leading dimension k)
+ * of the beta-bit truncated digits, |d| <= 2^beta - 1: int8 for executor
+ * DMP_EXEC_IMMA, bfloat16 bit patterns for DMP_EXEC_TC; for DMP_OZAKI_E4M3
+ * the nearest digits (|d| <= 16) as E4M3 bytes (sign bit 7, exponent bits
+ * 3..6 with bias 7, fraction bits 0..2). Workspace as for
+ * ozaki_gemm(m, 1, k, ...).
  */
 int ozaki_split(int64_t m, int64_t k, const double* A, int64_t lda, int32_t mode, int32_t slices,
                 int32_t executor, int32_t* exps, void* digits, void* ws, size_t ws_bytes,
@@ -252,7 +269,8 @@ int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* 
  * length `batch`; H[b] and P[b] are device pointers (n[b] x n[b], leading
  * dimension n[b]). infos (host, length batch, nullable) receives one report per
  * matrix. Each matrix stops on its own rule; the call returns DMP_OK when all
- * converged, else the largest status seen.
+ * converged, else the largest status seen. Modes DMP_OZAKI_INT8 and
+ * DMP_OZAKI_BF16 (DMP_OZAKI_E4M3 and DMP_FP64 give DMP_ERR_UNSUPPORTED).
  */
 int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n,
                       const int64_t* n_occ, double* const* P, const dmp_opts* opts,

@@ -40,12 +40,13 @@ struct Opts {
 int normalize(const dmp_opts* o, Opts& out) {
   if (o == nullptr) return DMP_ERR_INVALID_ARG;
   out.mode = o->mode;
-  if (out.mode != DMP_FP64 && out.mode != DMP_OZAKI_INT8 && out.mode != DMP_OZAKI_BF16)
+  if (out.mode != DMP_FP64 && out.mode != DMP_OZAKI_INT8 && out.mode != DMP_OZAKI_BF16 &&
+      out.mode != DMP_OZAKI_E4M3)
     return DMP_ERR_INVALID_ARG;
   out.beta = beta_of(out.mode);
   out.s = o->slices == 0 ? 7 : o->slices;
+  const int smax = max_slices(out.mode);
   if (out.mode != DMP_FP64) {
-    const int smax = out.beta == 7 ? 10 : 9;
     if (out.s < 1 || out.s > smax) return DMP_ERR_INVALID_ARG;
   } else {
     out.s = 0;
@@ -54,7 +55,8 @@ int normalize(const dmp_opts* o, Opts& out) {
   if (out.executor < DMP_EXEC_AUTO || out.executor > DMP_EXEC_TC) return DMP_ERR_INVALID_ARG;
   // the tcgen05 executor is the fast one on this GPU (bf16 tensor rate >> int8 mma.sync rate)
   if (out.mode != DMP_FP64 && out.executor == DMP_EXEC_AUTO) out.executor = DMP_EXEC_TC;
-  if (out.mode == DMP_OZAKI_BF16 && out.executor == DMP_EXEC_IMMA) return DMP_ERR_UNSUPPORTED;
+  if ((out.mode == DMP_OZAKI_BF16 || out.mode == DMP_OZAKI_E4M3) && out.executor == DMP_EXEC_IMMA)
+    return DMP_ERR_UNSUPPORTED;
   if (out.mode == DMP_FP64) out.executor = 0;
   out.max_iter = o->max_iter == 0 ? 100 : o->max_iter;
   if (out.max_iter < 0) return DMP_ERR_INVALID_ARG;
@@ -67,22 +69,30 @@ int normalize(const dmp_opts* o, Opts& out) {
   if (out.method < DMP_METHOD_PM || out.method > DMP_METHOD_SP2) return DMP_ERR_INVALID_ARG;
   out.refine = o->refine_slices;
   if (out.refine != 0 && out.mode == DMP_FP64) out.refine = -1;
-  if (out.refine < -1 || out.refine > (out.beta == 8 ? 9 : 10)) return DMP_ERR_INVALID_ARG;
+  if (out.refine < -1 || out.refine > smax) return DMP_ERR_INVALID_ARG;
   return DMP_OK;
 }
 
-// Level sums stay exact in int32 while s k (2^beta - 1)^2 < 2^31 (the IMMA
-// executor and the tcgen05 executor with beta = 7 keep them in int32; the
-// tcgen05 executor with beta = 8 keeps a two-word integer).
-bool levels_fit_int32(int64_t k, int s, int beta) {
-  const double bound = static_cast<double>(s) * static_cast<double>(k) *
-                       std::pow(2.0, beta) * std::pow(2.0, beta);
+// Level sums stay exact in int32 while s k dmax^2 < 2^31 (the IMMA executor
+// and the tcgen05 executor with beta = 7 or E4M3 digits keep them in int32;
+// the tcgen05 executor with beta = 8 keeps a two-word integer).
+bool levels_fit_int32(int64_t k, int s, int mode) {
+  const double dmax = digit_max(mode);
+  const double bound = static_cast<double>(s) * static_cast<double>(k) * dmax * dmax;
   return bound < 2147483648.0;
 }
 
 bool needs_int32(int mode, int executor) { return !(mode == DMP_OZAKI_BF16 && executor == DMP_EXEC_TC); }
-int elem_bytes(int executor) { return executor == DMP_EXEC_TC ? 2 : 1; }
-int elem_kind(int executor) { return executor == DMP_EXEC_TC ? 3 : 1; }
+// digit plane element: int8 (IMMA), bfloat16 (tcgen05) or E4M3 bytes (E4M3 mode)
+int elem_bytes(const Opts& o) { return (o.executor == DMP_EXEC_TC && o.mode != DMP_OZAKI_E4M3) ? 2 : 1; }
+int elem_kind(const Opts& o) {
+  if (o.mode == DMP_OZAKI_E4M3) return 4;
+  return o.executor == DMP_EXEC_TC ? 3 : 1;
+}
+// K padding of the digit planes: two swizzle atoms of the paired tcgen05 kernel
+int64_t k_pad_of(const Opts& o, int64_t k) {
+  return round_up(std::max<int64_t>(k, 1), o.mode == DMP_OZAKI_E4M3 ? kPadK8 : kPadK);
+}
 // digit-plane rows are padded to the executor's tile height (tcgen05: 256 so
 // that one plane set serves as A (128-row tiles) and B (256-row tiles))
 int64_t row_pad(int executor) { return executor == DMP_EXEC_TC ? 256 : kTileM; }
@@ -103,7 +113,7 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
   PurifyLayout L;
   Carver c;
   L.n_pad = round_up(n, o.mode == DMP_FP64 ? kTileM : row_pad(o.executor));
-  L.k_pad = round_up(n, kPadK);
+  L.k_pad = k_pad_of(o, n);
   L.state = c.take(sizeof(PurifyState));
   L.partials = c.take(static_cast<size_t>(kMeasureBlocks) * 10 * sizeof(double));  // 8 measures, 10 for SP2 / TRS4
   L.rowbuf = c.take(gershgorin_rowbuf_bytes(n));
@@ -115,7 +125,7 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
   if (o.mode != DMP_FP64) {
     // room for the refinement step's slices too
     const int smax = std::max(o.s, o.refine);
-    const size_t plane = static_cast<size_t>(smax) * L.n_pad * L.k_pad * elem_bytes(o.executor);
+    const size_t plane = static_cast<size_t>(smax) * L.n_pad * L.k_pad * elem_bytes(o);
     L.planesP = c.take(plane);
     L.planesX = c.take(plane);
   } else {
@@ -177,7 +187,7 @@ BackwardLayout backward_layout(int64_t n, const Opts& o) {
   Carver c;
   const size_t nn = static_cast<size_t>(n) * n * sizeof(double);
   B.n_pad = round_up(n, o.mode == DMP_FP64 ? kTileM : row_pad(o.executor));
-  B.k_pad = round_up(n, kPadK);
+  B.k_pad = k_pad_of(o, n);
   B.state = c.take(sizeof(PurifyState));
   B.scalars = c.take(sizeof(AdjScalars));
   B.p0 = c.take(sizeof(P0Adjoint));
@@ -194,7 +204,7 @@ BackwardLayout backward_layout(int64_t n, const Opts& o) {
   B.segP = c.take(nn * o.every);
   B.segX = c.take(nn * o.every);
   if (o.mode != DMP_FP64) {
-    const size_t plane = static_cast<size_t>(o.s) * B.n_pad * B.k_pad * elem_bytes(o.executor);
+    const size_t plane = static_cast<size_t>(o.s) * B.n_pad * B.k_pad * elem_bytes(o);
     B.planesP = c.take(plane);
     B.planesA = c.take(plane);
   } else {
@@ -260,9 +270,9 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   if (rc != DMP_OK) return rc;
   if (H == nullptr || P == nullptr || ws == nullptr) return DMP_ERR_INVALID_ARG;
   if (n < 2 || ldh < n || ldp < n || n_occ <= 0 || n_occ >= n) return DMP_ERR_INVALID_ARG;
-  if (o.mode != DMP_FP64 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.s, o.beta))
+  if (o.mode != DMP_FP64 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.s, o.mode))
     return DMP_ERR_UNSUPPORTED;
-  if (o.refine > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.refine, o.beta))
+  if (o.refine > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.refine, o.mode))
     return DMP_ERR_UNSUPPORTED;
   if ((o.refine != 0 || o.method != DMP_METHOD_PM) && tape != nullptr) return DMP_ERR_UNSUPPORTED;
   const PurifyLayout L = purify_layout(n, o);
@@ -319,7 +329,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
       DMP_CUDA(launch_gemm_f64(cur, ldcur, cur, ldcur, n, n, n, 1, e2, done, st));
     } else {
       DMP_CUDA(launch_split_rows(cur, n, n, ldcur, o.s, o.beta, expsP, planesP, L.n_pad, L.k_pad,
-                                 elem_kind(o.executor), nullptr, done, st));
+                                 elem_kind(o), nullptr, done, st));
       DMP_CUDA(launch_product(o, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e2, done,
                               err, scratch, st));
     }
@@ -352,9 +362,9 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
           DMP_CUDA(launch_gemm_f64(X2, n, alt, ldalt, n, n, n, 1, ez, done, st));
         } else {
           DMP_CUDA(launch_split_rows(X2, n, n, n, o.s, o.beta, expsX, planesX, L.n_pad, L.k_pad,
-                                     elem_kind(o.executor), nullptr, done, st));
+                                     elem_kind(o), nullptr, done, st));
           DMP_CUDA(launch_split_rows(alt, n, n, ldalt, o.s, o.beta, expsP, planesP, L.n_pad, L.k_pad,
-                                     elem_kind(o.executor), nullptr, done, st));
+                                     elem_kind(o), nullptr, done, st));
           DMP_CUDA(launch_product(o, planesX, planesP, expsX, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, ez, done,
                                   err, scratch, st));
         }
@@ -377,7 +387,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
       DMP_CUDA(launch_gemm_f64(cur, ldcur, X2, n, n, n, n, 1, e3, done, st));
     } else {
       DMP_CUDA(launch_split_rows(X2, n, n, n, o.s, o.beta, expsX, planesX, L.n_pad, L.k_pad,
-                                 elem_kind(o.executor), nullptr, done, st));
+                                 elem_kind(o), nullptr, done, st));
       DMP_CUDA(launch_product(o, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e3, done,
                               err, scratch, st));
     }
@@ -413,11 +423,11 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
         Opts orr = o;
         orr.s = o.refine;
         DMP_CUDA(launch_split_rows(cur, n, n, ldcur, orr.s, orr.beta, expsP, planesP, L.n_pad, L.k_pad,
-                                   elem_kind(o.executor), nullptr, nullptr, st));
+                                   elem_kind(o), nullptr, nullptr, st));
         DMP_CUDA(launch_product(orr, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, r2, nullptr,
                                 err, scratch, st));
         DMP_CUDA(launch_split_rows(X2, n, n, n, orr.s, orr.beta, expsX, planesX, L.n_pad, L.k_pad,
-                                   elem_kind(o.executor), nullptr, nullptr, st));
+                                   elem_kind(o), nullptr, nullptr, st));
         DMP_CUDA(launch_product(orr, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, r3, nullptr,
                                 err, scratch, st));
       }
@@ -494,13 +504,13 @@ int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int
   Carver c;
   const int64_t m_pad = round_up(std::max<int64_t>(m, 1), row_pad(o.executor));
   const int64_t n_pad = round_up(std::max<int64_t>(n, 1), row_pad(o.executor));
-  const int64_t k_pad = round_up(std::max<int64_t>(k, 1), kPadK);
+  const int64_t k_pad = k_pad_of(o, k);
   c.take(m_pad * sizeof(int32_t));
   c.take(n_pad * sizeof(int32_t));
   c.take(sizeof(int32_t));
   c.take(o.executor == DMP_EXEC_TC ? tc_scratch_bytes() : 0);
-  c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o.executor));
-  c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o.executor));
+  c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o));
+  c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o));
   c.take(static_cast<size_t>(n) * k * sizeof(double));
   *bytes = c.cur;
   return DMP_OK;
@@ -525,7 +535,7 @@ static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_
     DMP_CUDA(launch_gemm_f64(A, lda, B, ldb, m, n, k, 0, epi, nullptr, st));
     return DMP_OK;
   }
-  if ((needs_int32(o.mode, o.executor) || epi.kind == EPI_LEVELS) && !levels_fit_int32(k, o.s, o.beta))
+  if ((needs_int32(o.mode, o.executor) || epi.kind == EPI_LEVELS) && !levels_fit_int32(k, o.s, o.mode))
     return DMP_ERR_UNSUPPORTED;
   size_t need = 0;
   ozaki_gemm_workspace_size(m, n, k, mode, slices, executor, &need);
@@ -533,18 +543,18 @@ static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_
   Carver c;
   const int64_t m_pad = round_up(m, row_pad(o.executor));
   const int64_t n_pad = round_up(n, row_pad(o.executor));
-  const int64_t k_pad = round_up(std::max<int64_t>(k, 1), kPadK);
+  const int64_t k_pad = k_pad_of(o, k);
   int32_t* ea = reinterpret_cast<int32_t*>(at(ws, c.take(m_pad * sizeof(int32_t))));
   int32_t* eb = reinterpret_cast<int32_t*>(at(ws, c.take(n_pad * sizeof(int32_t))));
   int* err = reinterpret_cast<int*>(at(ws, c.take(sizeof(int32_t))));
   double* scratch = reinterpret_cast<double*>(at(ws, c.take(o.executor == DMP_EXEC_TC ? tc_scratch_bytes() : 0)));
-  void* pa = at(ws, c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o.executor)));
-  void* pb = at(ws, c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o.executor)));
+  void* pa = at(ws, c.take(static_cast<size_t>(o.s) * m_pad * k_pad * elem_bytes(o)));
+  void* pb = at(ws, c.take(static_cast<size_t>(o.s) * n_pad * k_pad * elem_bytes(o)));
   double* Bt = reinterpret_cast<double*>(at(ws, c.take(static_cast<size_t>(n) * k * sizeof(double))));
-  DMP_CUDA(launch_split_rows(A, m, k, lda, o.s, o.beta, ea, pa, m_pad, k_pad, elem_kind(o.executor), nullptr,
+  DMP_CUDA(launch_split_rows(A, m, k, lda, o.s, o.beta, ea, pa, m_pad, k_pad, elem_kind(o), nullptr,
                              nullptr, st));
   DMP_CUDA(launch_transpose(B, k, n, ldb, Bt, st));
-  DMP_CUDA(launch_split_rows(Bt, n, k, k, o.s, o.beta, eb, pb, n_pad, k_pad, elem_kind(o.executor), nullptr,
+  DMP_CUDA(launch_split_rows(Bt, n, k, k, o.s, o.beta, eb, pb, n_pad, k_pad, elem_kind(o), nullptr,
                              nullptr, st));
   if (o.executor == DMP_EXEC_TC) DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   DMP_CUDA(launch_product(o, pa, pb, ea, eb, m, n, m_pad, n_pad, k_pad, 0, epi, nullptr, err, scratch, st));
@@ -601,13 +611,13 @@ int ozaki_split(int64_t m, int64_t k, const double* A, int64_t lda, int32_t mode
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carver c;
   const int64_t m_pad = round_up(m, row_pad(o.executor));
-  const int64_t k_pad = round_up(k, kPadK);
+  const int64_t k_pad = k_pad_of(o, k);
   int32_t* ea = reinterpret_cast<int32_t*>(at(ws, c.take(m_pad * sizeof(int32_t))));
   c.take(round_up(1, row_pad(o.executor)) * sizeof(int32_t));
   c.take(sizeof(int32_t));
-  const int eb = elem_bytes(o.executor);
+  const int eb = elem_bytes(o);
   char* pa = at(ws, c.take(static_cast<size_t>(o.s) * m_pad * k_pad * eb));
-  DMP_CUDA(launch_split_rows(A, m, k, lda, o.s, o.beta, ea, pa, m_pad, k_pad, elem_kind(o.executor), nullptr,
+  DMP_CUDA(launch_split_rows(A, m, k, lda, o.s, o.beta, ea, pa, m_pad, k_pad, elem_kind(o), nullptr,
                              nullptr, st));
   DMP_CUDA(cudaMemcpyAsync(exps, ea, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   for (int i = 0; i < o.s; ++i) {
@@ -686,14 +696,14 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
     e.C = C;
     e.ldc = n;
     if (o.mode == DMP_FP64) return launch_gemm_f64(A, n, Pk, n, n, n, n, 0, e, nullptr, st);
-    cudaError_t r = launch_split_rows(A, n, n, n, o.s, o.beta, expsA, planesA, npad, kpad, elem_kind(o.executor),
+    cudaError_t r = launch_split_rows(A, n, n, n, o.s, o.beta, expsA, planesA, npad, kpad, elem_kind(o),
                                       nullptr, nullptr, st);
     if (r != cudaSuccess) return r;
     return launch_product(o, planesA, planesP, expsA, expsP, n, n, npad, npad, kpad, 0, e, nullptr, err, scratch, st);
   };
   auto split_P = [&](const double* Pk) -> cudaError_t {
     if (o.mode == DMP_FP64) return cudaSuccess;
-    return launch_split_rows(Pk, n, n, n, o.s, o.beta, expsP, planesP, npad, kpad, elem_kind(o.executor), nullptr,
+    return launch_split_rows(Pk, n, n, n, o.s, o.beta, expsP, planesP, npad, kpad, elem_kind(o), nullptr,
                              nullptr, st);
   };
 
@@ -749,7 +759,7 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
         if (o.mode == DMP_FP64) {
           DMP_CUDA(launch_gemm_f64(Pk, n, Xk, n, n, n, n, 1, e3, nullptr, st));
         } else {
-          DMP_CUDA(launch_split_rows(Xk, n, n, n, o.s, o.beta, expsA, planesA, npad, kpad, elem_kind(o.executor),
+          DMP_CUDA(launch_split_rows(Xk, n, n, n, o.s, o.beta, expsA, planesA, npad, kpad, elem_kind(o),
                                      nullptr, nullptr, st));
           DMP_CUDA(launch_product(o, planesP, planesA, expsP, expsA, n, n, npad, npad, kpad, 1, e3, nullptr, err,
                                   scratch, st));

@@ -236,6 +236,7 @@ int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* 
   if (batch <= 0 || n == nullptr || opts == nullptr || bytes == nullptr) return DMP_ERR_INVALID_ARG;
   for (int b = 0; b < batch; ++b)
     if (n[b] < 2) return DMP_ERR_INVALID_ARG;
+  if (opts->mode != DMP_OZAKI_INT8 && opts->mode != DMP_OZAKI_BF16) return DMP_ERR_UNSUPPORTED;
   const int beta = opts->mode == DMP_OZAKI_BF16 ? 8 : 7;
   const int s_max = opts->slices > 0 ? opts->slices : (beta == 8 ? 9 : 10);
   *bytes = batch_layout(batch, n, s_max, beta).total;

@@ -3,9 +3,13 @@
 // The digits are small integers (|d| <= 127 for beta = 7, <= 255 for beta = 8),
 // exactly representable in bfloat16, so the slice-pair products run on the
 // 5th-generation tensor cores (tcgen05.mma kind::f16, bf16 x bf16 -> fp32 in
-// tensor memory). An fp32 sum of such products is exact while every partial
+// tensor memory). The nearest digits of the E4M3 mode (beta = 5, |d| <= 16)
+// are exact E4M3 values and run on kind::f8f6f4 at twice the rate, with the
+// same shared-memory layout in bytes (a 128-byte swizzle row holds 128 of them
+// instead of 64). An fp32 sum of such products is exact while every partial
 // sum stays below 2^24 in magnitude; the K loop is therefore cut into chunks of
-// 1024 (beta = 7: 1024 * 127^2 < 2^24) or 256 (beta = 8) K elements. Each chunk
+// 1024 (beta = 7: 1024 * 127^2 < 2^24), 256 (beta = 8) or 65536 (beta = 5:
+// 65536 * 16^2 = 2^24, so a whole level is one chunk) K elements. Each chunk
 // lands in one of two TMEM accumulators; while the tensor core fills the other,
 // eight epilogue warps drain the finished one into exact integer level sums in
 // registers (int32; for beta = 8 a two-word hi/lo integer). At the end of a
@@ -42,7 +46,9 @@ namespace dmp {
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 64;  // bf16 elements per K block: one 128-byte swizzle row
+constexpr int TC_BK = 64;       // bf16 elements per K block: one 128-byte swizzle row
+constexpr int TC_ROW_BYTES = 128;  // bytes of one K block row (the swizzle atom width)
+constexpr int TC_MMA_PER_ATOM = 4;  // MMAs per K block: 32 bytes of K each (16 bf16 or 32 e4m3)
 constexpr int TC_THREADS = 320;
 constexpr int TC_EPI_WARPS = 8;
 
@@ -52,11 +58,12 @@ constexpr int TC_EPI_WARPS = 8;
 // A PAIR stage holds two 64-element K atoms of each operand (8 MMAs per stage
 // barrier round: with 4 the per-stage wait and commit left the tensor pipe
 // idle about a third of the time).
-template <int BN, bool PAIR = false>
+template <int BN, bool PAIR = false, bool F8 = false>
 struct TcCfg {
-  static constexpr int KSUB = PAIR ? 2 : 1;  // 64-element K atoms per stage
-  static constexpr int A_ATOM = TC_BM * TC_BK * 2;
-  static constexpr int B_ATOM = (PAIR ? BN / 2 : BN) * TC_BK * 2;
+  static constexpr int KSUB = PAIR ? 2 : 1;  // K atoms (128-byte rows) per stage
+  static constexpr int ATOM_K = F8 ? 128 : TC_BK;  // K elements per atom
+  static constexpr int A_ATOM = TC_BM * TC_ROW_BYTES;
+  static constexpr int B_ATOM = (PAIR ? BN / 2 : BN) * TC_ROW_BYTES;
   static constexpr int A_BYTES = KSUB * A_ATOM;
   static constexpr int B_BYTES = KSUB * B_ATOM;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -201,6 +208,20 @@ __device__ __forceinline__ void tmem_relinquish_pair() {
 __device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
+__device__ __forceinline__ void umma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_e4m3_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // one MMA of the 256-row pair tile: A rows from both CTAs, B halves from both
 __device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                                uint32_t accumulate) {
@@ -269,6 +290,10 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
+}
+// Instruction descriptor, kind::f8f6f4: fp32 D, E4M3 A and B (format 0), both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 // bounded wait; false on timeout or when another role aborted. CLUSTER: the
@@ -426,11 +451,11 @@ __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA,
 // leader's (rank 0) full barrier; the leader alone issues the cta_group::2
 // MMAs and its commits arrive on the stage and accumulator barriers of both
 // CTAs; both epilogues release a TMEM buffer on the leader's barrier.
-template <int BN, bool WIDE, bool PAIR>
+template <int BN, bool WIDE, bool PAIR, bool F8 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const TcParams p) {
-  using Cfg = TcCfg<BN, PAIR>;
+  using Cfg = TcCfg<BN, PAIR, F8>;
   if (p.done != nullptr && *p.done) return;  // uniform: the whole CTA leaves before any setup
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -519,13 +544,13 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 if (leader) mbar_arrive_expect_tx(full_bar(stage), expect_bytes);
 #pragma unroll
                 for (int u = 0; u < Cfg::KSUB; ++u) {
-                  tma_load_2d_pair(sa + u * Cfg::A_ATOM, jb.ta, fb, (kt + u) * TC_BK, ya);
-                  tma_load_2d_pair(sa + Cfg::A_BYTES + u * Cfg::B_ATOM, jb.tb, fb, (kt + u) * TC_BK, yb);
+                  tma_load_2d_pair(sa + u * Cfg::A_ATOM, jb.ta, fb, (kt + u) * Cfg::ATOM_K, ya);
+                  tma_load_2d_pair(sa + Cfg::A_BYTES + u * Cfg::B_ATOM, jb.tb, fb, (kt + u) * Cfg::ATOM_K, yb);
                 }
               } else {
                 mbar_arrive_expect_tx(full_bar(stage), expect_bytes);
-                tma_load_2d(sa, jb.ta, full_bar(stage), kt * TC_BK, ya);
-                tma_load_2d(sa + Cfg::A_BYTES, jb.tb, full_bar(stage), kt * TC_BK, yb);
+                tma_load_2d(sa, jb.ta, full_bar(stage), kt * Cfg::ATOM_K, ya);
+                tma_load_2d(sa + Cfg::A_BYTES, jb.tb, full_bar(stage), kt * Cfg::ATOM_K, yb);
               }
               armed |= 1u << stage;
               if (++stage == Cfg::STAGES) {
@@ -563,7 +588,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0 && leader) {
-      constexpr uint32_t idesc = idesc_bf16(PAIR ? 2 * TC_BM : TC_BM, BN);
+      constexpr uint32_t idesc = F8 ? idesc_e4m3(PAIR ? 2 * TC_BM : TC_BM, BN) : idesc_bf16(PAIR ? 2 * TC_BM : TC_BM, BN);
       int stage = 0;
       uint32_t phase = 0;
       int buf = 0;
@@ -601,10 +626,16 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
               const uint64_t ad = sdesc_sw128(sa + u * Cfg::A_ATOM);
               const uint64_t bd = sdesc_sw128(sa + Cfg::A_BYTES + u * Cfg::B_ATOM);
 #pragma unroll
-              for (int ks = 0; ks < TC_BK / 16; ++ks) {
-                // advance 16 bf16 = 32 bytes along K inside the swizzled row
+              for (int ks = 0; ks < TC_MMA_PER_ATOM; ++ks) {
+                // advance 32 bytes (16 bf16 or 32 e4m3) along K inside the swizzled row
                 const uint32_t acc = (first && u == 0 && ks == 0) ? 0u : 1u;
-                if (PAIR) {
+                if (F8) {
+                  if (PAIR) {
+                    umma_e4m3_pair(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
+                  } else {
+                    umma_e4m3(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
+                  }
+                } else if (PAIR) {
                   umma_bf16_pair(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
                 } else {
                   umma_bf16(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
@@ -771,15 +802,15 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
               }
             }
           } else {
-            // beta = 7: up to four consecutive levels combine exactly in int64,
-            // T = sum S_L 2^(7 (L_a - L)) < 2^53. At the end of a group (other
-            // than the last) its exact value T 2^(-7 L_a) is added to D in
-            // float64; the last group is finished by the output pass below.
+            // beta = 7 or 5: up to four consecutive levels combine exactly in
+            // int64, T = sum S_L 2^(beta (L_a - L)) < 2^53. At the end of a group
+            // (other than the last) its exact value T 2^(-beta L_a) is added to
+            // D in float64; the last group is finished by the output pass below.
             const int gpos = (s + 1 - L) & 3;
             const int La = L + gpos;
             const bool gend = (gpos == 3) && (L != 2);
             const bool first_group = (s + 1 - L) < 4;
-            const double gscale = ldexp(1.0, -7 * La);
+            const double gscale = ldexp(1.0, -p.beta * La);
 #pragma unroll
             for (int g = 0; g < COLS / 8; ++g) {
               long long told[8];
@@ -790,7 +821,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
               for (int t = 0; t < 8; ++t) {
                 const int c = 8 * g + t;
-                const long long T = (gpos > 0 ? told[t] : 0ll) + (static_cast<long long>(S[c]) << (7 * gpos));
+                const long long T = (gpos > 0 ? told[t] : 0ll) + static_cast<long long>(S[c]) * (1ll << (p.beta * gpos));
                 if (!gend) {
                   st_keep(scr_i + 32 * c, T, pol);
                 } else {
@@ -883,15 +914,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D view of s stacked bf16 digit planes: dim0 = k_pad (contiguous), dim1 = s * rows.
-bool make_plane_map(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows) {
+// 2-D view of s stacked digit planes (bf16, or E4M3 bytes when f8): dim0 = k_pad
+// (contiguous), dim1 = s * rows; boxes of one 128-byte row by box_rows.
+bool make_plane_map(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows,
+                    bool f8 = false) {
   auto fn = encode_fn();
   if (fn == nullptr) return false;
+  const int eb = f8 ? 1 : 2;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(k_pad), static_cast<cuuint64_t>(rows_total)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(k_pad * 2)};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(TC_BK), static_cast<cuuint32_t>(box_rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(k_pad * eb)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(TC_ROW_BYTES / eb), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(planes), dims, strides, box, estr,
+  CUresult r = fn(tm, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(planes), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -905,23 +940,23 @@ bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int6
 
 namespace {
 
-template <int BN, bool WIDE, bool PAIR>
+template <int BN, bool WIDE, bool PAIR, bool F8 = false>
 cudaError_t set_smem_attr() {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_tc_kernel<BN, WIDE, PAIR>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, PAIR>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(ozaki_tc_kernel<BN, WIDE, PAIR, F8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, PAIR, F8>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   return cudaSuccess;
 }
 
-template <int BN, bool WIDE, bool PAIR = false>
+template <int BN, bool WIDE, bool PAIR = false, bool F8 = false>
 cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& p, int grid,
                            cudaStream_t st) {
-  using Cfg = TcCfg<BN, PAIR>;
-  cudaError_t e = set_smem_attr<BN, WIDE, PAIR>();
+  using Cfg = TcCfg<BN, PAIR, F8>;
+  cudaError_t e = set_smem_attr<BN, WIDE, PAIR, F8>();
   if (e != cudaSuccess) return e;
   if (PAIR) {
     cudaLaunchConfig_t cfg;
@@ -937,10 +972,10 @@ cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const T
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, WIDE, PAIR>, ta, tb, p);
+    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, WIDE, PAIR, F8>, ta, tb, p);
     if (e != cudaSuccess) return e;
   } else {
-    ozaki_tc_kernel<BN, WIDE, PAIR><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
+    ozaki_tc_kernel<BN, WIDE, PAIR, F8><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
   }
   count_launch();
   return cudaGetLastError();
@@ -1001,15 +1036,17 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
                             const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   const bool wide = beta == 8;
+  const bool f8 = beta == 5;  // E4M3 nearest digits
   const int BN = wide ? 128 : 256;
-  if (rows_a % TC_BM != 0 || rows_b % BN != 0 || k_pad % TC_BK != 0) return cudaErrorInvalidValue;
-  // beta = 7 products run on CTA pairs (256 x 256 tiles, 2-SM MMA) when rows allow
-  const bool pair = !wide && g_pairing && rows_a % (2 * TC_BM) == 0 && k_pad % (2 * TC_BK) == 0 &&
+  const int atom_k = f8 ? 128 : TC_BK;
+  if (rows_a % TC_BM != 0 || rows_b % BN != 0 || k_pad % atom_k != 0) return cudaErrorInvalidValue;
+  // beta = 7 and 5 products run on CTA pairs (256 x 256 tiles, 2-SM MMA) when rows allow
+  const bool pair = !wide && g_pairing && rows_a % (2 * TC_BM) == 0 && k_pad % (2 * atom_k) == 0 &&
                     tc_max_pairs() > 0;
   const int BM = pair ? 2 * TC_BM : TC_BM;
   CUtensorMap ta, tb;
-  if (!make_plane_map(&ta, A, k_pad, static_cast<int64_t>(s) * rows_a, TC_BM)) return cudaErrorInvalidValue;
-  if (!make_plane_map(&tb, B, k_pad, static_cast<int64_t>(s) * rows_b, pair ? BN / 2 : BN))
+  if (!make_plane_map(&ta, A, k_pad, static_cast<int64_t>(s) * rows_a, TC_BM, f8)) return cudaErrorInvalidValue;
+  if (!make_plane_map(&tb, B, k_pad, static_cast<int64_t>(s) * rows_b, pair ? BN / 2 : BN, f8))
     return cudaErrorInvalidValue;
   TcParams p;
   p.mats = nullptr;
@@ -1018,8 +1055,10 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   p.cur = 0;
   p.s = s;
   p.beta = beta;
-  p.KT = static_cast<int>(k_pad / TC_BK);
-  p.CH = wide ? 4 : 16;  // K chunk: 256 (beta 8) or 1024 (beta 7) keeps fp32 partial sums below 2^24
+  p.KT = static_cast<int>(k_pad / atom_k);
+  // K chunk in atoms: 256 (beta 8), 1024 (beta 7) or 65536 (beta 5) K elements
+  // keep every fp32 partial sum at most 2^24 in magnitude
+  p.CH = wide ? 4 : (f8 ? 512 : 16);
   p.m = m;
   p.n = n;
   p.rows_a = rows_a;
@@ -1050,8 +1089,13 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   p.ntiles = ntiles;
   p.scratch = scratch;
   ProfScope prof(DMP_PROF_PRODUCT, st);
-  if (pair) return launch_tc_impl<256, false, true>(ta, tb, p, 2 * std::min(ntiles, tc_max_pairs()), st);
+  if (pair) {
+    const int grid = 2 * std::min(ntiles, tc_max_pairs());
+    return f8 ? launch_tc_impl<256, false, true, true>(ta, tb, p, grid, st)
+              : launch_tc_impl<256, false, true>(ta, tb, p, grid, st);
+  }
   const int grid = std::min(ntiles, tc_max_ctas());
+  if (f8) return launch_tc_impl<256, false, false, true>(ta, tb, p, grid, st);
   return wide ? launch_tc_impl<128, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
 }
 

@@ -10,6 +10,15 @@
 // starts beta i bits below its top (beta s <= 72 < 96). No floating-point
 // rounding is involved, so the digits are exact.
 //
+// Nearest digits (E4M3 mode, beta 5): the row exponent is one larger, so
+// |x| < 1/2, and d_i = floor(y + 1/2) for y = 2^5 x, x <- y - d_i. With
+// V = floor(x 2^95) in two's complement, the first i digits together are
+// N_i = floor(V 2^-(95 - 5i) + 1/2) (the remainder after them lies in
+// [-1/2, 1/2) units of their last place), so d_i = N_i - 32 N_(i-1) is a signed
+// 5-bit field of V plus the bit below it. Bits of x below 2^-95 never reach a
+// rounding bit (at most 60 + 1 bits are read), so the floor is harmless. Every
+// |d_i| <= 16 is an integer of at most four significant bits, exact in E4M3.
+//
 // One CTA per row. Each thread loads pairs of adjacent entries (16-byte loads,
 // 512 contiguous bytes per warp) and keeps up to 8192 entries of the row in
 // registers, so the row is read from memory once: a max-reduction, then the
@@ -94,6 +103,83 @@ __device__ __forceinline__ void store_digit_pair(uint32_t a0, uint32_t a1, uint3
   }
 }
 
+// V = floor(a 2^(95 - e_row)) = floor(x 2^95) as a 96-bit two's complement
+// integer (words v0: bits 64..95, v1, v2). The significand m of
+// a = +-m 2^(E - 1075), negated in two's complement for a < 0 and sign-extended,
+// is shifted by t = E - 1075 + 95 - e_row like U in fix96: left, or right,
+// where dropping bits of a two's complement number is exactly the floor.
+// |x| < 1/2 keeps |V| < 2^94; 32-bit operations only.
+__device__ __forceinline__ void fix95_signed(double a, int c_row95, uint32_t& v0, uint32_t& v1, uint32_t& v2) {
+  const uint32_t hi = static_cast<uint32_t>(__double2hiint(a));
+  const uint32_t lo = static_cast<uint32_t>(__double2loint(a));
+  const bool neg = (hi >> 31) != 0;
+  const int E = static_cast<int>((hi >> 20) & 0x7ffu);
+  const uint32_t mh = (hi & 0xfffffu) | (E != 0 ? 0x100000u : 0u);
+  const uint32_t s0 = neg ? (0u - lo) : lo;                          // word 0 of +-m
+  const uint32_t s1 = neg ? (~mh + (lo == 0u ? 1u : 0u)) : mh;      // word 1
+  const uint32_t sx = neg ? 0xffffffffu : 0u;                       // words 2, 3, ...
+  const int t = (E == 0 ? 1 : E) - c_row95;  // c_row95 = 1075 + e_row - 95
+  const int z = -(t >> 5);
+  const uint32_t bs = static_cast<uint32_t>(t) & 31u;
+  // word z + d of the sign-extended significand for d = -1 .. 2 (zero below word 0)
+  auto word = [&](int d) { const int i = z + d; return i < 0 ? 0u : (i == 0 ? s0 : (i == 1 ? s1 : sx)); };
+  const uint32_t m_m1 = word(-1), m_0 = word(0), m_1 = word(1), m_2 = word(2);
+  v2 = __funnelshift_l(m_m1, m_0, bs);
+  v1 = __funnelshift_l(m_0, m_1, bs);
+  v0 = __funnelshift_l(m_1, m_2, bs);
+}
+
+// Bits [Q, Q + 6) of V read as a signed 6-bit number (Q a compile-time position).
+template <int Q>
+__device__ __forceinline__ int sfield6(uint32_t v0, uint32_t v1, uint32_t v2) {
+  uint32_t w;
+  int pos;
+  if constexpr (Q >= 64) {
+    w = v0;
+    pos = Q - 64;
+  } else if constexpr (Q >= 32 && Q + 6 <= 64) {
+    w = v1;
+    pos = Q - 32;
+  } else if constexpr (Q >= 32) {
+    w = __funnelshift_r(v1, v0, Q - 32);
+    pos = 0;
+  } else if constexpr (Q + 6 <= 32) {
+    w = v2;
+    pos = Q;
+  } else {
+    w = __funnelshift_r(v2, v1, Q);
+    pos = 0;
+  }
+  int r;
+  asm("bfe.s32 %0, %1, %2, 6;" : "=r"(r) : "r"(w), "r"(pos));
+  return r;
+}
+
+// Nearest digit I + 1 from V: N_i = floor(V / 2^p + 1/2) at p = 95 - 5 i is
+// the rounding of V at that position, and d_i = N_i - 32 N_(i-1) works out to
+// the 5-bit field [p, p + 5) of V read as a signed number plus the bit p - 1,
+// i.e. (u + 1) >> 1 for the signed 6-bit field u = [p - 1, p + 5). The value
+// goes to a float exactly (1.5 2^23 + d + 16 holds d + 16 in its low bits), a
+// pair of them to two E4M3 bytes (exact: |d| <= 16).
+template <int I>
+__device__ __forceinline__ void store_nearest(int s, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t b0,
+                                              uint32_t b1, uint32_t b2, char* base, int pair_off,
+                                              int64_t plane_bytes) {
+  if constexpr (I < kMaxSlices) {
+    if (I < s) {
+      constexpr int Q = 89 - 5 * I;
+      const uint32_t ua = static_cast<uint32_t>((sfield6<Q>(a0, a1, a2) + 33) >> 1);  // d + 16 in [0, 32]
+      const uint32_t ub = static_cast<uint32_t>((sfield6<Q>(b0, b1, b2) + 33) >> 1);
+      const float fa = __uint_as_float(0x4B400000u | ua) - 12582928.0f;
+      const float fb = __uint_as_float(0x4B400000u | ub) - 12582928.0f;
+      uint16_t code;  // upper byte from the first operand: entry j + 1 above entry j
+      asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(code) : "f"(fb), "f"(fa));
+      reinterpret_cast<uint16_t*>(base + I * plane_bytes)[pair_off] = code;
+      store_nearest<I + 1>(s, a0, a1, a2, b0, b1, b2, base, pair_off, plane_bytes);
+    }
+  }
+}
+
 template <int I, int KIND, int BETA>
 __device__ __forceinline__ void store_digits(int s, uint32_t a0, uint32_t a1, uint32_t a2, bool na, uint32_t b0,
                                              uint32_t b1, uint32_t b2, bool nb, char* base, int pair_off,
@@ -141,7 +227,7 @@ __device__ __forceinline__ void max_bits(double a, uint32_t& mxh, uint32_t& mxl,
 // One row r of A (m x k, leading dimension lda) into exps[r] and the s planes
 // (row length k_pad, plane_stride elements apart); one whole CTA per row.
 // Offsets within a row are 32-bit (k_pad < 2^31, checked by the launcher).
-template <int KIND, int BETA>  // KIND 1: int8 digits, 3: bfloat16 holding the same integers
+template <int KIND, int BETA>  // KIND 1: int8 digits, 3: bfloat16 holding the same integers, 4: E4M3 nearest
 __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int64_t r, int64_t m, int k,
                                               int64_t lda, int s, int32_t* __restrict__ exps,
                                               void* __restrict__ planes, int k_pad, int64_t plane_stride,
@@ -185,7 +271,8 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
     mxl = max(mxl, red_l[w]);
     any_bad |= red_bad[w];
   }
-  const int e_row = any_bad ? 0 : row_exponent(mxh, mxl);
+  int e_row = any_bad ? 0 : row_exponent(mxh, mxl);
+  if (KIND == 4 && (mxh | mxl) != 0) ++e_row;  // nearest digits: |x| < 1/2 (a zero row keeps 0)
   if (tid == 0) {
     // a row holding NaN/Inf is marked; the product epilogue then writes NaN
     exps[r] = any_bad ? kBadExp : e_row;
@@ -193,7 +280,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
   }
   const int c_row = 1075 + e_row - 96;
 
-  constexpr int kElemBytes = KIND == 1 ? 1 : 2;
+  constexpr int kElemBytes = (KIND == 1 || KIND == 4) ? 1 : 2;
   char* base = static_cast<char*>(planes) + r * k_pad * kElemBytes;
   const int64_t plane_bytes = plane_stride * kElemBytes;
   for (int c0 = 0;;) {
@@ -201,11 +288,18 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
     for (int q = 0; q < kPairs; ++q) {
       const int j = c0 + 2 * (tid + kSplitThreads * q);
       if (j < k_pad) {
-        uint32_t a0, a1, a2, b0, b1, b2;
-        bool na, nb;
-        fix96(v[q].x, c_row, a0, a1, a2, na);
-        fix96(v[q].y, c_row, b0, b1, b2, nb);
-        store_digits<0, KIND, BETA>(s, a0, a1, a2, na, b0, b1, b2, nb, base, j >> 1, plane_bytes);
+        if constexpr (KIND == 4) {
+          uint32_t a0, a1, a2, b0, b1, b2;
+          fix95_signed(v[q].x, c_row + 1, a0, a1, a2);
+          fix95_signed(v[q].y, c_row + 1, b0, b1, b2);
+          store_nearest<0>(s, a0, a1, a2, b0, b1, b2, base, j >> 1, plane_bytes);
+        } else {
+          uint32_t a0, a1, a2, b0, b1, b2;
+          bool na, nb;
+          fix96(v[q].x, c_row, a0, a1, a2, na);
+          fix96(v[q].y, c_row, b0, b1, b2, nb);
+          store_digits<0, KIND, BETA>(s, a0, a1, a2, na, b0, b1, b2, nb, base, j >> 1, plane_bytes);
+        }
       }
     }
     if (k_pad - c0 <= kSweep) break;
@@ -282,6 +376,9 @@ cudaError_t launch_split_rows(const double* A, int64_t m, int64_t k, int64_t lda
                                                             flag, done);
   } else if (elem_kind == 3 && beta == 8) {
     split_rows_kernel<3, 8><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
+                                                            flag, done);
+  } else if (elem_kind == 4 && beta == 5) {
+    split_rows_kernel<4, 5><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
                                                             flag, done);
   } else {
     return cudaErrorInvalidValue;

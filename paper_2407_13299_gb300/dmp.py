@@ -16,10 +16,10 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdmp.so")
 
-MODES = {"fp64": 0, "int8": 1, "bf16": 2}
+MODES = {"fp64": 0, "int8": 1, "bf16": 2, "e4m3": 3}
 METHODS = {"pm": 0, "trs4": 1, "sp2": 2}
 EXECUTORS = {"auto": 0, "imma": 1, "tc": 2}
-BETA = {"int8": 7, "bf16": 8}
+BETA = {"int8": 7, "bf16": 8, "e4m3": 5}
 
 OK, NOT_CONVERGED, STALLED, C_OUT_OF_RANGE = 0, 1, 2, 3
 ERR_INVALID_ARG, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_WORKSPACE = -1, -2, -3, -4, -5, -6
@@ -264,11 +264,12 @@ def ozaki_level_sums(A: torch.Tensor, B: torch.Tensor, mode="int8", slices=7, ex
 
 def ozaki_split(A: torch.Tensor, mode="int8", slices=7, executor="auto", stream=None):
     """(row exponents int32 (m,), digit planes (s, m, k)): int8 for the IMMA
-    executor, bfloat16 for the tcgen05 executor."""
+    executor, bfloat16 for the tcgen05 executor, raw E4M3 bytes (uint8) for
+    mode "e4m3"."""
     _require_cuda(A)
     m, k = A.shape
     ex = executor if executor != "auto" else ("imma" if mode == "int8" else "tc")
-    dt = torch.int8 if ex == "imma" else torch.bfloat16
+    dt = torch.uint8 if mode == "e4m3" else (torch.int8 if ex == "imma" else torch.bfloat16)
     exps = torch.empty(m, dtype=torch.int32, device=A.device)
     digits = torch.empty((slices, m, k), dtype=dt, device=A.device)
     ws = workspace(gemm_workspace_bytes(m, 1, k, mode, slices, ex), A.device)
