@@ -52,11 +52,14 @@ def parse_args():
     ap.add_argument("--n", "--size", dest="n", type=int, default=8192, help="matrix size (8192 is the benchmark workload)")
     ap.add_argument("--slices", type=int, default=0, help="0: smallest s >= 6 meeting the energy target")
     ap.add_argument("--executor", default="tc", choices=["tc", "imma"])
+    ap.add_argument("--mode", default="int8", choices=["int8", "e4m3"],
+                    help="slice mode of the timed purification (int8: the headline; e4m3: nearest 5-bit digits "
+                         "on kind::f8f6f4, tcgen05 executor only)")
     ap.add_argument("--fp64", default="full", choices=["full", "skip"], help="time the FP64 purification once")
     ap.add_argument("--cpu-samples", type=int, default=5, help="oracle samples for cpu_baseline (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--targets", choices=("on", "off"), default="on",
-                    help="also time INT8 and BF16 at 1e-5 and 1e-8 (untimed search, 2 timed runs each)")
+                    help="also time INT8, BF16 and E4M3 at 1e-5 and 1e-8 (untimed search, 2 timed runs each)")
     ap.add_argument("--refine", default="auto",
                     help="refinement step after the loop: auto (pick the cheapest setting meeting the target, "
                          "with or without it), off, or the slice count of its products (-1: FP64)")
@@ -175,7 +178,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(H, n_occ, s, beta, iters, rows=512, cols=512, seed=0, refine_s=0):
+def oracle_sample(H, n_occ, s, beta, iters, rows=512, cols=512, seed=0, refine_s=0, rounding="trunc"):
     """One bounded sample of the CPU oracle on this workload, extrapolated to a
     whole purification (seconds).
 
@@ -202,13 +205,13 @@ def oracle_sample(H, n_occ, s, beta, iters, rows=512, cols=512, seed=0, refine_s
     r0 = int(rng.integers(0, n - rows + 1))
     c0 = int(rng.integers(0, n - cols + 1))
     t0 = time.perf_counter()
-    e, DA, _ = oz.split_rows(P[r0:r0 + rows], s, beta)
+    e, DA, _ = oz.split_rows(P[r0:r0 + rows], s, beta, rounding)
     t_sa = time.perf_counter() - t0
     t0 = time.perf_counter()
-    f, DBt, _ = oz.split_cols(P[:, c0:c0 + cols], s, beta)
+    f, DBt, _ = oz.split_cols(P[:, c0:c0 + cols], s, beta, rounding)
     t_sb = time.perf_counter() - t0
     t0 = time.perf_counter()
-    S = oz.level_sums(DA, DBt, beta)
+    S = oz.level_sums(DA, DBt, beta, rounding)
     t_lv = time.perf_counter() - t0
     t0 = time.perf_counter()
     oz.recombine(S, e, f, s, beta)
@@ -223,11 +226,11 @@ def oracle_sample(H, n_occ, s, beta, iters, rows=512, cols=512, seed=0, refine_s
     per_refine_product = 0.0
     if refine_s > 0:
         t0 = time.perf_counter()
-        e, DA, _ = oz.split_rows(P[r0:r0 + rows], refine_s, beta)
-        f, DBt, _ = oz.split_cols(P[:, c0:c0 + cols], refine_s, beta)
+        e, DA, _ = oz.split_rows(P[r0:r0 + rows], refine_s, beta, rounding)
+        f, DBt, _ = oz.split_cols(P[:, c0:c0 + cols], refine_s, beta, rounding)
         t_sp = time.perf_counter() - t0
         t0 = time.perf_counter()
-        oz.recombine(oz.level_sums(DA, DBt, beta), e, f, refine_s, beta)
+        oz.recombine(oz.level_sums(DA, DBt, beta, rounding), e, f, refine_s, beta)
         t_pr = time.perf_counter() - t0
         per_refine_product = t_sp * (n / rows) + t_pr * (n / rows) * (n / cols)
         total += 2.0 * per_refine_product + t_it
@@ -328,24 +331,32 @@ def run_ours(args):
     # with or without the paper's refinement step (one McWeeny step after the loop,
     # Sec. "Precision Requirements Sweep", in full double precision: products of 8
     # slices, 56 digit bits >= the 53 of FP64).
-    REFINE_SLICES = 8
+    # (E4M3: refinement products of 11 nearest 5-bit digits, 54 bits)
+    mode = args.mode
+    if mode == "e4m3" and args.executor != "tc":
+        raise SystemExit("--mode e4m3 needs --executor tc")
+    REFINE_SLICES = 11 if mode == "e4m3" else 8
     fixed_refine = None if args.refine in ("auto", "off") else int(args.refine)
     if args.slices:
         cands = [(args.slices, fixed_refine or 0)]
     elif args.refine == "off":
-        cands = [(6, 0), (7, 0), (8, 0), (9, 0)]
+        cands = [(c, 0) for c in ((6, 7, 8, 9, 10) if mode == "e4m3" else (6, 7, 8, 9))]
     elif fixed_refine is not None:
-        cands = [(c, fixed_refine) for c in (4, 5, 6, 7, 8)]
+        cands = [(c, fixed_refine) for c in ((5, 6, 7, 8, 9) if mode == "e4m3" else (4, 5, 6, 7, 8))]
+    elif mode == "e4m3":
+        cands = [(5, REFINE_SLICES), (6, 0), (6, REFINE_SLICES), (7, 0), (7, REFINE_SLICES), (8, 0), (9, 0),
+                 (10, 0)]
     else:
         cands = [(4, REFINE_SLICES), (5, REFINE_SLICES), (6, 0), (6, REFINE_SLICES), (7, 0), (7, REFINE_SLICES),
                  (8, 0), (9, 0)]
     s, refine = cands[-1]
     tune = []
     ws = dmp.workspace(max(dmp.purify_workspace_bytes(n, dmp.make_opts("int8", 9, args.executor, refine=9)),
-                           dmp.purify_workspace_bytes(n, dmp.make_opts("bf16", 9, args.executor, refine=9))), dev)
+                           dmp.purify_workspace_bytes(n, dmp.make_opts("bf16", 9, args.executor, refine=9)),
+                           dmp.purify_workspace_bytes(n, dmp.make_opts("e4m3", 11, "tc", refine=11))), dev)
     P = torch.empty_like(H)
     for cs, cr in cands:
-        _, info = dmp.purify(H, n_occ, mode="int8", slices=cs, executor=args.executor, refine=cr, P=P, ws=ws)
+        _, info = dmp.purify(H, n_occ, mode=mode, slices=cs, executor=args.executor, refine=cr, P=P, ws=ws)
         rel = abs(info["energy"] - E_star) / abs(E_star)
         tune.append({"slices": cs, "refine_slices": cr, "rel_energy": rel, "iters": info["iters"]})
         if rel <= REL_ENERGY_TARGET or len(cands) == 1:
@@ -353,7 +364,7 @@ def run_ours(args):
             break
 
     def step(slices=None, refine_slices=None):
-        return dmp.purify(H, n_occ, mode="int8", slices=slices or s, executor=args.executor,
+        return dmp.purify(H, n_occ, mode=mode, slices=slices or s, executor=args.executor,
                           refine=refine if refine_slices is None else refine_slices, P=P, ws=ws)
 
     for _ in range(max(args.warmup, 0)):
@@ -367,14 +378,14 @@ def run_ours(args):
     # (measured after the warm-up steps and before the timed region, so that both
     # run in the same warm state of the GPU; the first call through the host path,
     # whose device copy of H comes from torch's caching allocator, is untimed)
-    dmp.purify_host(H_host, n_occ, out=P_host, mode="int8", slices=s, executor=args.executor, ws=ws, P=P,
+    dmp.purify_host(H_host, n_occ, out=P_host, mode=mode, slices=s, executor=args.executor, ws=ws, P=P,
                     refine=refine)
     torch.cuda.synchronize()
     for _ in range(max(args.e2e_steps, 1)):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dmp.purify_host(H_host, n_occ, out=P_host, mode="int8", slices=s, executor=args.executor, ws=ws, P=P,
+        dmp.purify_host(H_host, n_occ, out=P_host, mode=mode, slices=s, executor=args.executor, ws=ws, P=P,
                         refine=refine)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
@@ -432,13 +443,19 @@ def run_ours(args):
     mix = {s: 2 * info["iters"] + 1}
     if refined and refine > 0:
         mix[refine] = mix.get(refine, 0) + 2
-    traffic = kernel_traffic("gemm_tc.cu", "ozaki_tc_kernel_n8192.md", mix) \
-        if args.executor == "tc" and n == 8192 else None
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "kernel": "ozaki_tc_kernel<256,false,true> (CTA pairs, 2-SM MMA)" if args.executor == "tc" else
+    f8 = mode == "e4m3"
+    traffic = kernel_traffic("gemm_tc.cu", "ozaki_tc_kernel_e4m3_n8192.md" if f8 else "ozaki_tc_kernel_n8192.md",
+                             mix) if args.executor == "tc" and n == 8192 else None
+    # E4M3 slice pairs run on kind::f8f6f4 at twice the bf16 rate: peak = measured
+    # bf16 x the nominal fp8 / bf16 ratio 2
+    run_peak = peak * (2.0 if f8 else 1.0)
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": run_peak, "unit": "TFLOP/s",
+                "frac": achieved / run_peak, "traffic": traffic,
+                "kernel": ("ozaki_tc_kernel<256,false,true,true> (CTA pairs, 2-SM MMA, kind::f8f6f4)" if f8 else
+                           "ozaki_tc_kernel<256,false,true> (CTA pairs, 2-SM MMA)") if args.executor == "tc" else
                 "ozaki_imma_kernel",
-                "peak_source": f"{peak_src} bf16 sustained (kernel timed inside a long step)",
+                "peak_source": (f"{peak_src} bf16 sustained x 2 (nominal fp8/bf16 ratio)" if f8 else
+                                f"{peak_src} bf16 sustained") + " (kernel timed inside a long step)",
                 "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
                 "launches": prod_n,
                 "launch_mix": f"{2 * info['iters'] + 1} x s={s}" + (f" + 2 x s={refine}" if refined else "") +
@@ -455,10 +472,11 @@ def run_ours(args):
     # ---- the cheapest setting without the refinement step, timed the same way (2 steps)
     plain = None
     if refine != 0 and not args.slices:
-        for cs in (6, 7, 8, 9):
+        plain_cands = (6, 7, 8, 9, 10) if mode == "e4m3" else (6, 7, 8, 9)
+        for cs in plain_cands:
             _, pi = step(cs, 0)
             prel = abs(pi["energy"] - E_star) / abs(E_star)
-            if prel <= REL_ENERGY_TARGET or cs == 9:
+            if prel <= REL_ENERGY_TARGET or cs == plain_cands[-1]:
                 break
         step(cs, 0)
         torch.cuda.synchronize()
@@ -476,10 +494,17 @@ def run_ours(args):
     # and 1e-8 relative band-energy error, each with its cheapest setting
     # (candidates by product work: 101 loop products of p(s) pairs, plus about 72
     # pair-products for the refinement; refinement products of 56 digit bits)
+    # Refinement products carry at least the 53 bits of FP64: 8 slices of 7 bits,
+    # 7 of 8, or 11 nearest digits of 5 bits (54). E4M3 slice pairs run at twice
+    # the bf16 tensor rate, so its peak is the measured bf16 one times the
+    # nominal fp8 / bf16 ratio of 2.
+    refine_of = {7: 8, 8: 7, 5: 11}
+    max_loop = {7: 9, 8: 8, 5: 11}
+
     def cheapest(mode, beta, target, method="pm"):
-        r_s = 8 if beta == 7 else 7
-        cand = sorted(((cs, cr) for cs in range(3, 10 if beta == 7 else 9) for cr in (0, r_s)),
-                      key=lambda c: 101 * c[0] * (c[0] + 1) // 2 + (72 if c[1] else 0))
+        r_s = refine_of[beta]
+        cand = sorted(((cs, cr) for cs in range(3, max_loop[beta] + 1) for cr in (0, r_s)),
+                      key=lambda c: 101 * pairs(c[0]) + (2 * pairs(c[1]) if c[1] else 0))
         for cs, cr in cand:
             _, ti = dmp.purify(H, n_occ, mode=mode, slices=cs, executor=args.executor, refine=cr, P=P, ws=ws,
                                method=method)
@@ -487,6 +512,8 @@ def run_ours(args):
             if trel <= target:
                 break
         torch.cuda.synchronize()
+        dmp.profile_enable(True)
+        dmp.profile_reset()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -494,13 +521,28 @@ def run_ours(args):
             dmp.purify(H, n_occ, mode=mode, slices=cs, executor=args.executor, refine=cr, P=P, ws=ws, method=method)
         b.record(stream)
         torch.cuda.synchronize()
-        return {"method": method, "mode": f"ozaki-{mode}", "target": target, "slices": cs, "refine_slices": cr,
-                "value": a.elapsed_time(b) / 2e3, "unit": UNIT, "rel_energy_error": trel, "iters": ti["iters"]}
+        dmp.profile_enable(False)
+        t_ms, t_n = dmp.profile_read(dmp.PROF_PRODUCT)
+        out = {"method": method, "mode": f"ozaki-{mode}", "target": target, "slices": cs, "refine_slices": cr,
+               "value": a.elapsed_time(b) / 2e3, "unit": UNIT, "rel_energy_error": trel, "iters": ti["iters"]}
+        if method == "pm" and args.executor == "tc" and t_n > 0:
+            # slice-pair flops of the two timed runs over their product launches
+            t_flops = 2 * ((2 * ti["iters"] + 1) * pairs(cs) + (2 * pairs(cr) if ti.get("refined") else 0)) * \
+                unit_flops
+            rate = t_flops / (t_ms / 1e3) / 1e12
+            tpeak = peak * (2.0 if mode == "e4m3" else 1.0)
+            out["products"] = {"ms_per_purification": t_ms / 2, "launches": t_n, "achieved_tflops": rate,
+                               "peak_tflops": tpeak, "frac": rate / tpeak,
+                               "peak_note": ("measured bf16 sustained x 2 (nominal fp8/bf16 ratio), "
+                                             "kind::f8f6f4" if mode == "e4m3" else "measured bf16 sustained")}
+        return out
 
     targets = []
     methods = []
     if args.targets == "on" and not args.slices:
-        for mode, beta in (("int8", 7), ("bf16", 8)):
+        for mode, beta in (("int8", 7), ("bf16", 8), ("e4m3", 5)):
+            if mode == "e4m3" and args.executor != "tc":
+                continue  # E4M3 digits run on the tcgen05 executor only
             for target in (1e-5, 1e-8):
                 targets.append(cheapest(mode, beta, target))
         # the other recursions of the family (TRS4 is the one the paper runs) at the
@@ -532,7 +574,8 @@ def run_ours(args):
         H_np = H.cpu().numpy()
         vals = []
         for k in range(args.cpu_samples):
-            v, _ = oracle_sample(H_np, n_occ, s, 7, info["iters"], seed=100 + k, refine_s=max(refine, 0))
+            v, _ = oracle_sample(H_np, n_occ, s, 5 if mode == "e4m3" else 7, info["iters"], seed=100 + k,
+                                 refine_s=max(refine, 0), rounding="nearest" if mode == "e4m3" else "trunc")
             vals.append(v)
         cpu = {"value": float(statistics.median(vals)), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{args.cpu_samples} samples: the oracle's Ozaki product (s={s}) on a 512x512 output block "
@@ -546,8 +589,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": workload_name(w), "mode": "ozaki-int8", "slices": s, "executor": args.executor,
+            "vs_baseline": None, "dtype": "e4m3" if mode == "e4m3" else "bf16", "data": "synthetic",
+            "config": {"workload": workload_name(w), "mode": f"ozaki-{mode}", "slices": s, "executor": args.executor,
                        "refinement": ("one McWeeny step after the loop (Sec. Precision Requirements Sweep) with "
                                       f"Ozaki products of {refine} slices" if refine > 0 else
                                       ("one McWeeny step with FP64 products" if refine < 0 else "none")),
@@ -557,7 +600,8 @@ def run_ours(args):
                        "idempotency": info["idem"], "without_refinement": plain, "targets": targets,
                        "other_methods": methods,
                        "l2": (f"inputs larger than L2 (H {n * n * 8 / 2**20:.0f} MiB, digit planes "
-                              f"{2 * s * n * n * 2 / 2**30:.2f} GiB)"), "slice_tuning": tune,
+                              f"{2 * s * n * n * (1 if mode == 'e4m3' else 2) / 2**30:.2f} GiB)"),
+                       "slice_tuning": tune,
                        "replicas": world},
             "roofline": roofline,
             "fp64_equivalent": fp64_equivalent,
