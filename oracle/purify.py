@@ -42,6 +42,13 @@ product with enough slices to reach FP64 accuracy); the returned P, energy and
 band energy are those of P', and the unrefined values are kept. The step is
 the update above with c = 1/2, but is written here as printed.
 
+FP32 storage (Sec. "Mixed Precision Purification"): the paper finds that the
+matrices of purification may be stored in FP32 as long as they are multiplied
+with FP64 accumulation, and tests it by rounding every matrix that enters a
+product to FP32. Reading: `store` rounds every matrix the loop keeps between
+products (P_0, each P^2, each updated P) to the nearest float32; P^3 is used at
+once and the refined P is left as computed.
+
 Energies: tr(P H) is reported as `energy`; the paper's band energy
 Tr(H K) = 2 tr(P H) is reported as `band_energy` (Sec. "Error Evaluation
 Criteria"), as are the RMSD of P and the commutator norm ||H K - K H||_F.
@@ -50,8 +57,10 @@ Parity: pinned. The tests check the closed-form projector of H = Q diag(e) Q^T,
 tr(P) = n_occ, idempotency, c in [0, 1], trace conservation of every update on
 arbitrary spectra, energy monotonicity, the c = 1/2 reduction to McWeeny's
 printed step, the Gershgorin enclosure of the spectrum, and agreement with a
-dense eigensolver on tiny inputs. The exact iteration counts of the Ozaki modes
-are measured outputs and are not pinned.
+dense eigensolver on tiny inputs; with FP32 storage, that every stored matrix
+is a float32 value and the projector and energy are reached to FP32
+resolution. The exact iteration counts of the Ozaki modes are measured outputs
+and are not pinned.
 """
 
 from __future__ import annotations
@@ -129,6 +138,13 @@ def pm_update(P, X2, X3, c):
     return alpha * P + b2 * X2 + b3 * X3
 
 
+def fp32_store(M):
+    """A matrix as FP32 storage holds it (Sec. "Mixed Precision Purification":
+    matrices kept in FP32, products formed with FP64 accumulation): every
+    element rounded to the nearest float32 (ties to even), returned as float64."""
+    return np.asarray(M, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
 def mcweeny_step(P, product=None):
     """One McWeeny step P' = 3 P^2 - 2 P^3 (the equation printed in Sec.
     "Precision Requirements Sweep"), with P^2 = P P and P^3 = P P^2 formed by
@@ -140,7 +156,7 @@ def mcweeny_step(P, product=None):
 
 
 def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
-           energy_tol: float = 0.0, record: bool = False, refine_product=None):
+           energy_tol: float = 0.0, record: bool = False, refine_product=None, store=None):
     """Canonical purification of H with the stopping rules of the module header.
 
     `product(A, B)` forms every matrix product (FP64 by default; pass a partial
@@ -153,10 +169,18 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
     products use it (the refinement of the module header); P, energy and
     band_energy then describe the refined matrix, energy_unrefined the one
     before, and idem stays that of the unrefined iterate.
+
+    `store(M)` is applied to every matrix the loop keeps between products: the
+    initial guess, each P^2 and each updated P (fp32_store for FP32 storage;
+    X3 is used at once and the refined P is left as computed). With
+    record=True the P^2 of every pass are returned as well ("squares").
     """
     product = fp64_product if product is None else product
+    store = (lambda M: M) if store is None else store
     H = np.asarray(H, dtype=np.float64)
     P, init = initial_guess(H, n_occ)
+    P = store(P)
+    squares = [] if record else None
     band = []
     idems = []
     traces = []
@@ -166,7 +190,9 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
     status = NOT_CONVERGED
     k = 0
     while True:
-        X2 = product(P, P)
+        X2 = store(product(P, P))
+        if record:
+            squares.append(X2.copy())
         t1 = float(np.trace(P))
         t2 = float(np.trace(X2))
         idem = float(np.linalg.norm(X2 - P))
@@ -197,7 +223,7 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
             status = C_OUT_OF_RANGE
             break
         alpha, b2, b3, br = pm_weights(c)
-        P = alpha * P + b2 * X2 + b3 * X3
+        P = store(alpha * P + b2 * X2 + b3 * X3)
         cs.append(c)
         branches.append(br)
         if record:
@@ -215,6 +241,7 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
                branch_history=branches, init=init)
     if record:
         out["iterates"] = iterates
+        out["squares"] = squares
     return out
 
 

@@ -81,9 +81,11 @@ def trs4_z(X, X2, gamma: float):
 
 
 def purify(H, n_occ: int, method: str = TRS4, tol: float = 1e-10, max_iter: int = 100, product=None,
-           record: bool = False):
+           record: bool = False, store=None):
     """SP2 or TRS4 purification of H with the stopping rules of the module
-    header; `product(A, B)` forms every matrix product (FP64 by default).
+    header; `product(A, B)` forms every matrix product (FP64 by default);
+    `store(M)` is applied to every matrix kept between products (X_0, each X^2,
+    each updated X and the TRS4 factor Z; purify.fp32_store for FP32 storage).
     Returns P (= the stopped iterate), status, iters (updates applied), energy
     = tr(P H), band_energy, idem, trace, the histories (idempotency, trace,
     steps: 'sq' / 'up' for SP2 steps, gamma for TRS4 steps) and, with
@@ -91,17 +93,19 @@ def purify(H, n_occ: int, method: str = TRS4, tol: float = 1e-10, max_iter: int 
     if method not in (SP2, TRS4):
         raise ValueError("method must be 'sp2' or 'trs4'")
     product = fp64_product if product is None else product
+    store = (lambda M: M) if store is None else store
     H = np.asarray(H, dtype=np.float64)
     n = H.shape[0]
     if not (0 < n_occ < n):
         raise ValueError("need 0 < n_occ < n")
     X, init = initial_guess(H)
+    X = store(X)
     idems, traces, steps = [], [], []
     iterates = [X.copy()] if record else None
     status = NOT_CONVERGED
     k = 0
     while True:
-        X2 = product(X, X)
+        X2 = store(product(X, X))
         t1 = float(np.trace(X))
         t2 = float(np.trace(X2))
         idem = float(np.linalg.norm(X2 - X))
@@ -121,18 +125,18 @@ def purify(H, n_occ: int, method: str = TRS4, tol: float = 1e-10, max_iter: int 
                 X = X2
                 steps.append("sq")
             else:
-                X = 2.0 * X - X2
+                X = store(2.0 * X - X2)
                 steps.append("up")
         else:
             t3 = float(np.sum(X * X2))
             t4 = float(np.sum(X2 * X2))
             gamma = trs4_gamma(t3, t4, idem, n_occ)
             if gamma > 6.0:
-                X = 2.0 * X - X2
+                X = store(2.0 * X - X2)
             elif gamma < 0.0:
                 X = X2
             else:
-                X = product(X2, trs4_z(X, X2, gamma))
+                X = store(product(X2, store(trs4_z(X, X2, gamma))))
             steps.append(gamma)
         if record:
             iterates.append(X.copy())

@@ -16,6 +16,7 @@ import pytest
 
 from oracle import ozaki as oz
 from oracle import purify as pu
+from oracle import variants as va
 from synth import config_hamiltonian, make_hamiltonian
 
 
@@ -285,3 +286,59 @@ def test_refinement_fixes_the_energy_of_a_low_slice_purification():
     assert r64["refined"] and after < 1e-2 * before and after < 1e-9
     assert np.max(np.abs(r9["P"] - r64["P"])) < 1e-13
     assert r64["iters"] == r9["iters"] and r64["band_energy"] == 2.0 * r64["energy"]
+
+
+# ----------------------------------------------------------------- FP32 storage (Sec. "Mixed Precision Purification")
+
+def _is_fp32_valued(M):
+    return np.array_equal(M, M.astype(np.float32).astype(np.float64))
+
+
+def test_fp32_storage_keeps_float32_values_and_reaches_the_projector():
+    """Every stored matrix is an FP32 value; the result still approaches the
+    exact projector to FP32 resolution, and the band energy (second order in
+    the error of P) far closer: the paper's finding that FP32 storage with
+    FP64 accumulation is adequate."""
+    h = make_hamiltonian(96, 24, seed=7)
+    P_star = _projector(h.Q, 24)
+    E_star = float(np.sum(h.e[:24]))
+    r = pu.purify(h.H, 24, tol=1e-10, store=pu.fp32_store, record=True)
+    assert all(_is_fp32_valued(P) for P in r["iterates"])
+    assert all(_is_fp32_valued(X2) for X2 in r["squares"])
+    err = np.max(np.abs(r["P"] - P_star))
+    assert 1e-9 < err < 2e-6  # FP32 resolution: well above FP64's, well below single digits
+    assert abs(r["energy"] - E_star) <= 2e-8 * abs(E_star)
+    ref = pu.purify(h.H, 24, tol=1e-10)
+    assert np.max(np.abs(ref["P"] - P_star)) < 1e-12  # the same loop with FP64 storage
+
+
+def test_fp32_storage_with_ozaki_products():
+    h = make_hamiltonian(96, 24, seed=9)
+    P_star = _projector(h.Q, 24)
+    r = pu.purify(h.H, 24, tol=1e-10, product=partial(oz.ozaki_gemm, s=7, beta=7), store=pu.fp32_store,
+                  record=True)
+    assert all(_is_fp32_valued(P) for P in r["iterates"])
+    assert np.max(np.abs(r["P"] - P_star)) < 2e-6
+
+
+def test_fp32_storage_in_trs4_and_sp2():
+    h = make_hamiltonian(96, 24, seed=10)
+    P_star = _projector(h.Q, 24)
+    for method in ("trs4", "sp2"):
+        r = va.purify(h.H, 24, method=method, tol=1e-10, store=pu.fp32_store, record=True)
+        assert all(_is_fp32_valued(X) for X in r["iterates"]), method
+        assert np.max(np.abs(r["P"] - P_star)) < 2e-6, method
+
+
+def test_planted_store_of_the_initial_guess_only_fails():
+    """A storage rule applied to P_0 alone leaves the later iterates off the FP32 grid."""
+    h = make_hamiltonian(64, 16, seed=11)
+    calls = {"n": 0}
+
+    def first_only(M):
+        calls["n"] += 1
+        return pu.fp32_store(M) if calls["n"] == 1 else M
+
+    r = pu.purify(h.H, 16, tol=1e-10, store=first_only, record=True)
+    assert _is_fp32_valued(r["iterates"][0])
+    assert not all(_is_fp32_valued(P) for P in r["iterates"])
