@@ -83,7 +83,17 @@ enum {
  * h_min, h_max of the initial guess as constants (no gradient through their
  * extreme rows). At convergence both choices agree to the convergence level,
  * because the converged projector does not depend on P_0. */
-enum { DMP_FLAG_BOUNDS_CONSTANT = 1 };
+/* DMP_FLAG_FP32_STORAGE: every matrix the purification stores between
+ * products (the initial guess, each P_k, each X^2, and for SP2/TRS4 the SP2
+ * updates and the TRS4 factor Z) is rounded to the nearest FP32 value when it
+ * is written, while the products, the recombination, the traces and the
+ * coefficients stay in FP64: the storage experiment of Sec. "Mixed Precision
+ * Purification", where matrices are held in FP32 and multiplied with FP64
+ * accumulation. The buffers themselves stay FP64 (this reproduces the
+ * precision of FP32 storage, not its memory saving). The refinement step
+ * writes its result unrounded. Not offered with a tape, in the backward pass
+ * or in the batched call (DMP_ERR_UNSUPPORTED). */
+enum { DMP_FLAG_BOUNDS_CONSTANT = 1, DMP_FLAG_FP32_STORAGE = 2 };
 
 /*
  * Purification method (dmp_opts.method).

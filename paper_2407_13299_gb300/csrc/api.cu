@@ -35,6 +35,7 @@ struct Opts {
   double tol, energy_tol;
   int refine;  // 0 off, -1 FP64 products, > 0 Ozaki slices of the refinement step
   int method;  // DMP_METHOD_*
+  bool store32;  // DMP_FLAG_FP32_STORAGE
 };
 
 int normalize(const dmp_opts* o, Opts& out) {
@@ -65,6 +66,7 @@ int normalize(const dmp_opts* o, Opts& out) {
   out.tol = o->tol == 0.0 ? 1e-10 : o->tol;
   out.energy_tol = o->energy_tol;
   if (!(out.tol >= 0.0) || !(out.energy_tol >= 0.0)) return DMP_ERR_INVALID_ARG;
+  out.store32 = (o->flags & DMP_FLAG_FP32_STORAGE) != 0;
   out.method = o->method;
   if (out.method < DMP_METHOD_PM || out.method > DMP_METHOD_SP2) return DMP_ERR_INVALID_ARG;
   out.refine = o->refine_slices;
@@ -274,7 +276,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     return DMP_ERR_UNSUPPORTED;
   if (o.refine > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.refine, o.mode))
     return DMP_ERR_UNSUPPORTED;
-  if ((o.refine != 0 || o.method != DMP_METHOD_PM) && tape != nullptr) return DMP_ERR_UNSUPPORTED;
+  if ((o.refine != 0 || o.method != DMP_METHOD_PM || o.store32) && tape != nullptr) return DMP_ERR_UNSUPPORTED;
   const PurifyLayout L = purify_layout(n, o);
   if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
   TapeLayout TL{};
@@ -304,6 +306,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   init.max_iter = o.max_iter;
   init.status = DMP_NOT_CONVERGED;
   init.method = o.method;
+  init.store32 = o.store32 ? 1 : 0;
   DMP_CUDA(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st));
   DMP_CUDA(launch_gershgorin_init(H, n, ldh, n_occ, rowbuf, state, P, ldp, st));
 
@@ -325,6 +328,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     e2.kind = EPI_SYM_STORE;
     e2.C = X2;
     e2.ldc = n;
+    e2.round32 = o.store32 ? 1 : 0;
     if (o.mode == DMP_FP64) {
       DMP_CUDA(launch_gemm_f64(cur, ldcur, cur, ldcur, n, n, n, 1, e2, done, st));
     } else {
@@ -358,6 +362,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
         ez.kind = EPI_SYM_STORE;
         ez.C = cur;
         ez.ldc = ldcur;
+        ez.round32 = o.store32 ? 1 : 0;
         if (o.mode == DMP_FP64) {
           DMP_CUDA(launch_gemm_f64(X2, n, alt, ldalt, n, n, n, 1, ez, done, st));
         } else {
@@ -383,6 +388,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     e3.X2 = X2;
     e3.ldx = n;
     e3.state = state;
+    e3.round32 = o.store32 ? 1 : 0;
     if (o.mode == DMP_FP64) {
       DMP_CUDA(launch_gemm_f64(cur, ldcur, X2, n, n, n, n, 1, e3, done, st));
     } else {
@@ -643,7 +649,7 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
   Opts o;
   int rc = normalize(opts, o);
   if (rc != DMP_OK) return rc;
-  if (o.method != DMP_METHOD_PM || o.refine != 0) return DMP_ERR_UNSUPPORTED;  // the tape is canonical only
+  if (o.method != DMP_METHOD_PM || o.refine != 0 || o.store32) return DMP_ERR_UNSUPPORTED;  // canonical tapes only
   if (H == nullptr || tape == nullptr || dLdP == nullptr || dLdH == nullptr || ws == nullptr)
     return DMP_ERR_INVALID_ARG;
   if (n < 2 || n_occ <= 0 || n_occ >= n) return DMP_ERR_INVALID_ARG;

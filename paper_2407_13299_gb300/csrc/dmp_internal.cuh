@@ -62,8 +62,14 @@ struct PurifyState {
   // options copied for the device
   double tol, energy_tol;
   int32_t max_iter;
-  int32_t pad_;
+  int32_t store32;  // DMP_FLAG_FP32_STORAGE: stored matrices rounded to FP32 values
 };
+
+// A matrix element as it is stored: rounded to the nearest FP32 value under
+// DMP_FLAG_FP32_STORAGE (round to nearest even, subnormals kept), else as is.
+__device__ __forceinline__ double stored_value(double v, bool round32) {
+  return round32 ? static_cast<double>(__double2float_rn(v)) : v;
+}
 
 // ---------------------------------------------------------------- kernels (host launchers)
 // All launchers return cudaSuccess or the launch error; they count launches.
@@ -93,6 +99,7 @@ struct EpiArgs {
   int64_t ldx;        // leading dimension of X2
   const PurifyState* state;  // EPI_PM_UPDATE weights
   int32_t* levels;    // EPI_LEVELS: [s][m][n]
+  int round32;        // round every stored element to an FP32 value (DMP_FLAG_FP32_STORAGE)
 };
 
 // IMMA executor: level sums of int8 planes with fused FP64 recombination.
@@ -164,6 +171,7 @@ __device__ __forceinline__ void epi_apply(const EpiArgs& e, int64_t r, int64_t c
     const double x2 = e.X2[r * e.ldx + c];
     v = e.state->alpha * p + e.state->b2 * x2 + e.state->b3 * v;
   }
+  v = stored_value(v, e.round32 != 0);
   e.C[r * e.ldc + c] = v;
   if (mirror) e.C[c * e.ldc + r] = v;
 }

@@ -418,6 +418,7 @@ __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA,
   j.ea = M.expsP;
   j.epi.state = M.state;
   j.epi.levels = nullptr;
+  j.epi.round32 = 0;
   if (p.phase == 0) {
     j.tb = &M.tmPb;
     j.eb = M.expsP;
@@ -879,6 +880,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             double v = (er == kBadExp || ecv[t] == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
                                                             : scale_pow2(acc, er + ecv[t]);
             if (upd) v = wa * pv[t] + w2 * xv[t] + w3 * v;
+            v = stored_value(v, jb.epi.round32 != 0);
             Cout[r * ldc + col] = v;
             if (jb.sym && r < col) Cout[col * ldc + r] = v;
           }

@@ -142,6 +142,7 @@ __global__ void p0_kernel(const double* __restrict__ H, int64_t n, int64_t ldh, 
   const double a = st->lam / dn, mu = st->mu, occ = static_cast<double>(n_occ) / dn;
   // SP2 / TRS4: X_0 = (h_max I - H) / (h_max - h_min)
   const bool var = st->method != DMP_METHOD_PM;
+  const bool r32 = st->store32 != 0;
   const double hmax = st->h_max, width = st->h_max - st->h_min;
   const int64_t r0 = static_cast<int64_t>(bi) * 32, c0 = static_cast<int64_t>(bj) * 32;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
@@ -165,14 +166,15 @@ __global__ void p0_kernel(const double* __restrict__ H, int64_t n, int64_t ldh, 
       } else {
         v = var ? -tile[y][x] / width : -a * tile[y][x];
       }
-      P[r * ldp + c] = v;
+      P[r * ldp + c] = stored_value(v, r32);
     }
   }
   if (bi != bj) {
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
       // write the transposed tile: P[c0 + y][r0 + x] = -a H[r0 + x][c0 + y]
       const int64_t r = c0 + y, c = r0 + threadIdx.x;
-      if (r < n && c < n) P[r * ldp + c] = var ? -tile[threadIdx.x][y] / width : -a * tile[threadIdx.x][y];
+      if (r < n && c < n)
+        P[r * ldp + c] = stored_value(var ? -tile[threadIdx.x][y] / width : -a * tile[threadIdx.x][y], r32);
     }
   }
 }
@@ -300,8 +302,10 @@ __global__ void __launch_bounds__(256)
 axpby_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2, int64_t ldx2,
              double* __restrict__ out, int64_t ldo, int64_t n, const PurifyState* st) {
   const double a = st->alpha, b = st->b2;
+  const bool r32 = st->store32 != 0;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) out[i * ldo + j] = a * X[i * ldx + j] + b * X2[i * ldx2 + j];
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+      out[i * ldo + j] = stored_value(a * X[i * ldx + j] + b * X2[i * ldx2 + j], r32);
   }
 }
 
@@ -310,10 +314,11 @@ __global__ void __launch_bounds__(256)
 trs4_z_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ X2, int64_t ldx2,
               double* __restrict__ out, int64_t ldo, int64_t n, const PurifyState* st) {
   const double zd = st->zd, zx = st->zx, zx2 = st->zx2;
+  const bool r32 = st->store32 != 0;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
       const double v = zx * X[i * ldx + j] + zx2 * X2[i * ldx2 + j];
-      out[i * ldo + j] = j == i ? v + zd : v;
+      out[i * ldo + j] = stored_value(j == i ? v + zd : v, r32);
     }
   }
 }

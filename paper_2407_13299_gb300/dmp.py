@@ -158,13 +158,18 @@ def _require_cuda(*ts):
             raise TypeError("expected a float64 CUDA tensor")
 
 
+FLAG_BOUNDS_CONSTANT, FLAG_FP32_STORAGE = 1, 2
+
+
 def make_opts(mode="int8", slices=7, executor="auto", tol=1e-10, energy_tol=0.0, max_iter=100,
-              checkpoint_every=8, refine=0, method="pm") -> Opts:
+              checkpoint_every=8, refine=0, method="pm", fp32_storage=False) -> Opts:
     """refine: 0 none, -1 a McWeeny refinement step with FP64 products, s_r > 0
     one with Ozaki products of s_r slices (see dm_purify). method: "pm"
-    (canonical purification), "trs4" or "sp2" (DMP_METHOD_*)."""
+    (canonical purification), "trs4" or "sp2" (DMP_METHOD_*). fp32_storage:
+    every stored matrix rounded to an FP32 value (DMP_FLAG_FP32_STORAGE)."""
     return Opts(MODES[mode], int(slices) if mode != "fp64" else 0, EXECUTORS[executor], int(max_iter),
-                int(checkpoint_every), 0, float(tol), float(energy_tol), int(refine), METHODS[method])
+                int(checkpoint_every), FLAG_FP32_STORAGE if fp32_storage else 0, float(tol), float(energy_tol),
+                int(refine), METHODS[method])
 
 
 def workspace(nbytes: int, device=None) -> torch.Tensor:
@@ -185,17 +190,19 @@ def tape_bytes(n: int, opts: Opts) -> int:
 
 def purify(H: torch.Tensor, n_occ: int, mode="int8", slices=7, executor="auto", tol=1e-10,
            energy_tol=0.0, max_iter=100, P=None, ws=None, tape=None, stream=None, checkpoint_every=8, refine=0,
-           method="pm"):
+           method="pm", fp32_storage=False):
     """dm_purify on a float64 CUDA tensor H. Returns (P, info dict).
 
     `ws`, `P` and `tape` may be passed preallocated (see purify_workspace_bytes,
     tape_bytes) so that repeated calls allocate nothing. `refine` adds the
     McWeeny refinement step, `method` picks canonical purification, TRS4 or
-    SP2 (make_opts).
+    SP2, `fp32_storage` rounds every stored matrix to an FP32 value
+    (make_opts).
     """
     _require_cuda(H)
     n = H.shape[0]
-    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every, refine, method)
+    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every, refine, method,
+                     fp32_storage)
     if P is None:
         P = torch.empty_like(H)
     if ws is None:
@@ -293,7 +300,7 @@ def purify_backward(H: torch.Tensor, n_occ: int, tape: torch.Tensor, G: torch.Te
     _require_cuda(H, G)
     n = H.shape[0]
     opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every)
-    opts.flags = 1 if bounds_constant else 0
+    opts.flags = FLAG_BOUNDS_CONSTANT if bounds_constant else 0
     H = H.contiguous()
     G = G.contiguous()
     out = torch.empty_like(H)
