@@ -540,11 +540,11 @@ def run_ours(args):
     targets = []
     methods = []
     if args.targets == "on" and not args.slices:
-        for mode, beta in (("int8", 7), ("bf16", 8), ("e4m3", 5)):
-            if mode == "e4m3" and args.executor != "tc":
+        for t_mode, t_beta in (("int8", 7), ("bf16", 8), ("e4m3", 5)):
+            if t_mode == "e4m3" and args.executor != "tc":
                 continue  # E4M3 digits run on the tcgen05 executor only
             for target in (1e-5, 1e-8):
-                targets.append(cheapest(mode, beta, target))
+                targets.append(cheapest(t_mode, t_beta, target))
         # the other recursions of the family (TRS4 is the one the paper runs) at the
         # headline target; canonical purification stays the headline method
         for method in ("trs4", "sp2"):

@@ -41,11 +41,16 @@ def _gpu_grad(dmp, H, n_occ, W, **kw):
     return float(L.item()), Hd.grad.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode,s", [("fp64", 0), ("int8", 7)])
+@pytest.mark.parametrize("mode,s", [("fp64", 0), ("int8", 7), ("e4m3", 10)])
 def test_matches_oracle_gradient(dmp, mode, s):
     h = make_hamiltonian(160, 40, occ=(-2.0, -0.25), virt=(0.25, 2.0), seed=51)
     W = symmetric_gaussian(160, seed=52)
-    prod = None if mode == "fp64" else partial(oz.ozaki_gemm, s=s, beta=7)
+    if mode == "fp64":
+        prod = None
+    elif mode == "int8":
+        prod = partial(oz.ozaki_gemm, s=s, beta=7)
+    else:
+        prod = partial(oz.ozaki_gemm, s=s, beta=5, rounding="nearest")
     _, G_or, _ = ad.grad_trace_loss(h.H, 40, W, tol=1e-10, product=prod)
     G_or = 0.5 * (G_or + G_or.T)
     _, G = _gpu_grad(dmp, h.H, 40, W, mode=mode, slices=s or 7, executor="tc", tol=1e-10, checkpoint_every=4)
