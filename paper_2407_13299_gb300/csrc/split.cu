@@ -161,22 +161,40 @@ __device__ __forceinline__ int sfield6(uint32_t v0, uint32_t v1, uint32_t v2) {
 // i.e. (u + 1) >> 1 for the signed 6-bit field u = [p - 1, p + 5). The value
 // goes to a float exactly (1.5 2^23 + d + 16 holds d + 16 in its low bits), a
 // pair of them to two E4M3 bytes (exact: |d| <= 16).
+// Four consecutive entries (two register pairs) go to one 4-byte word per plane:
+// a warp writes 128 contiguous bytes per plane.
 template <int I>
-__device__ __forceinline__ void store_nearest(int s, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t b0,
-                                              uint32_t b1, uint32_t b2, char* base, int pair_off,
-                                              int64_t plane_bytes) {
+__device__ __forceinline__ void store_nearest4(int s, const uint32_t (&w)[4][3], char* base, int quad_off,
+                                               int64_t plane_bytes) {
   if constexpr (I < kMaxSlices) {
     if (I < s) {
       constexpr int Q = 89 - 5 * I;
-      const uint32_t ua = static_cast<uint32_t>((sfield6<Q>(a0, a1, a2) + 33) >> 1);  // d + 16 in [0, 32]
-      const uint32_t ub = static_cast<uint32_t>((sfield6<Q>(b0, b1, b2) + 33) >> 1);
-      const float fa = __uint_as_float(0x4B400000u | ua) - 12582928.0f;
-      const float fb = __uint_as_float(0x4B400000u | ub) - 12582928.0f;
-      uint16_t code;  // upper byte from the first operand: entry j + 1 above entry j
-      asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(code) : "f"(fb), "f"(fa));
-      reinterpret_cast<uint16_t*>(base + I * plane_bytes)[pair_off] = code;
-      store_nearest<I + 1>(s, a0, a1, a2, b0, b1, b2, base, pair_off, plane_bytes);
+      float f[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t d16 = static_cast<uint32_t>((sfield6<Q>(w[u][0], w[u][1], w[u][2]) + 33) >> 1);
+        f[u] = __uint_as_float(0x4B400000u | d16) - 12582928.0f;
+      }
+      uint16_t lo, hi;  // upper byte from the first operand
+      asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(f[1]), "f"(f[0]));
+      asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(f[3]), "f"(f[2]));
+      reinterpret_cast<uint32_t*>(base + I * plane_bytes)[quad_off] =
+          static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+      store_nearest4<I + 1>(s, w, base, quad_off, plane_bytes);
     }
+  }
+}
+
+// First entry of register pair q of a thread in the sweep starting at c0:
+// adjacent pairs across the threads (bf16 and int8 digits), or two adjacent
+// pairs per thread (E4M3 digits, so that each thread owns four consecutive
+// entries and stores 4-byte words).
+template <int KIND>
+__device__ __forceinline__ int entry_of(int c0, int tid, int q) {
+  if constexpr (KIND == 4) {
+    return c0 + 4 * (tid + kSplitThreads * (q >> 1)) + 2 * (q & 1);
+  } else {
+    return c0 + 2 * (tid + kSplitThreads * q);
   }
 }
 
@@ -241,7 +259,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
 
   double2 v[kPairs];
 #pragma unroll
-  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, 2 * (tid + kSplitThreads * q), k, live, vec);
+  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<KIND>(0, tid, q), k, live, vec);
   uint32_t mxh = 0, mxl = 0;
   bool bad = false;
 #pragma unroll
@@ -285,14 +303,17 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
   const int64_t plane_bytes = plane_stride * kElemBytes;
   for (int c0 = 0;;) {
 #pragma unroll
-    for (int q = 0; q < kPairs; ++q) {
-      const int j = c0 + 2 * (tid + kSplitThreads * q);
+    for (int q = 0; q < kPairs; q += (KIND == 4 ? 2 : 1)) {
+      const int j = entry_of<KIND>(c0, tid, q);
       if (j < k_pad) {
         if constexpr (KIND == 4) {
-          uint32_t a0, a1, a2, b0, b1, b2;
-          fix95_signed(v[q].x, c_row + 1, a0, a1, a2);
-          fix95_signed(v[q].y, c_row + 1, b0, b1, b2);
-          store_nearest<0>(s, a0, a1, a2, b0, b1, b2, base, j >> 1, plane_bytes);
+          // entries j .. j + 3 (k_pad is a multiple of 4, so all four are inside)
+          uint32_t w[4][3];
+          fix95_signed(v[q].x, c_row + 1, w[0][0], w[0][1], w[0][2]);
+          fix95_signed(v[q].y, c_row + 1, w[1][0], w[1][1], w[1][2]);
+          fix95_signed(v[q + 1].x, c_row + 1, w[2][0], w[2][1], w[2][2]);
+          fix95_signed(v[q + 1].y, c_row + 1, w[3][0], w[3][1], w[3][2]);
+          store_nearest4<0>(s, w, base, j >> 2, plane_bytes);
         } else {
           uint32_t a0, a1, a2, b0, b1, b2;
           bool na, nb;
@@ -305,7 +326,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
     if (k_pad - c0 <= kSweep) break;
     c0 += kSweep;
 #pragma unroll
-    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, c0 + 2 * (tid + kSplitThreads * q), k, live, vec);
+    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<KIND>(c0, tid, q), k, live, vec);
   }
 }
 
