@@ -42,6 +42,15 @@ product with enough slices to reach FP64 accuracy); the returned P, energy and
 band energy are those of P', and the unrefined values are kept. The step is
 the update above with c = 1/2, but is written here as printed.
 
+Late-slice schedule (an option; Sec. "Precision Requirements Sweep" weighs
+adjusting the precision across iterations): the subspace an iterate spans is
+disturbed by a product error in proportion to the error over the gap between
+its occupied and virtual eigenvalues, a gap that doubles about every three
+iterations of the loop, while the refinement step repairs the eigenvalues.
+Reading: once an iterate's ||P^2 - P||_F is below a threshold, all later
+passes use a second product (fewer slices); the switch is taken after the
+update, so it applies from the next pass on, and it is never undone.
+
 FP32 storage (Sec. "Mixed Precision Purification"): the paper finds that the
 matrices of purification may be stored in FP32 as long as they are multiplied
 with FP64 accumulation, and tests it by rounding every matrix that enters a
@@ -156,7 +165,8 @@ def mcweeny_step(P, product=None):
 
 
 def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
-           energy_tol: float = 0.0, record: bool = False, refine_product=None, store=None):
+           energy_tol: float = 0.0, record: bool = False, refine_product=None, store=None,
+           late_product=None, late_idem: float = 0.0):
     """Canonical purification of H with the stopping rules of the module header.
 
     `product(A, B)` forms every matrix product (FP64 by default; pass a partial
@@ -174,6 +184,11 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
     initial guess, each P^2 and each updated P (fp32_store for FP32 storage;
     X3 is used at once and the refined P is left as computed). With
     record=True the P^2 of every pass are returned as well ("squares").
+
+    With `late_product` set, once an iterate's idempotency ||P^2 - P||_F has
+    fallen below `late_idem`, every later pass forms its products with
+    `late_product` instead (the late-slice schedule of the module header);
+    `late_iters` counts the passes (P^2 products) that did.
     """
     product = fp64_product if product is None else product
     store = (lambda M: M) if store is None else store
@@ -181,6 +196,8 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
     P, init = initial_guess(H, n_occ)
     P = store(P)
     squares = [] if record else None
+    late = False
+    late_iters = 0
     band = []
     idems = []
     traces = []
@@ -190,7 +207,9 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
     status = NOT_CONVERGED
     k = 0
     while True:
-        X2 = store(product(P, P))
+        prod_k = late_product if late else product
+        late_iters += 1 if late else 0
+        X2 = store(prod_k(P, P))
         if record:
             squares.append(X2.copy())
         t1 = float(np.trace(P))
@@ -213,7 +232,7 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
         if k >= max_iter:
             status = NOT_CONVERGED
             break
-        X3 = product(P, X2)
+        X3 = prod_k(P, X2)
         t3 = float(np.trace(X3))
         if not (t1 - t2 > 0):
             status = C_OUT_OF_RANGE
@@ -226,6 +245,8 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
         P = store(alpha * P + b2 * X2 + b3 * X3)
         cs.append(c)
         branches.append(br)
+        if late_product is not None and idem < late_idem:
+            late = True
         if record:
             iterates.append(P.copy())
         k += 1
@@ -238,7 +259,7 @@ def purify(H, n_occ: int, tol: float = 1e-10, max_iter: int = 100, product=None,
                energy=energy, band_energy=2.0 * energy, energy_unrefined=energy_unrefined,
                refined=refine_product is not None, idem=idems[-1], trace=traces[-1],
                band_history=band, idem_history=idems, trace_history=traces, c_history=cs,
-               branch_history=branches, init=init)
+               branch_history=branches, init=init, late_iters=late_iters)
     if record:
         out["iterates"] = iterates
         out["squares"] = squares

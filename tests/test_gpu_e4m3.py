@@ -188,3 +188,37 @@ def test_rejected_combinations(dmp):
         dmp.ozaki_gemm(A, A, "e4m3", 5, "imma")  # E4M3 digits run on the tensor-core executor only
     with pytest.raises(RuntimeError):
         dmp.purify_batched([A, A], [2, 2], mode="e4m3", slices=7)
+
+
+def test_nonfinite_rows_and_columns(dmp):
+    """A NaN in a row of A or an Inf in a column of B gives that row or column
+    of NaN; every other output is the oracle's product of the finite parts."""
+    A = _mixed(150, 90, seed=5)
+    B = _mixed(90, 300, seed=6)
+    A[7, 3] = np.nan
+    B[11, 20] = np.inf
+    got = dmp.ozaki_gemm(_dev(A), _dev(B), "e4m3", 7, "tc").cpu().numpy()
+    assert np.all(np.isnan(got[7, :])) and np.all(np.isnan(got[:, 20]))
+    A2, B2 = A.copy(), B.copy()
+    A2[7, :] = 0.0
+    B2[:, 20] = 0.0
+    want = oz.ozaki_gemm(A2, B2, 7, BETA, rounding="nearest")
+    mask = np.ones_like(got, dtype=bool)
+    mask[7, :] = False
+    mask[:, 20] = False
+    assert np.array_equal(got[mask], want[mask])
+
+
+def test_purify_ragged_size_and_nonfinite_input(dmp):
+    """n = 333 (padded to 512 rows and K): same iterations and P as the oracle;
+    a NaN in H is refused."""
+    h = make_hamiltonian(333, 80, seed=41)
+    ref = pu.purify(h.H, 80, tol=1e-10, product=partial(oz.ozaki_gemm, s=10, beta=BETA, rounding="nearest"))
+    P, info = dmp.purify(_dev(h.H), 80, mode="e4m3", slices=10, tol=1e-10)
+    assert abs(info["iters"] - ref["iters"]) <= 1
+    assert np.max(np.abs(P.cpu().numpy() - ref["P"])) <= 1e-8
+    H = h.H.copy()
+    H[5, 9] = np.nan
+    with pytest.raises(dmp.DmpError) as e:
+        dmp.purify(_dev(H), 80, mode="e4m3", slices=7)
+    assert e.value.code == dmp.ERR_NONFINITE

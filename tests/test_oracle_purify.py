@@ -342,3 +342,58 @@ def test_planted_store_of_the_initial_guess_only_fails():
     r = pu.purify(h.H, 16, tol=1e-10, store=first_only, record=True)
     assert _is_fp32_valued(r["iterates"][0])
     assert not all(_is_fp32_valued(P) for P in r["iterates"])
+
+
+# ----------------------------------------------------------------- late-slice schedule
+
+def test_late_schedule_with_the_same_product_changes_nothing():
+    h = make_hamiltonian(96, 24, seed=12)
+    prod = partial(oz.ozaki_gemm, s=6, beta=7)
+    ref = pu.purify(h.H, 24, tol=1e-10, product=prod)
+    same = pu.purify(h.H, 24, tol=1e-10, product=prod, late_product=prod, late_idem=10.0)
+    off = pu.purify(h.H, 24, tol=1e-10, product=prod, late_product=partial(oz.ozaki_gemm, s=3, beta=7), late_idem=0.0)
+    for r in (same, off):
+        assert np.array_equal(r["P"], ref["P"]) and r["iters"] == ref["iters"]
+        assert r["idem_history"] == ref["idem_history"]
+    assert same["late_iters"] > 0 and off["late_iters"] == 0
+
+
+def test_late_schedule_switches_after_the_first_iterate_below_the_threshold():
+    """The passes after the first update whose iterate had ||P^2 - P||_F below
+    the threshold use the late product, and only those."""
+    h = make_hamiltonian(128, 32, seed=13)
+    seen = []
+
+    def tag(s):
+        def prod(A, B):
+            seen.append(s)
+            return oz.ozaki_gemm(A, B, s, 7)
+        return prod
+
+    tau = 1.0
+    r = pu.purify(h.H, 32, tol=1e-10, product=tag(6), late_product=tag(4), late_idem=tau)
+    idem = r["idem_history"]
+    k_star = next(k for k, v in enumerate(idem) if v < tau)
+    # pass k forms P^2 and P^3 (the last pass stops after P^2, or after P^3
+    # when c leaves [0, 1]): late from pass k_star + 1 on
+    last = 2 if r["status"] == pu.C_OUT_OF_RANGE else 1
+    passes = []
+    for k in range(r["iters"] + 1):
+        passes += [k] * (2 if k < r["iters"] else last)
+    assert [s for s in seen] == [4 if k > k_star else 6 for k in passes]
+    assert r["late_iters"] == r["iters"] - k_star
+
+
+def test_late_slices_keep_most_of_the_refined_energy():
+    """With the refinement step, loop products of four slices once the iterate
+    is within 1 of idempotency cost little energy accuracy: the error stays far
+    below that of four slices throughout (the subspace is fixed early, while
+    the gap between occupied and virtual eigenvalues is small)."""
+    h = make_hamiltonian(256, 64, occ=(-1.5, -0.01), virt=(0.01, 1.5), seed=77)
+    E = float(np.sum(h.e[:64]))
+    s5, s4 = partial(oz.ozaki_gemm, s=5, beta=7), partial(oz.ozaki_gemm, s=4, beta=7)
+    r8 = partial(oz.ozaki_gemm, s=8, beta=7)
+    low = pu.purify(h.H, 64, tol=1e-10, product=s4, refine_product=r8)
+    sched = pu.purify(h.H, 64, tol=1e-10, product=s5, late_product=s4, late_idem=1.0, refine_product=r8)
+    assert sched["late_iters"] > 0.25 * sched["iters"]
+    assert abs(sched["energy"] - E) < 0.1 * abs(low["energy"] - E)
