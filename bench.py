@@ -572,6 +572,25 @@ def run_ours(args):
                      "note": "every stored iterate rounded to an FP32 value; buffers stay FP64, so the time "
                              "measures the precision effect, not a memory saving"}
 
+    # ---- the headline setting with the late-slice schedule (one slice fewer once
+    # the iterate is within 0.5 of idempotency); reported, not used for the headline
+    late_sched = None
+    if args.targets == "on" and not args.slices and s > 1:
+        kw = dict(mode=mode, slices=s, executor=args.executor, refine=refine, P=P, ws=ws, late_slices=s - 1,
+                  late_idem=0.5)
+        _, li = dmp.purify(H, n_occ, **kw)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(2):
+            dmp.purify(H, n_occ, **kw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        late_sched = {"slices": s, "late_slices": s - 1, "late_idem": 0.5, "refine_slices": refine,
+                      "value": a.elapsed_time(b) / 2e3, "unit": UNIT, "iters": li["iters"],
+                      "late_iters": li["late_iters"], "rel_energy_error": abs(li["energy"] - E_star) / abs(E_star)}
+
     # ---- FP64 purification on the same GPU (once)
     fp64 = None
     if args.fp64 == "full":
@@ -620,7 +639,7 @@ def run_ours(args):
                        "rel_energy_error": rel_energy, "rel_energy_error_unrefined":
                            abs(info["energy_unrefined"] - E_star) / abs(E_star),
                        "idempotency": info["idem"], "without_refinement": plain, "targets": targets,
-                       "other_methods": methods, "fp32_storage": storage32,
+                       "other_methods": methods, "fp32_storage": storage32, "late_schedule": late_sched,
                        "l2": (f"inputs larger than L2 (H {n * n * 8 / 2**20:.0f} MiB, digit planes "
                               f"{2 * s * n * n * (1 if mode == 'e4m3' else 2) / 2**30:.2f} GiB)"),
                        "slice_tuning": tune,

@@ -129,6 +129,10 @@ typedef struct {
   int32_t refine_slices;    /* refinement after the loop (see dm_purify): 0 off,
                                -1 FP64 products, s_r > 0 Ozaki products of s_r slices */
   int32_t method;           /* DMP_METHOD_* (0: canonical purification)              */
+  int32_t late_slices;      /* late-slice schedule (see dm_purify): 0 off, else the
+                               slice count of every pass after an iterate with
+                               ||P^2 - P||_F < late_idem                              */
+  double late_idem;         /* threshold of the late-slice schedule                  */
 } dmp_opts;
 
 /* Per-run report, filled when the host pointer is non-NULL (the call then
@@ -147,7 +151,7 @@ typedef struct {
   double h_min, h_max; /* Gershgorin bounds used for the initial guess          */
   double energy_unrefined; /* tr(P H) before the refinement step (= energy if none) */
   int32_t refined;     /* 1 if the refinement step was applied                   */
-  int32_t reserved;
+  int32_t late_iters;  /* passes (P^2 products) formed with late_slices slices     */
 } dmp_info;
 
 /* Bytes of workspace dm_purify needs for this n and these options. */
@@ -175,6 +179,16 @@ int dmp_tape_size(int64_t n, const dmp_opts* opts, size_t* bytes);
  * slices (9 reaches FP64 accuracy; the level-sum limit below applies to it).
  * info->energy then describes P' and info->energy_unrefined P_k; info->idem
  * stays that of P_k. Refinement with a tape is DMP_ERR_UNSUPPORTED.
+ * Late-slice schedule (an option of this library; the paper weighs adjusting
+ * the precision across iterations in Sec. "Precision Requirements Sweep"):
+ * with opts->late_slices = s_l > 0, once an iterate has ||P_k^2 - P_k||_F <
+ * opts->late_idem, every later pass forms its products with s_l slices (the
+ * switch applies from pass k + 1 and is never undone; info->late_iters counts
+ * those passes). A product error disturbs the occupied subspace in proportion
+ * to the error over the gap between the iterate's occupied and virtual
+ * eigenvalues, and that gap grows geometrically along the loop, so late
+ * passes tolerate fewer slices, the more so with the refinement step, which
+ * repairs the eigenvalues. Canonical purification only; not with a tape.
  *   H      n x n, leading dimension ldh. Only the upper triangle is read; the
  *          lower triangle is taken as its mirror.
  *   P      n x n output, leading dimension ldp (may not alias H).

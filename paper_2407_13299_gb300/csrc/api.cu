@@ -36,6 +36,8 @@ struct Opts {
   int refine;  // 0 off, -1 FP64 products, > 0 Ozaki slices of the refinement step
   int method;  // DMP_METHOD_*
   bool store32;  // DMP_FLAG_FP32_STORAGE
+  int late_s;    // late-slice schedule: 0 off, else the slice count after the switch
+  double late_idem;
 };
 
 int normalize(const dmp_opts* o, Opts& out) {
@@ -72,6 +74,10 @@ int normalize(const dmp_opts* o, Opts& out) {
   out.refine = o->refine_slices;
   if (out.refine != 0 && out.mode == DMP_FP64) out.refine = -1;
   if (out.refine < -1 || out.refine > smax) return DMP_ERR_INVALID_ARG;
+  out.late_s = out.mode == DMP_FP64 ? 0 : o->late_slices;
+  out.late_idem = o->late_idem;
+  if (out.late_s < 0 || out.late_s > smax || !(out.late_idem >= 0.0)) return DMP_ERR_INVALID_ARG;
+  if (out.late_s > 0 && out.method != DMP_METHOD_PM) return DMP_ERR_UNSUPPORTED;
   return DMP_OK;
 }
 
@@ -126,7 +132,7 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
   L.X2 = c.take(static_cast<size_t>(n) * n * sizeof(double));
   if (o.mode != DMP_FP64) {
     // room for the refinement step's slices too
-    const int smax = std::max(o.s, o.refine);
+    const int smax = std::max(std::max(o.s, o.refine), o.late_s);
     const size_t plane = static_cast<size_t>(smax) * L.n_pad * L.k_pad * elem_bytes(o);
     L.planesP = c.take(plane);
     L.planesX = c.take(plane);
@@ -276,7 +282,10 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     return DMP_ERR_UNSUPPORTED;
   if (o.refine > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.refine, o.mode))
     return DMP_ERR_UNSUPPORTED;
-  if ((o.refine != 0 || o.method != DMP_METHOD_PM || o.store32) && tape != nullptr) return DMP_ERR_UNSUPPORTED;
+  if (o.late_s > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.late_s, o.mode))
+    return DMP_ERR_UNSUPPORTED;
+  if ((o.refine != 0 || o.method != DMP_METHOD_PM || o.store32 || o.late_s > 0) && tape != nullptr)
+    return DMP_ERR_UNSUPPORTED;
   const PurifyLayout L = purify_layout(n, o);
   if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
   TapeLayout TL{};
@@ -318,7 +327,14 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   double* alt = Palt;
   int64_t ldalt = n;
   const int* done = &state->done;
+  bool late = false;  // the late-slice schedule has switched
+  int late_iters = 0;
   for (int k = 0; k <= o.max_iter; ++k) {
+    Opts oi = o;  // this pass's slice count
+    if (late) {
+      oi.s = o.late_s;
+      ++late_iters;
+    }
     if (tape != nullptr && k % o.every == 0) {
       DMP_CUDA(cudaMemcpy2DAsync(tape_ck + static_cast<size_t>(k / o.every) * n * n, n * sizeof(double),
                                  cur, ldcur * sizeof(double), n * sizeof(double), n,
@@ -332,9 +348,9 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     if (o.mode == DMP_FP64) {
       DMP_CUDA(launch_gemm_f64(cur, ldcur, cur, ldcur, n, n, n, 1, e2, done, st));
     } else {
-      DMP_CUDA(launch_split_rows(cur, n, n, ldcur, o.s, o.beta, expsP, planesP, L.n_pad, L.k_pad,
+      DMP_CUDA(launch_split_rows(cur, n, n, ldcur, oi.s, oi.beta, expsP, planesP, L.n_pad, L.k_pad,
                                  elem_kind(o), nullptr, done, st));
-      DMP_CUDA(launch_product(o, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e2, done,
+      DMP_CUDA(launch_product(oi, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e2, done,
                               err, scratch, st));
     }
     if (o.method == DMP_METHOD_PM) {
@@ -343,9 +359,11 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
       DMP_CUDA(launch_measure_variant(cur, ldcur, X2, n, H, ldh, n, partials, state, st));
     }
     int32_t flags[3] = {0, 0, 0};
+    double idem2 = 0.0;
     DMP_CUDA(cudaMemcpyAsync(&flags[0], &state->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     DMP_CUDA(cudaMemcpyAsync(&flags[1], err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     DMP_CUDA(cudaMemcpyAsync(&flags[2], &state->step_kind, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (o.late_s > 0) DMP_CUDA(cudaMemcpyAsync(&idem2, &state->idem2, sizeof(double), cudaMemcpyDeviceToHost, st));
     DMP_CUDA(cudaStreamSynchronize(st));
     if (flags[1]) return DMP_ERR_TIMEOUT;
     if (flags[0]) break;
@@ -366,11 +384,11 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
         if (o.mode == DMP_FP64) {
           DMP_CUDA(launch_gemm_f64(X2, n, alt, ldalt, n, n, n, 1, ez, done, st));
         } else {
-          DMP_CUDA(launch_split_rows(X2, n, n, n, o.s, o.beta, expsX, planesX, L.n_pad, L.k_pad,
+          DMP_CUDA(launch_split_rows(X2, n, n, n, oi.s, oi.beta, expsX, planesX, L.n_pad, L.k_pad,
                                      elem_kind(o), nullptr, done, st));
-          DMP_CUDA(launch_split_rows(alt, n, n, ldalt, o.s, o.beta, expsP, planesP, L.n_pad, L.k_pad,
+          DMP_CUDA(launch_split_rows(alt, n, n, ldalt, oi.s, oi.beta, expsP, planesP, L.n_pad, L.k_pad,
                                      elem_kind(o), nullptr, done, st));
-          DMP_CUDA(launch_product(o, planesX, planesP, expsX, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, ez, done,
+          DMP_CUDA(launch_product(oi, planesX, planesP, expsX, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, ez, done,
                                   err, scratch, st));
         }
       }
@@ -392,13 +410,15 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     if (o.mode == DMP_FP64) {
       DMP_CUDA(launch_gemm_f64(cur, ldcur, X2, n, n, n, n, 1, e3, done, st));
     } else {
-      DMP_CUDA(launch_split_rows(X2, n, n, n, o.s, o.beta, expsX, planesX, L.n_pad, L.k_pad,
+      DMP_CUDA(launch_split_rows(X2, n, n, n, oi.s, oi.beta, expsX, planesX, L.n_pad, L.k_pad,
                                  elem_kind(o), nullptr, done, st));
-      DMP_CUDA(launch_product(o, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e3, done,
+      DMP_CUDA(launch_product(oi, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e3, done,
                               err, scratch, st));
     }
     std::swap(cur, alt);
     std::swap(ldcur, ldalt);
+    // the late-slice schedule switches after an update whose iterate was within late_idem of idempotency
+    if (o.late_s > 0 && std::sqrt(idem2) < o.late_idem) late = true;
   }
   // ---- refinement (Sec. "Precision Requirements Sweep"): one McWeeny step in
   // full precision, P' = 3 P^2 - 2 P^3, run as the update with the weights of c = 1/2
@@ -484,6 +504,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     info->band_energy = 2.0 * info->energy;
     info->energy_unrefined = fin.energy;
     info->refined = refined ? 1 : 0;
+    info->late_iters = late_iters;
     info->idem = std::sqrt(fin.idem2);
     info->trace = fin.t1;
     info->c_last = fin.c;

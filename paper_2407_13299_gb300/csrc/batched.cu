@@ -253,6 +253,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   if (opts->executor != DMP_EXEC_AUTO && opts->executor != DMP_EXEC_TC) return DMP_ERR_UNSUPPORTED;
   if (opts->refine_slices != 0) return DMP_ERR_UNSUPPORTED;  // no batched refinement step
   if (opts->flags & DMP_FLAG_FP32_STORAGE) return DMP_ERR_UNSUPPORTED;
+  if (opts->late_slices != 0) return DMP_ERR_UNSUPPORTED;  // one slice count per batched launch
   if (opts->method != DMP_METHOD_PM) return DMP_ERR_UNSUPPORTED;  // canonical purification only
   const int beta = opts->mode == DMP_OZAKI_BF16 ? 8 : 7;
   const int smax_mode = beta == 8 ? 9 : 10;

@@ -35,7 +35,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("slices", ctypes.c_int32), ("executor", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("tol", ctypes.c_double), ("energy_tol", ctypes.c_double),
-                ("refine_slices", ctypes.c_int32), ("method", ctypes.c_int32)]
+                ("refine_slices", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("late_slices", ctypes.c_int32), ("late_idem", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -43,10 +44,10 @@ class Info(ctypes.Structure):
                 ("executor_used", ctypes.c_int32), ("energy", ctypes.c_double),
                 ("band_energy", ctypes.c_double), ("idem", ctypes.c_double), ("trace", ctypes.c_double),
                 ("c_last", ctypes.c_double), ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
-                ("energy_unrefined", ctypes.c_double), ("refined", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("energy_unrefined", ctypes.c_double), ("refined", ctypes.c_int32), ("late_iters", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _lib = None
@@ -162,14 +163,17 @@ FLAG_BOUNDS_CONSTANT, FLAG_FP32_STORAGE = 1, 2
 
 
 def make_opts(mode="int8", slices=7, executor="auto", tol=1e-10, energy_tol=0.0, max_iter=100,
-              checkpoint_every=8, refine=0, method="pm", fp32_storage=False) -> Opts:
+              checkpoint_every=8, refine=0, method="pm", fp32_storage=False, late_slices=0,
+              late_idem=0.0) -> Opts:
     """refine: 0 none, -1 a McWeeny refinement step with FP64 products, s_r > 0
     one with Ozaki products of s_r slices (see dm_purify). method: "pm"
     (canonical purification), "trs4" or "sp2" (DMP_METHOD_*). fp32_storage:
-    every stored matrix rounded to an FP32 value (DMP_FLAG_FP32_STORAGE)."""
+    every stored matrix rounded to an FP32 value (DMP_FLAG_FP32_STORAGE).
+    late_slices, late_idem: the late-slice schedule (passes after an iterate
+    with ||P^2 - P||_F < late_idem use late_slices slices; 0: off)."""
     return Opts(MODES[mode], int(slices) if mode != "fp64" else 0, EXECUTORS[executor], int(max_iter),
                 int(checkpoint_every), FLAG_FP32_STORAGE if fp32_storage else 0, float(tol), float(energy_tol),
-                int(refine), METHODS[method])
+                int(refine), METHODS[method], int(late_slices), float(late_idem))
 
 
 def workspace(nbytes: int, device=None) -> torch.Tensor:
@@ -190,19 +194,19 @@ def tape_bytes(n: int, opts: Opts) -> int:
 
 def purify(H: torch.Tensor, n_occ: int, mode="int8", slices=7, executor="auto", tol=1e-10,
            energy_tol=0.0, max_iter=100, P=None, ws=None, tape=None, stream=None, checkpoint_every=8, refine=0,
-           method="pm", fp32_storage=False):
+           method="pm", fp32_storage=False, late_slices=0, late_idem=0.0):
     """dm_purify on a float64 CUDA tensor H. Returns (P, info dict).
 
     `ws`, `P` and `tape` may be passed preallocated (see purify_workspace_bytes,
     tape_bytes) so that repeated calls allocate nothing. `refine` adds the
     McWeeny refinement step, `method` picks canonical purification, TRS4 or
-    SP2, `fp32_storage` rounds every stored matrix to an FP32 value
-    (make_opts).
+    SP2, `fp32_storage` rounds every stored matrix to an FP32 value,
+    `late_slices` / `late_idem` set the late-slice schedule (make_opts).
     """
     _require_cuda(H)
     n = H.shape[0]
     opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, checkpoint_every, refine, method,
-                     fp32_storage)
+                     fp32_storage, late_slices, late_idem)
     if P is None:
         P = torch.empty_like(H)
     if ws is None:
