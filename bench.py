@@ -381,16 +381,21 @@ def run_ours(args):
     dmp.purify_host(H_host, n_occ, out=P_host, mode=mode, slices=s, executor=args.executor, ws=ws, P=P,
                     refine=refine)
     torch.cuda.synchronize()
+    e2e_parts = []
     for _ in range(max(args.e2e_steps, 1)):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        parts = {}
         dmp.purify_host(H_host, n_occ, out=P_host, mode=mode, slices=s, executor=args.executor, ws=ws, P=P,
-                        refine=refine)
+                        refine=refine, timings=parts)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
+        e2e_parts.append(parts)
+    med = sorted(range(len(e2e_times)), key=lambda i: e2e_times[i])[len(e2e_times) // 2]
     e2e = {"value": max_over_ranks(statistics.median(e2e_times), dev), "unit": UNIT,
-           "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8}
+           "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8,
+           "runs_s": e2e_times, "median_run_parts_s": e2e_parts[med]}
 
     # ---- timed region: K full purifications, H resident in HBM (512 MiB > L2)
     dmp.profile_enable(True)

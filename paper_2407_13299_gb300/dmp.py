@@ -9,6 +9,7 @@ library is missing or no GPU is present, the calls raise.
 from __future__ import annotations
 
 import ctypes
+import time
 import os
 
 import torch
@@ -221,15 +222,23 @@ def purify(H: torch.Tensor, n_occ: int, mode="int8", slices=7, executor="auto", 
     return P, info.as_dict()
 
 
-def purify_host(H_host: torch.Tensor, n_occ: int, out: torch.Tensor | None = None, **kw):
+def purify_host(H_host: torch.Tensor, n_occ: int, out: torch.Tensor | None = None, timings: dict | None = None,
+                **kw):
     """End-to-end call from host memory: copies H to the device, purifies, and
     copies P back into `out` (a host tensor; pinned memory keeps the copies at
-    full PCIe/C2C speed). Returns (P on the host, info)."""
+    full PCIe/C2C speed). Returns (P on the host, info). `timings`, if given,
+    receives the host-clock seconds of the copy in plus the purification (which
+    synchronises) and of the copy out."""
+    t0 = time.perf_counter()
     H = H_host.to("cuda", non_blocking=True)
     P, info = purify(H, n_occ, **kw)
+    t1 = time.perf_counter()
     if out is None:
         out = torch.empty(P.shape, dtype=P.dtype, pin_memory=H_host.is_pinned())
     out.copy_(P, non_blocking=False)
+    if timings is not None:
+        timings["in_and_purify"] = t1 - t0
+        timings["out"] = time.perf_counter() - t1
     return out, info
 
 
