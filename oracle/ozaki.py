@@ -18,25 +18,27 @@ path as well:
   the same way (f_c), i.e. B^T is scaled per row.
 * digits: for i = 1..S, y = x 2^beta, d_i = trunc(y), x = y - d_i. Every step is
   exact in FP64 and |d_i| <= 2^beta - 1. beta = 7 gives digits in int8 range
-  (the INT8 mode); beta = 8 gives integers exactly representable in bfloat16.
-  There is no remainder slice: the truncation of the last digit is the error
+  (the INT8 mode). There is no remainder slice: the truncation of the last digit is the error
   that the diagonal i + j = S + 1 carries.
-* nearest digits (the E4M3 mode): the extraction of the original Ozaki scheme
+* nearest digits (the E4M3 and BF16 modes): the extraction of the original Ozaki scheme
   rounds to nearest instead of truncating. Here the row exponent is one larger
   (e_r = ilogb(max_j |A_rj|) + 2, so x lies in (-1/2, 1/2)) and
   d_i = floor(y + 1/2) (ties upward), x = y - d_i in [-1/2, 1/2). With
   beta = 5 every digit lies in [-16, 16]: integers of at most four
   significant bits, exact in the FP8 format E4M3 (4-bit exponent, 3-bit
-  fraction). Each slice carries one bit more than a truncated digit of the
-  same range would.
+  fraction). With beta = 8 every digit lies in [-128, 128], exact in bfloat16
+  (8 significant bits), and a product of two is at most 2^14, as for 7-bit
+  truncated digits. Each slice carries one bit more than a truncated digit of
+  the same range would.
 * level sums: S_L = sum over i + j = L of D_i^A (D_j^B)^T, exact integers,
   for L = 2 .. S + 1 (these are exactly the kept pairs).
 * recombination: C = 2^(e_r + f_c) * (S_{S+1} 2^-beta(S+1) + ... + S_2 2^-2beta)
-  in FP64. Up to four consecutive levels (beta = 7) are first combined exactly
-  as one integer whose value is an exact float64; these group values are added
-  in FP64 from the smallest group to the largest, rounding at each addition.
-  For S <= 8 there are at most two groups, so C is the correctly rounded value
-  of the exact sum of the kept pairs.
+  in FP64. Up to four consecutive levels (beta <= 7; three for beta = 8) are
+  first combined exactly as one integer whose value is an exact float64; these
+  group values are added in FP64 from the smallest group to the largest,
+  rounding at each addition. For S <= 8 (S <= 6 for beta = 8) there are at
+  most two groups, so C is the correctly rounded value of the exact sum of the
+  kept pairs.
 
 Parity: pinned. The tests check digit reconstruction with exact rationals,
 the digit rule (truncation, or the nearest-digit remainder interval) on exact
@@ -51,7 +53,7 @@ import numpy as np
 
 # digit width per precision mode (bits of magnitude per slice) and digit rule
 BETA = {"int8": 7, "bf16": 8, "e4m3": 5}
-ROUNDING = {"int8": "trunc", "bf16": "trunc", "e4m3": "nearest"}
+ROUNDING = {"int8": "trunc", "bf16": "nearest", "e4m3": "nearest"}
 
 
 def max_digit(beta: int, rounding: str = "trunc") -> int:
@@ -165,9 +167,10 @@ def level_sums(DA: np.ndarray, DBt: np.ndarray, beta: int, rounding: str = "trun
 def level_groups(s: int, beta: int):
     """Consecutive levels combined exactly before any rounding: groups of up to
     four for beta <= 7 (four level sums below 2^31 weighted by 1, 2^beta,
-    2^2beta, 2^3beta stay below 2^53), single levels for beta = 8. Groups start
-    from the smallest level L = s + 1; each is listed largest L first."""
-    size = 4 if beta <= 7 else 1
+    2^2beta, 2^3beta stay below 2^53), of up to three for beta = 8 (weights 1,
+    2^8, 2^16). Groups start from the smallest level L = s + 1; each is listed
+    largest L first."""
+    size = 4 if beta <= 7 else 3
     levels = list(range(s + 1, 1, -1))
     return [levels[i:i + size] for i in range(0, len(levels), size)]
 
@@ -179,8 +182,8 @@ def recombine(S: dict, e_row: np.ndarray, f_col: np.ndarray, s: int, beta: int) 
     integer T = sum_L S_L 2^(beta (L_a - L)), L_a the group's largest L, so that
     its value T 2^(-beta L_a) is an exact float64; the groups are then added in
     float64 from the smallest to the largest, rounding at each addition. With at
-    most two groups (s <= 8 for beta = 7) the result is the correctly rounded
-    value of the exact sum.
+    most two groups (s <= 8 for beta <= 7, s <= 6 for beta = 8) the result is
+    the correctly rounded value of the exact sum.
     """
     m = e_row.shape[0]
     n = f_col.shape[0]

@@ -471,3 +471,59 @@ def test_planted_truncated_digits_fail_the_nearest_rule():
 
     with pytest.raises(AssertionError):
         _check_nearest_split(split_trunc_digits, _mixed_matrix(4, 6, seed=98), 3, 5)
+
+
+# ----------------------------------------------------------------- nearest 8-bit digits (BF16 mode)
+
+def _bf16_integer_values():
+    """Integers a bfloat16 holds exactly (8 significant bits) up to 300 in magnitude."""
+    vals = set()
+    for v in range(0, 301):
+        b = bin(v)[2:].rstrip("0") if v else "0"
+        if len(b) <= 8:
+            vals.update({v, -v})
+    return vals
+
+
+def test_nearest_8bit_digits_are_exact_in_bf16_and_products_fit_2_14():
+    vals = _bf16_integer_values()
+    assert oz.max_digit(oz.BETA["bf16"], oz.ROUNDING["bf16"]) == 128
+    assert all(d in vals for d in range(-128, 129))
+    assert 128 * 128 == 2 ** 14 and 1024 * 2 ** 14 == 2 ** 24  # an fp32 chunk of 1024 stays exact
+
+
+@pytest.mark.parametrize("s", [1, 4, 9])
+def test_nearest_8bit_split_matches_digit_rule(s):
+    _check_nearest_split(oz.split_rows, _mixed_matrix(5, 9, seed=170 + s), s, 8)
+    _check_nearest_split(oz.split_rows, _tie_matrix(), s, 8)
+
+
+@pytest.mark.parametrize("s", [2, 5, 6])
+def test_nearest_8bit_error_within_bound_and_levels_exact(s):
+    A = _mixed_matrix(6, 8, seed=191)
+    B = _mixed_matrix(8, 5, seed=192)
+    C, parts = oz.ozaki_gemm(A, B, s, 8, return_parts=True, rounding="nearest")
+    want = _brute_levels(parts["DA"], parts["DBt"])
+    for L in want:
+        assert np.array_equal(parts["S"][L], np.array(want[L], dtype=np.int64)), L
+    exact = _exact_product(A, B)
+    bound = oz.truncation_bound(parts["e"], parts["f"], A.shape[1], s, 8, rounding="nearest")
+    for r in range(A.shape[0]):
+        for c in range(B.shape[1]):
+            assert abs(Fraction(float(C[r, c])) - exact[r][c]) <= Fraction(float(bound[r, c])), (r, c)
+
+
+@pytest.mark.parametrize("s", [1, 3, 4, 6])
+def test_recombination_8bit_groups_of_three_correctly_rounded(s):
+    """Groups of three levels for beta = 8: level sums up to 2^30 weighted by 1,
+    2^8, 2^16 stay exact, and with at most two groups (s <= 6) the float64
+    result is the correctly rounded exact sum."""
+    beta = 8
+    assert all(len(g) <= 3 for g in oz.level_groups(s, beta))
+    assert len(oz.level_groups(s, beta)) <= 2
+    rng = np.random.default_rng(300 + s)
+    S = {L: rng.integers(-(2 ** 30), 2 ** 30, size=(6, 5), dtype=np.int64) for L in range(2, s + 2)}
+    C = oz.recombine(S, np.zeros(6, dtype=np.int64), np.zeros(5, dtype=np.int64), s, beta)
+    for r in range(6):
+        for c in range(5):
+            assert C[r, c] == float(_exact_level_value(S, s, beta, r, c))
