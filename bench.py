@@ -351,9 +351,11 @@ def run_ours(args):
                  (8, 0), (9, 0)]
     s, refine = cands[-1]
     tune = []
-    ws = dmp.workspace(max(dmp.purify_workspace_bytes(n, dmp.make_opts("int8", 9, args.executor, refine=9)),
-                           dmp.purify_workspace_bytes(n, dmp.make_opts("bf16", 9, args.executor, refine=9)),
-                           dmp.purify_workspace_bytes(n, dmp.make_opts("e4m3", 11, "tc", refine=11))), dev)
+    ws_need = [dmp.purify_workspace_bytes(n, dmp.make_opts("int8", 9, args.executor, refine=9))]
+    if args.executor == "tc":  # the BF16 and E4M3 modes run on the tcgen05 executor only
+        ws_need += [dmp.purify_workspace_bytes(n, dmp.make_opts("bf16", 9, "tc", refine=9)),
+                    dmp.purify_workspace_bytes(n, dmp.make_opts("e4m3", 11, "tc", refine=11))]
+    ws = dmp.workspace(max(ws_need), dev)
     P = torch.empty_like(H)
     for cs, cr in cands:
         _, info = dmp.purify(H, n_occ, mode=mode, slices=cs, executor=args.executor, refine=cr, P=P, ws=ws)
@@ -546,8 +548,8 @@ def run_ours(args):
     methods = []
     if args.targets == "on" and not args.slices:
         for t_mode, t_beta in (("int8", 7), ("bf16", 8), ("e4m3", 5)):
-            if t_mode == "e4m3" and args.executor != "tc":
-                continue  # E4M3 digits run on the tcgen05 executor only
+            if t_mode != "int8" and args.executor != "tc":
+                continue  # BF16 and E4M3 digits run on the tcgen05 executor only
             for target in (1e-5, 1e-8):
                 targets.append(cheapest(t_mode, t_beta, target))
         # the other recursions of the family (TRS4 is the one the paper runs) at the

@@ -81,16 +81,14 @@ int normalize(const dmp_opts* o, Opts& out) {
   return DMP_OK;
 }
 
-// Level sums stay exact in int32 while s k dmax^2 < 2^31 (the IMMA executor
-// and the tcgen05 executor with beta = 7 or E4M3 digits keep them in int32;
-// the tcgen05 executor with beta = 8 keeps a two-word integer).
+// Level sums stay exact in int32 while s k dmax^2 < 2^31 (both executors keep
+// them in int32).
 bool levels_fit_int32(int64_t k, int s, int mode) {
   const double dmax = digit_max(mode);
   const double bound = static_cast<double>(s) * static_cast<double>(k) * dmax * dmax;
   return bound < 2147483648.0;
 }
 
-bool needs_int32(int mode, int executor) { return !(mode == DMP_OZAKI_BF16 && executor == DMP_EXEC_TC); }
 // digit plane element: int8 (IMMA), bfloat16 (tcgen05) or E4M3 bytes (E4M3 mode)
 int elem_bytes(const Opts& o) { return (o.executor == DMP_EXEC_TC && o.mode != DMP_OZAKI_E4M3) ? 2 : 1; }
 int elem_kind(const Opts& o) {
@@ -278,11 +276,11 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   if (rc != DMP_OK) return rc;
   if (H == nullptr || P == nullptr || ws == nullptr) return DMP_ERR_INVALID_ARG;
   if (n < 2 || ldh < n || ldp < n || n_occ <= 0 || n_occ >= n) return DMP_ERR_INVALID_ARG;
-  if (o.mode != DMP_FP64 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.s, o.mode))
+  if (o.mode != DMP_FP64 && !levels_fit_int32(n, o.s, o.mode))
     return DMP_ERR_UNSUPPORTED;
-  if (o.refine > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.refine, o.mode))
+  if (o.refine > 0 && !levels_fit_int32(n, o.refine, o.mode))
     return DMP_ERR_UNSUPPORTED;
-  if (o.late_s > 0 && needs_int32(o.mode, o.executor) && !levels_fit_int32(n, o.late_s, o.mode))
+  if (o.late_s > 0 && !levels_fit_int32(n, o.late_s, o.mode))
     return DMP_ERR_UNSUPPORTED;
   if ((o.refine != 0 || o.method != DMP_METHOD_PM || o.store32 || o.late_s > 0) && tape != nullptr)
     return DMP_ERR_UNSUPPORTED;
@@ -562,7 +560,7 @@ static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_
     DMP_CUDA(launch_gemm_f64(A, lda, B, ldb, m, n, k, 0, epi, nullptr, st));
     return DMP_OK;
   }
-  if ((needs_int32(o.mode, o.executor) || epi.kind == EPI_LEVELS) && !levels_fit_int32(k, o.s, o.mode))
+  if (!levels_fit_int32(k, o.s, o.mode))
     return DMP_ERR_UNSUPPORTED;
   size_t need = 0;
   ozaki_gemm_workspace_size(m, n, k, mode, slices, executor, &need);

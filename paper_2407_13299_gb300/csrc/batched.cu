@@ -261,7 +261,9 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   for (int b = 0; b < batch; ++b) {
     if (H[b] == nullptr || P[b] == nullptr || n[b] < 2 || n_occ[b] <= 0 || n_occ[b] >= n[b])
       return DMP_ERR_INVALID_ARG;
-    if (beta == 7 && static_cast<double>(smax_mode) * n[b] * 16129.0 >= 2147483648.0) return DMP_ERR_UNSUPPORTED;
+    // exact int32 level sums: s k dmax^2 < 2^31 (dmax 127, or 128 for the nearest 8-bit digits)
+    const double dmax = beta == 8 ? 128.0 : 127.0;
+    if (static_cast<double>(smax_mode) * n[b] * dmax * dmax >= 2147483648.0) return DMP_ERR_UNSUPPORTED;
   }
   const int s_cap = opts->slices > 0 ? opts->slices : smax_mode;
   const BatchLayout L = batch_layout(batch, n, s_cap, beta);
@@ -356,8 +358,8 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       BatchMat& M = hm[b];
       const int64_t rows = static_cast<int64_t>(s) * M.n_pad;
       if (!make_map(&M.tmPa, M.planesP, M.k_pad, rows, 128)) return false;
-      if (!make_map(&M.tmPb, M.planesP, M.k_pad, rows, beta == 8 ? 128 : tile_n)) return false;
-      if (!make_map(&M.tmXb, M.planesX, M.k_pad, rows, beta == 8 ? 128 : tile_n)) return false;
+      if (!make_map(&M.tmPb, M.planesP, M.k_pad, rows, tile_n)) return false;
+      if (!make_map(&M.tmXb, M.planesX, M.k_pad, rows, tile_n)) return false;
     }
     return true;
   };
@@ -421,7 +423,6 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     }
     bn = best_bn;
   }
-  if (beta == 8) bn = 128;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = std::make_pair(s, bn);

@@ -21,8 +21,11 @@ constexpr int kPadK8 = 256;      // the same for one-byte E4M3 digits (two 128-e
 constexpr int32_t kBadExp = 0x7fffffff;  // row exponent of a row holding NaN/Inf
 
 inline int beta_of(int mode) { return mode == DMP_OZAKI_BF16 ? 8 : (mode == DMP_OZAKI_E4M3 ? 5 : 7); }
-// largest digit magnitude: 2^beta - 1 for truncated digits, 16 for the nearest E4M3 digits
-inline int digit_max(int mode) { return mode == DMP_OZAKI_E4M3 ? 16 : (1 << beta_of(mode)) - 1; }
+// largest digit magnitude: 127 for the truncated INT8 digits, 2^(beta-1) for
+// the nearest digits (E4M3: 16, BF16: 128)
+inline int digit_max(int mode) {
+  return mode == DMP_OZAKI_E4M3 ? 16 : (mode == DMP_OZAKI_BF16 ? 128 : 127);
+}
 // largest slice count: 70 bits (beta 7), 72 (beta 8), 60 (E4M3 nearest digits)
 inline int max_slices(int mode) { return mode == DMP_OZAKI_E4M3 ? 12 : (mode == DMP_OZAKI_BF16 ? 9 : 10); }
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -76,9 +79,10 @@ __device__ __forceinline__ double stored_value(double v, bool round32) {
 
 // Row split: exponents e_r and `s` digit planes of beta bits of the m x k matrix
 // A (leading dimension lda). Planes are [s][m_pad][k_pad], element kind 1
-// (int8 truncated digits), 3 (the same integers in bfloat16) or 4 (beta 5
-// nearest digits as E4M3 bytes; e_r one larger). Padding rows/columns are
-// zero. Sets *flag to 1 if A holds a NaN/Inf.
+// (int8 truncated digits), 3 (bfloat16: the beta 7 truncated digits, or the
+// beta 8 nearest digits) or 4 (beta 5 nearest digits as E4M3 bytes). Nearest
+// digits take a row exponent one larger. Padding rows/columns are zero. Sets
+// *flag to 1 if A holds a NaN/Inf.
 cudaError_t launch_split_rows(const double* A, int64_t m, int64_t k, int64_t lda, int s, int beta,
                               int32_t* exps, void* planes, int64_t m_pad, int64_t k_pad,
                               int elem_kind, int* flag, const int* done, cudaStream_t st);
@@ -112,8 +116,8 @@ cudaError_t launch_ozaki_imma(const int8_t* A, const int8_t* B, const int32_t* e
 
 // tcgen05 executor (bf16-carried digits, TMEM accumulators, TMA operands).
 // A planes [s][rows_a][k_pad], B planes [s][rows_b][k_pad] in bfloat16 (E4M3
-// bytes for beta 5); rows_a a multiple of 128, rows_b of 256 (beta 7, 5) or
-// 128 (beta 8), k_pad of 64 (128 for beta 5).
+// bytes for beta 5); rows_a a multiple of 128, rows_b of 256, k_pad of 64
+// (128 for beta 5).
 // *err is set to 1 if a bounded device wait expired. `scratch` holds
 // tc_scratch_bytes() of per-CTA float64 partial sums (the kernel is persistent:
 // at most kTcMaxCtas CTAs, one per SM).

@@ -1,21 +1,21 @@
 // tcgen05 executor for the Ozaki slice-pair products (Sec. "Ozaki Scheme", Fig. 2).
 //
-// The digits are small integers (|d| <= 127 for beta = 7, <= 255 for beta = 8),
-// exactly representable in bfloat16, so the slice-pair products run on the
-// 5th-generation tensor cores (tcgen05.mma kind::f16, bf16 x bf16 -> fp32 in
-// tensor memory). The nearest digits of the E4M3 mode (beta = 5, |d| <= 16)
-// are exact E4M3 values and run on kind::f8f6f4 at twice the rate, with the
-// same shared-memory layout in bytes (a 128-byte swizzle row holds 128 of them
-// instead of 64). An fp32 sum of such products is exact while every partial
-// sum stays below 2^24 in magnitude; the K loop is therefore cut into chunks of
-// 1024 (beta = 7: 1024 * 127^2 < 2^24), 256 (beta = 8) or 65536 (beta = 5:
-// 65536 * 16^2 = 2^24, so a whole level is one chunk) K elements. Each chunk
-// lands in one of two TMEM accumulators; while the tensor core fills the other,
-// eight epilogue warps drain the finished one into exact integer level sums in
-// registers (int32; for beta = 8 a two-word hi/lo integer). At the end of a
-// level L the exact S_L is folded into a float64 accumulator kept in the output
-// buffer: acc = S_L 2^(-beta L) + acc, levels from L = s+1 down to 2 -- the
-// same operation sequence as the definition, so the float64 result is
+// The digits are small integers (|d| <= 127 for the truncated beta = 7 digits,
+// <= 128 for the nearest beta = 8 digits), exactly representable in bfloat16,
+// so the slice-pair products run on the 5th-generation tensor cores
+// (tcgen05.mma kind::f16, bf16 x bf16 -> fp32 in tensor memory). The nearest
+// digits of the E4M3 mode (beta = 5, |d| <= 16) are exact E4M3 values and run
+// on kind::f8f6f4 at twice the rate, with the same shared-memory layout in
+// bytes (a 128-byte swizzle row holds 128 of them instead of 64). An fp32 sum
+// of such products is exact while every partial sum stays at most 2^24 in
+// magnitude; the K loop is therefore cut into chunks of 1024 (beta = 7 and 8:
+// 1024 * 128^2 = 2^24) or 65536 (beta = 5: 65536 * 16^2 = 2^24, so a whole
+// level is one chunk) K elements. Each chunk lands in one of two TMEM
+// accumulators; while the tensor core fills the other, eight epilogue warps
+// drain the finished one into exact int32 level sums in registers. Up to G
+// consecutive levels (G = 4 for beta 7 and 5, 3 for beta 8) are combined
+// exactly in int64 and the groups are added in float64 from L = s+1 down to 2
+// -- the same operation sequence as the definition, so the float64 result is
 // bit-for-bit the one the IMMA executor and the oracle produce.
 //
 // CTA layout (320 threads, one CTA per SM):
@@ -25,9 +25,9 @@
 //               stage, commits free the stage and publish finished chunks
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (one output
 //               row per thread) and half of the BN columns
-// Output tile 128 x BN (BN = 256 for beta = 7, 128 for beta = 8). In symmetric
-// mode only tiles holding some element with row <= column run; each element
-// with row <= column is accumulated and written once, and mirrored.
+// Output tile 128 x BN (BN = 256; 128 or 256 in the batched path). In
+// symmetric mode only tiles holding some element with row <= column run; each
+// element with row <= column is accumulated and written once, and mirrored.
 //
 // Every mbarrier wait is bounded by a %globaltimer deadline; on expiry the CTA
 // raises an error flag, drains what it has in flight (bounded again), frees
@@ -76,6 +76,7 @@ struct TcCfg {
 
 struct TcParams {
   int s, beta, KT, CH, ntiles;
+  int group;        // levels combined exactly per int64 group: 4 (beta 7, 5) or 3 (beta 8)
   double* scratch;  // per-CTA float64 partial sums, TC_BM * BN doubles per CTA
   int64_t m, n;
   int64_t rows_a, rows_b;  // padded rows per digit plane
@@ -452,7 +453,7 @@ __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA,
 // leader's (rank 0) full barrier; the leader alone issues the cta_group::2
 // MMAs and its commits arrive on the stage and accumulator barriers of both
 // CTAs; both epilogues release a TMEM buffer on the leader's barrier.
-template <int BN, bool WIDE, bool PAIR, bool F8 = false>
+template <int BN, bool PAIR, bool F8 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const TcParams p) {
@@ -700,7 +701,6 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     long long* scr_d = scr_i + TC_BM * BN;
 
     int32_t S[COLS];
-    int32_t Shi[WIDE ? COLS : 1];
     int buf = 0;
     uint32_t aph[2] = {0u, 0u};
     bool ok = true;
@@ -721,10 +721,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (skip) continue;
       for (int L = s + 1; L >= 2 && ok; --L) {
 #pragma unroll
-        for (int c = 0; c < COLS; ++c) {
-          S[c] = 0;
-          if (WIDE) Shi[c] = 0;
-        }
+        for (int c = 0; c < COLS; ++c) S[c] = 0;
         const int nkb = npairs_of(L, s) * KT;
         const int nch = (nkb + CH - 1) / CH;
         for (int ch = 0; ch < nch; ++ch) {
@@ -754,14 +751,6 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
           aph[buf] ^= 1u;
           buf ^= 1;
-          if (WIDE && ((ch & 63) == 63 || ch == nch - 1)) {
-            // keep the low word in [0, 2^24): value = hi 2^24 + lo
-#pragma unroll
-            for (int c = 0; c < COLS; ++c) {
-              Shi[c] += S[c] >> 24;
-              S[c] &= 0xFFFFFF;
-            }
-          }
         }
         if (!ok) break;
         if (p.epi.kind == EPI_LEVELS && p.mats == nullptr) {
@@ -771,11 +760,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
             for (int c = 0; c < COLS; ++c) {
               const int64_t col = n0 + cbase + c;
-              if (col < p.n) {
-                const int32_t val =
-                    WIDE ? static_cast<int32_t>(static_cast<int64_t>(Shi[c]) * 16777216ll + S[c]) : S[c];
-                p.epi.levels[static_cast<int64_t>(L - 2) * p.m * p.n + r * p.n + col] = val;
-              }
+              if (col < p.n) p.epi.levels[static_cast<int64_t>(L - 2) * p.m * p.n + r * p.n + col] = S[c];
             }
           }
           continue;
@@ -783,53 +768,34 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         // ---- fold the exact level sum (groups of levels, smallest first; see the header)
         {
           const uint64_t pol = policy_evict_last();
-          if (WIDE) {
-            // beta = 8: every level is its own group: D = S_L 2^(-8L) + D in float64
-            const double scale = ldexp(1.0, -p.beta * L);
-            const bool first_level = (L == s + 1);
+          // up to G consecutive levels (G = 4 for beta 7 and 5, 3 for beta 8)
+          // combine exactly in int64, T = sum S_L 2^(beta (L_a - L)) < 2^53. At
+          // the end of a group (other than the last) its exact value
+          // T 2^(-beta L_a) is added to D in float64; the last group is
+          // finished by the output pass below.
+          const int G = p.group;
+          const int gpos = (s + 1 - L) % G;
+          const int La = L + gpos;
+          const bool gend = (gpos == G - 1) && (L != 2);
+          const bool first_group = (s + 1 - L) < G;
+          const double gscale = ldexp(1.0, -p.beta * La);
 #pragma unroll
-            for (int g = 0; g < COLS / 8; ++g) {
-              long long old[8];
-              if (!first_level) {
+          for (int g = 0; g < COLS / 8; ++g) {
+            long long told[8];
+            if (gpos > 0) {
 #pragma unroll
-                for (int t = 0; t < 8; ++t) old[t] = ld_keep(scr_d + 32 * (8 * g + t), pol);
-              }
-#pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                const int c = 8 * g + t;
-                const double Sd = static_cast<double>(Shi[c]) * 16777216.0 + static_cast<double>(S[c]);
-                const double d = first_level ? Sd * scale : fma(Sd, scale, __longlong_as_double(old[t]));
-                st_keep(scr_d + 32 * c, __double_as_longlong(d), pol);
-              }
+              for (int t = 0; t < 8; ++t) told[t] = ld_keep(scr_i + 32 * (8 * g + t), pol);
             }
-          } else {
-            // beta = 7 or 5: up to four consecutive levels combine exactly in
-            // int64, T = sum S_L 2^(beta (L_a - L)) < 2^53. At the end of a group
-            // (other than the last) its exact value T 2^(-beta L_a) is added to
-            // D in float64; the last group is finished by the output pass below.
-            const int gpos = (s + 1 - L) & 3;
-            const int La = L + gpos;
-            const bool gend = (gpos == 3) && (L != 2);
-            const bool first_group = (s + 1 - L) < 4;
-            const double gscale = ldexp(1.0, -p.beta * La);
 #pragma unroll
-            for (int g = 0; g < COLS / 8; ++g) {
-              long long told[8];
-              if (gpos > 0) {
-#pragma unroll
-                for (int t = 0; t < 8; ++t) told[t] = ld_keep(scr_i + 32 * (8 * g + t), pol);
-              }
-#pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                const int c = 8 * g + t;
-                const long long T = (gpos > 0 ? told[t] : 0ll) + static_cast<long long>(S[c]) * (1ll << (p.beta * gpos));
-                if (!gend) {
-                  st_keep(scr_i + 32 * c, T, pol);
-                } else {
-                  const double gv = static_cast<double>(T) * gscale;
-                  const double d = first_group ? gv : __longlong_as_double(ld_keep(scr_d + 32 * c, pol)) + gv;
-                  st_keep(scr_d + 32 * c, __double_as_longlong(d), pol);
-                }
+            for (int t = 0; t < 8; ++t) {
+              const int c = 8 * g + t;
+              const long long T = (gpos > 0 ? told[t] : 0ll) + static_cast<long long>(S[c]) * (1ll << (p.beta * gpos));
+              if (!gend) {
+                st_keep(scr_i + 32 * c, T, pol);
+              } else {
+                const double gv = static_cast<double>(T) * gscale;
+                const double d = first_group ? gv : __longlong_as_double(ld_keep(scr_d + 32 * c, pol)) + gv;
+                st_keep(scr_d + 32 * c, __double_as_longlong(d), pol);
               }
             }
           }
@@ -844,9 +810,9 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const double wa = upd ? jb.epi.state->alpha : 0.0;
         const double w2 = upd ? jb.epi.state->b2 : 0.0;
         const double w3 = upd ? jb.epi.state->b3 : 0.0;
-        // last group (levels 2 .. L_a, L_a = 2 + ((s - 1) & 3)); earlier groups are in D
-        const double lscale = ldexp(1.0, -p.beta * (WIDE ? 2 : 2 + ((s - 1) & 3)));
-        const bool has_d = WIDE || s > 4;
+        // last group (levels 2 .. L_a, L_a = 2 + (s - 1) mod G); earlier groups are in D
+        const double lscale = ldexp(1.0, -p.beta * (2 + (s - 1) % p.group));
+        const bool has_d = s > p.group;
         const uint64_t pol = policy_evict_last();
         double* Cout = jb.epi.C;
         const int64_t ldc = jb.epi.ldc;
@@ -862,7 +828,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             const int c = 8 * g + t;
             const int64_t col = col0 + t;
             const bool ok = col < jb.n;
-            ti[t] = WIDE ? 0ll : ld_keep(scr_i + 32 * c, pol);
+            ti[t] = ld_keep(scr_i + 32 * c, pol);
             td[t] = has_d ? ld_keep(scr_d + 32 * c, pol) : 0ll;
             ecv[t] = ok ? jb.eb[col] : 0;
             // P and P^2 are exactly symmetric: read them at (col, r), coalesced across the warp
@@ -874,9 +840,8 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             const int64_t col = col0 + t;
             if (col >= jb.n) break;
             if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
-            const double acc = WIDE ? __longlong_as_double(td[t])
-                                    : (has_d ? __longlong_as_double(td[t]) + static_cast<double>(ti[t]) * lscale
-                                             : static_cast<double>(ti[t]) * lscale);
+            const double acc = has_d ? __longlong_as_double(td[t]) + static_cast<double>(ti[t]) * lscale
+                                     : static_cast<double>(ti[t]) * lscale;
             double v = (er == kBadExp || ecv[t] == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
                                                             : scale_pow2(acc, er + ecv[t]);
             if (upd) v = wa * pv[t] + w2 * xv[t] + w3 * v;
@@ -942,11 +907,11 @@ bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int6
 
 namespace {
 
-template <int BN, bool WIDE, bool PAIR, bool F8 = false>
+template <int BN, bool PAIR, bool F8 = false>
 cudaError_t set_smem_attr() {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_tc_kernel<BN, WIDE, PAIR, F8>,
+    cudaError_t e = cudaFuncSetAttribute(ozaki_tc_kernel<BN, PAIR, F8>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, PAIR, F8>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -954,11 +919,11 @@ cudaError_t set_smem_attr() {
   return cudaSuccess;
 }
 
-template <int BN, bool WIDE, bool PAIR = false, bool F8 = false>
+template <int BN, bool PAIR = false, bool F8 = false>
 cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& p, int grid,
                            cudaStream_t st) {
   using Cfg = TcCfg<BN, PAIR, F8>;
-  cudaError_t e = set_smem_attr<BN, WIDE, PAIR, F8>();
+  cudaError_t e = set_smem_attr<BN, PAIR, F8>();
   if (e != cudaSuccess) return e;
   if (PAIR) {
     cudaLaunchConfig_t cfg;
@@ -974,10 +939,10 @@ cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const T
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, WIDE, PAIR, F8>, ta, tb, p);
+    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, PAIR, F8>, ta, tb, p);
     if (e != cudaSuccess) return e;
   } else {
-    ozaki_tc_kernel<BN, WIDE, PAIR, F8><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
+    ozaki_tc_kernel<BN, PAIR, F8><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
   }
   count_launch();
   return cudaGetLastError();
@@ -990,7 +955,7 @@ int tc_max_pairs() {
   static int pairs = -1;
   if (pairs < 0) {
     pairs = 0;
-    if (set_smem_attr<256, false, true>() == cudaSuccess) {
+    if (set_smem_attr<256, true>() == cudaSuccess) {
       cudaLaunchConfig_t cfg;
       std::memset(&cfg, 0, sizeof(cfg));
       cfg.gridDim = dim3(2);
@@ -1004,7 +969,7 @@ int tc_max_pairs() {
       cfg.attrs = at;
       cfg.numAttrs = 1;
       int c = 0;
-      if (cudaOccupancyMaxActiveClusters(&c, ozaki_tc_kernel<256, false, true>, &cfg) == cudaSuccess) pairs = c;
+      if (cudaOccupancyMaxActiveClusters(&c, ozaki_tc_kernel<256, true>, &cfg) == cudaSuccess) pairs = c;
     }
     (void)cudaGetLastError();
     pairs = std::min(pairs, kTcMaxCtas / 2);
@@ -1037,14 +1002,12 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
                             int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int s, int beta, int sym,
                             const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  const bool wide = beta == 8;
   const bool f8 = beta == 5;  // E4M3 nearest digits
-  const int BN = wide ? 128 : 256;
+  const int BN = 256;
   const int atom_k = f8 ? 128 : TC_BK;
   if (rows_a % TC_BM != 0 || rows_b % BN != 0 || k_pad % atom_k != 0) return cudaErrorInvalidValue;
-  // beta = 7 and 5 products run on CTA pairs (256 x 256 tiles, 2-SM MMA) when rows allow
-  const bool pair = !wide && g_pairing && rows_a % (2 * TC_BM) == 0 && k_pad % (2 * atom_k) == 0 &&
-                    tc_max_pairs() > 0;
+  // products run on CTA pairs (256 x 256 tiles, 2-SM MMA) when rows allow
+  const bool pair = g_pairing && rows_a % (2 * TC_BM) == 0 && k_pad % (2 * atom_k) == 0 && tc_max_pairs() > 0;
   const int BM = pair ? 2 * TC_BM : TC_BM;
   CUtensorMap ta, tb;
   if (!make_plane_map(&ta, A, k_pad, static_cast<int64_t>(s) * rows_a, TC_BM, f8)) return cudaErrorInvalidValue;
@@ -1058,9 +1021,10 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   p.s = s;
   p.beta = beta;
   p.KT = static_cast<int>(k_pad / atom_k);
-  // K chunk in atoms: 256 (beta 8), 1024 (beta 7) or 65536 (beta 5) K elements
-  // keep every fp32 partial sum at most 2^24 in magnitude
-  p.CH = wide ? 4 : (f8 ? 512 : 16);
+  // K chunk in atoms: 1024 (beta 7: 127^2; beta 8 nearest: 128^2) or 65536
+  // (beta 5 nearest: 16^2) K elements keep every fp32 partial sum at most 2^24
+  p.CH = f8 ? 512 : 16;
+  p.group = beta == 8 ? 3 : 4;
   p.m = m;
   p.n = n;
   p.rows_a = rows_a;
@@ -1093,12 +1057,10 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   ProfScope prof(DMP_PROF_PRODUCT, st);
   if (pair) {
     const int grid = 2 * std::min(ntiles, tc_max_pairs());
-    return f8 ? launch_tc_impl<256, false, true, true>(ta, tb, p, grid, st)
-              : launch_tc_impl<256, false, true>(ta, tb, p, grid, st);
+    return f8 ? launch_tc_impl<256, true, true>(ta, tb, p, grid, st) : launch_tc_impl<256, true>(ta, tb, p, grid, st);
   }
   const int grid = std::min(ntiles, tc_max_ctas());
-  if (f8) return launch_tc_impl<256, false, false, true>(ta, tb, p, grid, st);
-  return wide ? launch_tc_impl<128, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
+  return f8 ? launch_tc_impl<256, false, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
 }
 
 cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, int beta,
@@ -1107,7 +1069,8 @@ cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int
   TcParams p;
   std::memset(&p, 0, sizeof(p));
   p.beta = beta;
-  p.CH = beta == 8 ? 4 : 16;
+  p.CH = 16;
+  p.group = beta == 8 ? 3 : 4;
   p.ntiles = ntiles;
   p.scratch = scratch;
   p.sym = 1;
@@ -1122,7 +1085,6 @@ cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int
   std::memset(&unused, 0, sizeof(unused));
   const int grid = std::min(ntiles, tc_max_ctas());
   ProfScope prof(DMP_PROF_PRODUCT, st);
-  if (beta == 8) return launch_tc_impl<128, true>(unused, unused, p, grid, st);
   if (bn == 128) return launch_tc_impl<128, false>(unused, unused, p, grid, st);
   return launch_tc_impl<256, false>(unused, unused, p, grid, st);
 }

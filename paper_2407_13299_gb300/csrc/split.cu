@@ -10,21 +10,22 @@
 // starts beta i bits below its top (beta s <= 72 < 96). No floating-point
 // rounding is involved, so the digits are exact.
 //
-// Nearest digits (E4M3 mode, beta 5): the row exponent is one larger, so
-// |x| < 1/2, and d_i = floor(y + 1/2) for y = 2^5 x, x <- y - d_i. With
-// V = floor(x 2^95) in two's complement, the first i digits together are
-// N_i = floor(V 2^-(95 - 5i) + 1/2) (the remainder after them lies in
-// [-1/2, 1/2) units of their last place), so d_i = N_i - 32 N_(i-1) is a signed
-// 5-bit field of V plus the bit below it. Bits of x below 2^-95 never reach a
-// rounding bit (at most 60 + 1 bits are read), so the floor is harmless. Every
-// |d_i| <= 16 is an integer of at most four significant bits, exact in E4M3.
+// Nearest digits (E4M3 mode, beta 5; BF16 mode, beta 8): the row exponent is
+// one larger, so |x| < 1/2, and d_i = floor(y + 1/2) for y = 2^beta x,
+// x <- y - d_i. With V = floor(x 2^95) in two's complement, the first i digits
+// together are N_i = floor(V 2^-(95 - beta i) + 1/2) (the remainder after them
+// lies in [-1/2, 1/2) units of their last place), so d_i = N_i - 2^beta N_(i-1)
+// is a signed beta-bit field of V plus the bit below it. Bits of x below 2^-95
+// never reach a rounding bit (at most 72 + 1 bits are read), so the floor is
+// harmless. |d_i| <= 2^(beta-1): integers exact in E4M3 (beta 5) and in
+// bfloat16 (beta 8).
 //
 // One CTA per row. Each thread loads pairs of adjacent entries (16-byte loads,
 // 512 contiguous bytes per warp) and keeps up to 8192 entries of the row in
 // registers, so the row is read from memory once: a max-reduction, then the
 // digits of the same registers go to every plane (4-byte stores of two bf16 or
-// 2-byte stores of two int8 digits per plane). Longer rows take further sweeps
-// that read the rest of the row again.
+// 2-byte stores of two int8 digits per plane; nearest digits: four entries per
+// thread). Longer rows take further sweeps that read the rest of the row again.
 
 #include <cuda_bf16.h>
 
@@ -129,21 +130,21 @@ __device__ __forceinline__ void fix95_signed(double a, int c_row95, uint32_t& v0
   v0 = __funnelshift_l(m_1, m_2, bs);
 }
 
-// Bits [Q, Q + 6) of V read as a signed 6-bit number (Q a compile-time position).
-template <int Q>
-__device__ __forceinline__ int sfield6(uint32_t v0, uint32_t v1, uint32_t v2) {
+// Bits [Q, Q + W) of V read as a signed W-bit number (compile-time position and width).
+template <int Q, int W>
+__device__ __forceinline__ int sfield(uint32_t v0, uint32_t v1, uint32_t v2) {
   uint32_t w;
   int pos;
   if constexpr (Q >= 64) {
     w = v0;
     pos = Q - 64;
-  } else if constexpr (Q >= 32 && Q + 6 <= 64) {
+  } else if constexpr (Q >= 32 && Q + W <= 64) {
     w = v1;
     pos = Q - 32;
   } else if constexpr (Q >= 32) {
     w = __funnelshift_r(v1, v0, Q - 32);
     pos = 0;
-  } else if constexpr (Q + 6 <= 32) {
+  } else if constexpr (Q + W <= 32) {
     w = v2;
     pos = Q;
   } else {
@@ -151,36 +152,48 @@ __device__ __forceinline__ int sfield6(uint32_t v0, uint32_t v1, uint32_t v2) {
     pos = 0;
   }
   int r;
-  asm("bfe.s32 %0, %1, %2, 6;" : "=r"(r) : "r"(w), "r"(pos));
+  asm("bfe.s32 %0, %1, %2, %3;" : "=r"(r) : "r"(w), "r"(pos), "r"(W));
   return r;
 }
 
-// Nearest digit I + 1 from V: N_i = floor(V / 2^p + 1/2) at p = 95 - 5 i is
-// the rounding of V at that position, and d_i = N_i - 32 N_(i-1) works out to
-// the 5-bit field [p, p + 5) of V read as a signed number plus the bit p - 1,
-// i.e. (u + 1) >> 1 for the signed 6-bit field u = [p - 1, p + 5). The value
-// goes to a float exactly (1.5 2^23 + d + 16 holds d + 16 in its low bits), a
-// pair of them to two E4M3 bytes (exact: |d| <= 16).
-// Four consecutive entries (two register pairs) go to one 4-byte word per plane:
-// a warp writes 128 contiguous bytes per plane.
-template <int I>
+// Nearest digit I + 1 from V: N_i = floor(V / 2^p + 1/2) at p = 95 - beta i
+// is the rounding of V at that position, and d_i = N_i - 2^beta N_(i-1) works
+// out to the beta-bit field [p, p + beta) of V read as a signed number plus the
+// bit p - 1, i.e. (u + 1) >> 1 for the signed (beta + 1)-bit field
+// u = [p - 1, p + beta). The value goes to a float exactly (1.5 2^23 + d +
+// 2^(beta-1) holds d + 2^(beta-1) in its low bits). E4M3 digits (beta 5,
+// |d| <= 16): a pair of floats becomes two E4M3 bytes in one conversion.
+// bfloat16 digits (beta 8, |d| <= 128, at most 8 significant bits): the upper
+// half of each float. Four consecutive entries (two register pairs) go to one
+// 4-byte (E4M3) or 8-byte (bfloat16) store per plane: a warp writes 128 or
+// 256 contiguous bytes per plane.
+template <int I, int KIND, int BETA>
 __device__ __forceinline__ void store_nearest4(int s, const uint32_t (&w)[4][3], char* base, int quad_off,
                                                int64_t plane_bytes) {
   if constexpr (I < kMaxSlices) {
     if (I < s) {
-      constexpr int Q = 89 - 5 * I;
+      constexpr int Q = 94 - BETA * (I + 1);
+      constexpr uint32_t kHalf = 1u << (BETA - 1);
       float f[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const uint32_t d16 = static_cast<uint32_t>((sfield6<Q>(w[u][0], w[u][1], w[u][2]) + 33) >> 1);
-        f[u] = __uint_as_float(0x4B400000u | d16) - 12582928.0f;
+        const uint32_t dh = static_cast<uint32_t>((sfield<Q, BETA + 1>(w[u][0], w[u][1], w[u][2]) + 1 +
+                                                   (1 << BETA)) >> 1);  // d + 2^(beta-1)
+        f[u] = __uint_as_float(0x4B400000u | dh) - (12582912.0f + static_cast<float>(kHalf));
       }
-      uint16_t lo, hi;  // upper byte from the first operand
-      asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(f[1]), "f"(f[0]));
-      asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(f[3]), "f"(f[2]));
-      reinterpret_cast<uint32_t*>(base + I * plane_bytes)[quad_off] =
-          static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
-      store_nearest4<I + 1>(s, w, base, quad_off, plane_bytes);
+      if constexpr (KIND == 4) {
+        uint16_t lo, hi;  // upper byte from the first operand
+        asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(f[1]), "f"(f[0]));
+        asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(f[3]), "f"(f[2]));
+        reinterpret_cast<uint32_t*>(base + I * plane_bytes)[quad_off] =
+            static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+      } else {
+        uint2 pk;
+        pk.x = __byte_perm(__float_as_uint(f[0]), __float_as_uint(f[1]), 0x7632);
+        pk.y = __byte_perm(__float_as_uint(f[2]), __float_as_uint(f[3]), 0x7632);
+        reinterpret_cast<uint2*>(base + I * plane_bytes)[quad_off] = pk;
+      }
+      store_nearest4<I + 1, KIND, BETA>(s, w, base, quad_off, plane_bytes);
     }
   }
 }
@@ -189,9 +202,9 @@ __device__ __forceinline__ void store_nearest4(int s, const uint32_t (&w)[4][3],
 // adjacent pairs across the threads (bf16 and int8 digits), or two adjacent
 // pairs per thread (E4M3 digits, so that each thread owns four consecutive
 // entries and stores 4-byte words).
-template <int KIND>
+template <bool QUAD>
 __device__ __forceinline__ int entry_of(int c0, int tid, int q) {
-  if constexpr (KIND == 4) {
+  if constexpr (QUAD) {
     return c0 + 4 * (tid + kSplitThreads * (q >> 1)) + 2 * (q & 1);
   } else {
     return c0 + 2 * (tid + kSplitThreads * q);
@@ -245,11 +258,14 @@ __device__ __forceinline__ void max_bits(double a, uint32_t& mxh, uint32_t& mxl,
 // One row r of A (m x k, leading dimension lda) into exps[r] and the s planes
 // (row length k_pad, plane_stride elements apart); one whole CTA per row.
 // Offsets within a row are 32-bit (k_pad < 2^31, checked by the launcher).
-template <int KIND, int BETA>  // KIND 1: int8 digits, 3: bfloat16 holding the same integers, 4: E4M3 nearest
+// KIND 1: int8 digits, 3: bfloat16 holding the same integers, 4: E4M3 bytes.
+// BETA 7: truncated digits; BETA 5 and 8: nearest digits (four entries per thread).
+template <int KIND, int BETA>
 __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int64_t r, int64_t m, int k,
                                               int64_t lda, int s, int32_t* __restrict__ exps,
                                               void* __restrict__ planes, int k_pad, int64_t plane_stride,
                                               int* flag) {
+  constexpr bool kNearest = BETA != 7;
   const int tid = threadIdx.x;
   __shared__ uint32_t red_h[kSplitThreads / 32], red_l[kSplitThreads / 32];
   __shared__ int red_bad[kSplitThreads / 32];
@@ -259,7 +275,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
 
   double2 v[kPairs];
 #pragma unroll
-  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<KIND>(0, tid, q), k, live, vec);
+  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<kNearest>(0, tid, q), k, live, vec);
   uint32_t mxh = 0, mxl = 0;
   bool bad = false;
 #pragma unroll
@@ -290,7 +306,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
     any_bad |= red_bad[w];
   }
   int e_row = any_bad ? 0 : row_exponent(mxh, mxl);
-  if (KIND == 4 && (mxh | mxl) != 0) ++e_row;  // nearest digits: |x| < 1/2 (a zero row keeps 0)
+  if (kNearest && (mxh | mxl) != 0) ++e_row;  // nearest digits: |x| < 1/2 (a zero row keeps 0)
   if (tid == 0) {
     // a row holding NaN/Inf is marked; the product epilogue then writes NaN
     exps[r] = any_bad ? kBadExp : e_row;
@@ -303,17 +319,17 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
   const int64_t plane_bytes = plane_stride * kElemBytes;
   for (int c0 = 0;;) {
 #pragma unroll
-    for (int q = 0; q < kPairs; q += (KIND == 4 ? 2 : 1)) {
-      const int j = entry_of<KIND>(c0, tid, q);
+    for (int q = 0; q < kPairs; q += (kNearest ? 2 : 1)) {
+      const int j = entry_of<kNearest>(c0, tid, q);
       if (j < k_pad) {
-        if constexpr (KIND == 4) {
+        if constexpr (kNearest) {
           // entries j .. j + 3 (k_pad is a multiple of 4, so all four are inside)
           uint32_t w[4][3];
           fix95_signed(v[q].x, c_row + 1, w[0][0], w[0][1], w[0][2]);
           fix95_signed(v[q].y, c_row + 1, w[1][0], w[1][1], w[1][2]);
           fix95_signed(v[q + 1].x, c_row + 1, w[2][0], w[2][1], w[2][2]);
           fix95_signed(v[q + 1].y, c_row + 1, w[3][0], w[3][1], w[3][2]);
-          store_nearest4<0>(s, w, base, j >> 2, plane_bytes);
+          store_nearest4<0, KIND, BETA>(s, w, base, j >> 2, plane_bytes);
         } else {
           uint32_t a0, a1, a2, b0, b1, b2;
           bool na, nb;
@@ -326,7 +342,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
     if (k_pad - c0 <= kSweep) break;
     c0 += kSweep;
 #pragma unroll
-    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<KIND>(c0, tid, q), k, live, vec);
+    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<kNearest>(c0, tid, q), k, live, vec);
   }
 }
 

@@ -134,30 +134,42 @@ def test_extreme_digits_stay_exact(dmp, executor):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("pairing", [1, 0])
 @pytest.mark.parametrize("m,n,k,s", [(300, 260, 520, 6), (128, 128, 4096, 5), (64, 500, 77, 9)])
-def test_bf16_mode_bit_exact(dmp, m, n, k, s):
-    """beta = 8 digits (|d| <= 255) on the tensor-core executor: 256-wide K
-    chunks and two-word integer level sums."""
+def test_bf16_mode_bit_exact(dmp, pairing, m, n, k, s):
+    """Nearest beta = 8 digits (|d| <= 128) on the tensor-core executor: 1024-wide
+    K chunks and groups of three levels, on CTA pairs and on single CTAs."""
     A = _mixed(m, k, seed=21)
     B = _mixed(k, n, seed=22)
-    want = oz.ozaki_gemm(A, B, s, 8)
-    got = dmp.ozaki_gemm(_dev(A), _dev(B), "bf16", s, "tc").cpu().numpy()
+    want = oz.ozaki_gemm(A, B, s, 8, rounding="nearest")
+    prev = dmp.set_tc_pairing(pairing)
+    try:
+        got = dmp.ozaki_gemm(_dev(A), _dev(B), "bf16", s, "tc").cpu().numpy()
+    finally:
+        dmp.set_tc_pairing(prev)
     assert np.array_equal(got.view(np.int64), want.view(np.int64))
-    e, D, _ = oz.split_rows(A, s, 8)
+    e, D, _ = oz.split_rows(A, s, 8, "nearest")
     ge, gd = dmp.ozaki_split(_dev(A), "bf16", s, "tc")
     assert np.array_equal(ge.cpu().numpy(), e.astype(np.int32))
     assert np.array_equal(gd.float().cpu().numpy().astype(np.int64), D)
 
 
-def test_bf16_mode_large_level_sums(dmp):
-    """beta = 8 level sums beyond int32 (s k 255^2 > 2^31) stay exact in the
-    two-word accumulators: max-magnitude digits, k = 8192."""
-    n, k, s = 128, 8192, 6
-    v = 1.0 - 2.0 ** -48  # six digits of 255
+def test_bf16_mode_chunk_bound(dmp):
+    """Entries 0.4990234375 give a first digit of 128 (y = 127.75) and a second
+    of -64: every 1024-long fp32 chunk of the level-2 product sums 1024 * 2^14
+    = 2^24, the exactness bound, with both signs across the columns."""
+    n, k, s = 256, 8192, 4
+    v = 127.75 / 256.0
     A = np.full((n, k), v)
     B = np.full((k, n), v)
     B[:, 1::2] *= -1.0
-    want = oz.ozaki_gemm(A, B, s, 8)
+    A[3, ::5] *= -1.0
+    _, parts = oz.ozaki_gemm(A, B, s, 8, return_parts=True, rounding="nearest")
+    assert np.all(np.abs(parts["DA"][0]) == 128)
+    S = dmp.ozaki_level_sums(_dev(A), _dev(B), "bf16", s, "tc").cpu().numpy()
+    for L in range(2, s + 2):
+        assert np.array_equal(S[L - 2].astype(np.int64), parts["S"][L]), L
+    want = oz.ozaki_gemm(A, B, s, 8, rounding="nearest")
     got = dmp.ozaki_gemm(_dev(A), _dev(B), "bf16", s, "tc").cpu().numpy()
     assert np.array_equal(got, want)
 
@@ -167,4 +179,4 @@ def test_invalid_arguments(dmp):
     with pytest.raises(dmp.DmpError):
         dmp.ozaki_gemm(A, A, "int8", 11, "imma")  # s beyond 10 for beta 7
     with pytest.raises(dmp.DmpError):
-        dmp.ozaki_gemm(A, A, "bf16", 3, "imma")  # 8-bit digits do not fit int8
+        dmp.ozaki_gemm(A, A, "bf16", 3, "imma")  # the BF16 mode runs on the tensor-core executor only

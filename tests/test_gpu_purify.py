@@ -60,7 +60,7 @@ def test_ozaki_int8_matches_oracle(dmp, executor, n, n_occ, s):
 
 def test_bf16_mode_matches_oracle(dmp):
     h = make_hamiltonian(300, 75, seed=17)
-    ref = pu.purify(h.H, 75, tol=1e-10, product=partial(oz.ozaki_gemm, s=6, beta=8))
+    ref = pu.purify(h.H, 75, tol=1e-10, product=partial(oz.ozaki_gemm, s=6, beta=8, rounding="nearest"))
     P, info = dmp.purify(_dev(h.H), 75, mode="bf16", slices=6, executor="tc", tol=1e-10)
     P = P.cpu().numpy()
     assert np.max(np.abs(P - ref["P"])) <= 1e-8
