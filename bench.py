@@ -458,8 +458,8 @@ def run_ours(args):
     run_peak = peak * (2.0 if f8 else 1.0)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": run_peak, "unit": "TFLOP/s",
                 "frac": achieved / run_peak, "traffic": traffic,
-                "kernel": ("ozaki_tc_kernel<256,false,true,true> (CTA pairs, 2-SM MMA, kind::f8f6f4)" if f8 else
-                           "ozaki_tc_kernel<256,false,true> (CTA pairs, 2-SM MMA)") if args.executor == "tc" else
+                "kernel": ("ozaki_tc_kernel<256,true,true> (CTA pairs, 2-SM MMA, kind::f8f6f4)" if f8 else
+                           "ozaki_tc_kernel<256,true,false> (CTA pairs, 2-SM MMA)") if args.executor == "tc" else
                 "ozaki_imma_kernel",
                 "peak_source": (f"{peak_src} bf16 sustained x 2 (nominal fp8/bf16 ratio)" if f8 else
                                 f"{peak_src} bf16 sustained") + " (kernel timed inside a long step)",

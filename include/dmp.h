@@ -40,8 +40,11 @@ extern "C" {
  * DMP_FP64        every product in float64 (FP64 mma on the GPU).
  * DMP_OZAKI_INT8  Ozaki products with beta = 7 digit slices (|d| <= 127, the
  *                 int8 range): exact s32 accumulation of the level sums.
- * DMP_OZAKI_BF16  Ozaki products with beta = 8 digit slices (|d| <= 255, the
- *                 integers bfloat16 holds exactly), bf16 tensor cores only.
+ * DMP_OZAKI_BF16  Ozaki products with beta = 8 digit slices rounded to nearest
+ *                 (row exponent one larger, d_i = floor(y + 1/2), |d| <= 128,
+ *                 integers bfloat16 holds exactly; digit products stay within
+ *                 2^14 as for INT8 digits), tensor-core executor only. s in
+ *                 [1, 9].
  * DMP_OZAKI_E4M3  Ozaki products with beta = 5 digit slices rounded to nearest
  *                 (the extraction of the original Ozaki scheme): the row
  *                 exponent is one larger (max_j |A_rj| < 2^(e_r - 1)) and
@@ -211,18 +214,18 @@ int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int
  * ozaki_gemm: C = A B, m x k times k x n, through the Ozaki scheme
  * (Sec. "Ozaki Scheme"): A scaled per row and B per column by powers of two,
  * split into `slices` digit planes of beta bits (mode DMP_OZAKI_INT8: beta 7;
- * DMP_OZAKI_BF16: beta 8; DMP_OZAKI_E4M3: beta 5, nearest digits), level sums
+ * DMP_OZAKI_BF16: beta 8 and DMP_OZAKI_E4M3: beta 5, both nearest digits), level sums
  * S_L = sum_{i+j=L} A_i B_j formed exactly for L = 2..s+1, and
  * C = 2^(e_r+f_c) * sum_L S_L 2^(-beta L) in float64: groups of up to four
- * consecutive levels (beta 7 and 5; single levels for beta 8) are first
- * combined exactly in 64-bit integers, then the groups are added in float64
- * from the L = s+1 end to L = 2. With at most two groups (s <= 8 for beta 7
- * and 5) this is the correctly rounded value of the exact sum of the kept
- * pairs. The result is bit-for-bit the same for every executor. mode DMP_FP64
+ * consecutive levels (beta 7 and 5; three for beta 8) are first combined
+ * exactly in 64-bit integers, then the groups are added in float64 from the
+ * L = s+1 end to L = 2. With at most two groups (s <= 8 for beta 7 and 5,
+ * s <= 6 for beta 8) this is the correctly rounded value of the exact sum of
+ * the kept pairs. The result is bit-for-bit the same for every executor. mode DMP_FP64
  * computes a plain float64 product instead.
  * A row of A or column of B holding NaN/Inf gives a NaN row/column of C.
- * Limits: s * k * dmax^2 < 2^31 (exact s32 level sums; dmax = 2^beta - 1, or
- * 16 for E4M3).
+ * Limits: s * k * dmax^2 < 2^31 (exact s32 level sums; dmax = 127 for INT8,
+ * 128 for BF16, 16 for E4M3).
  */
 int ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                int64_t ldb, double* C, int64_t ldc, int32_t mode, int32_t slices, int32_t executor,
@@ -271,11 +274,13 @@ int ozaki_level_sums(int64_t m, int64_t n, int64_t k, const double* A, int64_t l
 /*
  * ozaki_split: the row scaling and digit planes of A (m x k), the first step
  * of the scheme, exactly as the product kernels consume them. exps[m] receives
- * e_r (max_j |A_rj| < 2^e_r, or < 2^(e_r - 1) for DMP_OZAKI_E4M3; 0 for a
+ * e_r (max_j |A_rj| < 2^e_r, or < 2^(e_r - 1) for the nearest digits of
+ * DMP_OZAKI_BF16 and DMP_OZAKI_E4M3; 0 for a
  * zero row; INT32_MAX for a row holding NaN or Inf, whose products are then
  * NaN). digits receives s planes of m x k (plane-major, leading dimension k)
- * of the beta-bit truncated digits, |d| <= 2^beta - 1: int8 for executor
- * DMP_EXEC_IMMA, bfloat16 bit patterns for DMP_EXEC_TC; for DMP_OZAKI_E4M3
+ * of the digits: int8 for executor DMP_EXEC_IMMA, bfloat16 bit patterns for
+ * DMP_EXEC_TC (truncated 7-bit digits, or nearest 8-bit ones for
+ * DMP_OZAKI_BF16); for DMP_OZAKI_E4M3
  * the nearest digits (|d| <= 16) as E4M3 bytes (sign bit 7, exponent bits
  * 3..6 with bias 7, fraction bits 0..2). Workspace as for
  * ozaki_gemm(m, 1, k, ...).
