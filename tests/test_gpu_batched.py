@@ -20,22 +20,24 @@ def _proj(h):
     return V @ V.T
 
 
-def test_small_mixed_batch_matches_single_and_oracle(dmp):
+@pytest.mark.parametrize("mode,s", [("int8", 7), ("bf16", 6)])
+def test_small_mixed_batch_matches_single_and_oracle(dmp, mode, s):
     sizes = [(128, 32), (160, 40), (256, 64), (300, 75), (448, 112), (520, 130)]
     hs = [make_hamiltonian(n, o, seed=700 + n) for n, o in sizes]
     Hs = [torch.from_numpy(h.H).cuda() for h in hs]
-    Ps, infos, rc = dmp.purify_batched(Hs, [o for _, o in sizes], mode="int8", slices=7)
+    Ps, infos, rc = dmp.purify_batched(Hs, [o for _, o in sizes], mode=mode, slices=s)
     assert rc in (dmp.OK, dmp.C_OUT_OF_RANGE, dmp.STALLED)
     for h, H, P, info in zip(hs, Hs, Ps, infos):
         Pn = P.cpu().numpy()
-        P1, i1 = dmp.purify(H, h.n_occ, mode="int8", slices=7, executor="tc")
+        P1, i1 = dmp.purify(H, h.n_occ, mode=mode, slices=s, executor="tc")
         assert np.max(np.abs(Pn - P1.cpu().numpy())) <= 1e-10, h.n
         assert abs(info["iters"] - i1["iters"]) <= 1
         assert np.max(np.abs(Pn - _proj(h))) <= 1e-8
         assert np.array_equal(Pn, Pn.T)
     # one of them against the oracle run in the same mode
     h = hs[3]
-    ref = pu.purify(h.H, h.n_occ, tol=1e-10, product=partial(oz.ozaki_gemm, s=7, beta=7))
+    beta, rounding = (7, "trunc") if mode == "int8" else (8, "nearest")
+    ref = pu.purify(h.H, h.n_occ, tol=1e-10, product=partial(oz.ozaki_gemm, s=s, beta=beta, rounding=rounding))
     assert np.max(np.abs(Ps[3].cpu().numpy() - ref["P"])) <= 1e-8
 
 
