@@ -58,6 +58,24 @@ def test_ozaki_variants_match_oracle(dmp, executor, method, n, n_occ, s):
 
 
 @pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("mode,s,beta", [("bf16", 6, 8), ("e4m3", 9, 5)])
+def test_nearest_digit_modes_match_oracle(dmp, method, mode, s, beta):
+    """SP2 and TRS4 with the nearest-digit modes (BF16: 8-bit digits in
+    bfloat16; E4M3: 5-bit digits in FP8) against the oracle run in the same mode."""
+    n, n_occ = 300, 75
+    h = make_hamiltonian(n, n_occ, seed=n + s + 17)
+    prod = partial(oz.ozaki_gemm, s=s, beta=beta, rounding="nearest")
+    ref = va.purify(h.H, n_occ, method=method, tol=1e-10, product=prod)
+    P, info = dmp.purify(_dev(h.H), n_occ, mode=mode, slices=s, executor="tc", tol=1e-10, method=method)
+    P = P.cpu().numpy()
+    assert info["status"] in (dmp.OK, dmp.C_OUT_OF_RANGE)
+    assert np.max(np.abs(P - ref["P"])) <= 1e-8
+    proj = _projector(h)
+    assert np.max(np.abs(P - proj)) <= max(1e-8, 2.0 * np.max(np.abs(ref["P"] - proj)))
+    assert np.array_equal(P, P.T)
+
+
+@pytest.mark.parametrize("method", METHODS)
 def test_variants_with_refinement_reach_the_energy_target(dmp, method):
     """n = 2048, the benchmark's spectrum: s = 5 loop plus the refinement step."""
     n, n_occ = 2048, 512
