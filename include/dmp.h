@@ -298,8 +298,8 @@ int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* 
  * length `batch`; H[b] and P[b] are device pointers (n[b] x n[b], leading
  * dimension n[b]). infos (host, length batch, nullable) receives one report per
  * matrix. Each matrix stops on its own rule; the call returns DMP_OK when all
- * converged, else the largest status seen. Modes DMP_OZAKI_INT8 and
- * DMP_OZAKI_BF16 (DMP_OZAKI_E4M3 and DMP_FP64 give DMP_ERR_UNSUPPORTED).
+ * converged, else the largest status seen. Modes DMP_OZAKI_INT8, DMP_OZAKI_BF16
+ * and DMP_OZAKI_E4M3 (DMP_FP64 gives DMP_ERR_UNSUPPORTED).
  */
 int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n,
                       const int64_t* n_occ, double* const* P, const dmp_opts* opts,

@@ -155,7 +155,8 @@ int tiles_of(int64_t n_pad, int bn) {
 BatchLayout batch_layout(int batch, const int64_t* n, int s_max, int beta) {
   BatchLayout L;
   Carve c;
-  const int eb = 2;  // bf16 planes (tcgen05 executor)
+  const int eb = beta == 5 ? 1 : 2;  // E4M3 bytes or bf16 planes (tcgen05 executor)
+  const int64_t kq = beta == 5 ? kPadK8 : kPadK;
   L.mats = c.take(sizeof(BatchMat) * batch, 128);
   L.ntiles = 0;
   for (int b = 0; b < batch; ++b) L.ntiles += tiles_of(round_up(n[b], 256), 128);  // the larger of the two counts
@@ -166,7 +167,7 @@ BatchLayout batch_layout(int batch, const int64_t* n, int s_max, int beta) {
   L.scratch = c.take(tc_scratch_bytes());
   int64_t nmax = 2;
   for (int b = 0; b < batch; ++b) {
-    const int64_t np = round_up(n[b], 256), kp = round_up(n[b], kPadK);
+    const int64_t np = round_up(n[b], 256), kp = round_up(n[b], kq);
     L.n_pad.push_back(np);
     L.k_pad.push_back(kp);
     L.state.push_back(c.take(sizeof(PurifyState)));
@@ -181,8 +182,8 @@ BatchLayout batch_layout(int batch, const int64_t* n, int s_max, int beta) {
   }
   // room for the slice-count tuner's single-matrix runs on the largest matrix
   dmp_opts t{};
-  t.mode = beta == 8 ? DMP_OZAKI_BF16 : DMP_OZAKI_INT8;
-  t.slices = beta == 8 ? 9 : 10;
+  t.mode = beta == 8 ? DMP_OZAKI_BF16 : (beta == 5 ? DMP_OZAKI_E4M3 : DMP_OZAKI_INT8);
+  t.slices = max_slices(t.mode);
   t.executor = DMP_EXEC_TC;
   size_t tb = 0;
   dmp_workspace_size(nmax, &t, &tb);
@@ -213,9 +214,11 @@ cudaStream_t capture_stream() {
   return s;
 }
 
-bool make_map(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows) {
-  return make_plane_map_ext(tm, planes, k_pad, rows_total, box_rows);
+bool make_map(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows, bool f8) {
+  return make_plane_map_ext(tm, planes, k_pad, rows_total, box_rows, f8);
 }
+
+bool batch_mode(int32_t mode) { return mode == DMP_OZAKI_INT8 || mode == DMP_OZAKI_BF16 || mode == DMP_OZAKI_E4M3; }
 
 #define DMP_CUDA(call)                          \
   do {                                          \
@@ -236,9 +239,9 @@ int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* 
   if (batch <= 0 || n == nullptr || opts == nullptr || bytes == nullptr) return DMP_ERR_INVALID_ARG;
   for (int b = 0; b < batch; ++b)
     if (n[b] < 2) return DMP_ERR_INVALID_ARG;
-  if (opts->mode != DMP_OZAKI_INT8 && opts->mode != DMP_OZAKI_BF16) return DMP_ERR_UNSUPPORTED;
-  const int beta = opts->mode == DMP_OZAKI_BF16 ? 8 : 7;
-  const int s_max = opts->slices > 0 ? opts->slices : (beta == 8 ? 9 : 10);
+  if (!batch_mode(opts->mode)) return DMP_ERR_UNSUPPORTED;
+  const int beta = beta_of(opts->mode);
+  const int s_max = opts->slices > 0 ? opts->slices : max_slices(opts->mode);
   *bytes = batch_layout(batch, n, s_max, beta).total;
   return DMP_OK;
 }
@@ -249,20 +252,21 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   if (batch <= 0 || H == nullptr || n == nullptr || n_occ == nullptr || P == nullptr || opts == nullptr ||
       ws == nullptr)
     return DMP_ERR_INVALID_ARG;
-  if (opts->mode != DMP_OZAKI_INT8 && opts->mode != DMP_OZAKI_BF16) return DMP_ERR_UNSUPPORTED;
+  if (!batch_mode(opts->mode)) return DMP_ERR_UNSUPPORTED;
   if (opts->executor != DMP_EXEC_AUTO && opts->executor != DMP_EXEC_TC) return DMP_ERR_UNSUPPORTED;
   if (opts->refine_slices != 0) return DMP_ERR_UNSUPPORTED;  // no batched refinement step
   if (opts->flags & DMP_FLAG_FP32_STORAGE) return DMP_ERR_UNSUPPORTED;
   if (opts->late_slices != 0) return DMP_ERR_UNSUPPORTED;  // one slice count per batched launch
   if (opts->method != DMP_METHOD_PM) return DMP_ERR_UNSUPPORTED;  // canonical purification only
-  const int beta = opts->mode == DMP_OZAKI_BF16 ? 8 : 7;
-  const int smax_mode = beta == 8 ? 9 : 10;
+  const int beta = beta_of(opts->mode);
+  const int smax_mode = max_slices(opts->mode);
+  const bool f8 = beta == 5;
   if (opts->slices < 0 || opts->slices > smax_mode) return DMP_ERR_INVALID_ARG;
   for (int b = 0; b < batch; ++b) {
     if (H[b] == nullptr || P[b] == nullptr || n[b] < 2 || n_occ[b] <= 0 || n_occ[b] >= n[b])
       return DMP_ERR_INVALID_ARG;
-    // exact int32 level sums: s k dmax^2 < 2^31 (dmax 127, or 128 for the nearest 8-bit digits)
-    const double dmax = beta == 8 ? 128.0 : 127.0;
+    // exact int32 level sums: s k dmax^2 < 2^31 (dmax 127, 128 or 16)
+    const double dmax = digit_max(opts->mode);
     if (static_cast<double>(smax_mode) * n[b] * dmax * dmax >= 2147483648.0) return DMP_ERR_UNSUPPORTED;
   }
   const int s_cap = opts->slices > 0 ? opts->slices : smax_mode;
@@ -357,9 +361,9 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     for (int b = 0; b < batch; ++b) {
       BatchMat& M = hm[b];
       const int64_t rows = static_cast<int64_t>(s) * M.n_pad;
-      if (!make_map(&M.tmPa, M.planesP, M.k_pad, rows, 128)) return false;
-      if (!make_map(&M.tmPb, M.planesP, M.k_pad, rows, tile_n)) return false;
-      if (!make_map(&M.tmXb, M.planesX, M.k_pad, rows, tile_n)) return false;
+      if (!make_map(&M.tmPa, M.planesP, M.k_pad, rows, 128, f8)) return false;
+      if (!make_map(&M.tmPb, M.planesP, M.k_pad, rows, tile_n, f8)) return false;
+      if (!make_map(&M.tmXb, M.planesX, M.k_pad, rows, tile_n, f8)) return false;
     }
     return true;
   };
@@ -392,8 +396,9 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   std::vector<int4> htiles;
   DMP_CUDA(cudaMemcpyAsync(drow, hrow.data(), sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, st));
 
-  if (!tuned && beta == 7) {
+  if (!tuned && !f8) {
     // tile width: time the P^2 product of the batch's initial guesses with both
+    // (the E4M3 digits run on 256-column tiles only)
     float best = 1e30f;
     int best_bn = 256;
     int rc = init_states();
@@ -444,6 +449,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   std::string gkey(reinterpret_cast<const char*>(hm.data()), sizeof(BatchMat) * batch);
   gkey.append(reinterpret_cast<const char*>(&ws), sizeof(ws));
   gkey.append(reinterpret_cast<const char*>(&bn), sizeof(bn));
+  gkey.append(reinterpret_cast<const char*>(&tbeta), sizeof(tbeta));  // the digit rule picks the kernels
   cudaGraphExec_t exec = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_graph_mu);

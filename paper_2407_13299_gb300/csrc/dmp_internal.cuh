@@ -259,7 +259,8 @@ struct alignas(128) BatchMat {
 
 // 2-D TMA map over s stacked bf16 digit planes (k_pad contiguous, rows_total
 // rows), 64 x box_rows boxes with 128-byte swizzle.
-bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows);
+bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows,
+                        bool f8);
 
 // Grouped kernels (every launch covers all matrices; finished ones are skipped).
 // `which`: 0 = buf[0], 1 = buf[1], 2 = X2.

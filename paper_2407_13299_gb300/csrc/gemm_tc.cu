@@ -412,7 +412,7 @@ __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA,
   j.m = M.n;
   j.n = M.n;
   j.s = M.s;
-  j.KT = static_cast<int>(M.k_pad / TC_BK);
+  j.KT = static_cast<int>(M.k_pad / (p.beta == 5 ? 128 : TC_BK));  // K atoms of 128 bytes
   j.skip = M.state->done != 0;
   j.sym = true;
   j.ta = &M.tmPa;
@@ -901,8 +901,9 @@ bool make_plane_map(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t 
 
 }  // namespace
 
-bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows) {
-  return make_plane_map(tm, planes, k_pad, rows_total, box_rows);
+bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int64_t rows_total, int box_rows,
+                        bool f8) {
+  return make_plane_map(tm, planes, k_pad, rows_total, box_rows, f8);
 }
 
 namespace {
@@ -1069,7 +1070,7 @@ cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int
   TcParams p;
   std::memset(&p, 0, sizeof(p));
   p.beta = beta;
-  p.CH = 16;
+  p.CH = beta == 5 ? 512 : 16;
   p.group = beta == 8 ? 3 : 4;
   p.ntiles = ntiles;
   p.scratch = scratch;
@@ -1085,6 +1086,8 @@ cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int
   std::memset(&unused, 0, sizeof(unused));
   const int grid = std::min(ntiles, tc_max_ctas());
   ProfScope prof(DMP_PROF_PRODUCT, st);
+  if (beta == 5) return bn == 256 ? launch_tc_impl<256, false, true>(unused, unused, p, grid, st)
+                                  : cudaErrorInvalidValue;  // E4M3 digits: 256-column tiles
   if (bn == 128) return launch_tc_impl<128, false>(unused, unused, p, grid, st);
   return launch_tc_impl<256, false>(unused, unused, p, grid, st);
 }

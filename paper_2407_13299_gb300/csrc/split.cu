@@ -358,7 +358,7 @@ split_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t ld
 
 // Grouped: CTA x covers row x - row_start[b] of matrix b (row_start ascending,
 // row_start[nmats] = total padded rows). Finished matrices are skipped.
-template <int BETA>
+template <int KIND, int BETA>
 __global__ void __launch_bounds__(kSplitThreads, 2)
 split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restrict__ row_start, int nmats,
                      int which) {
@@ -375,8 +375,8 @@ split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restric
   const int64_t lda = which == 0 ? M.ldp : M.n;
   int32_t* exps = which == 2 ? M.expsX : M.expsP;
   void* planes = which == 2 ? M.planesX : M.planesP;
-  split_one_row<3, BETA>(A, r, M.n, static_cast<int>(M.n), lda, M.s, exps, planes, static_cast<int>(M.k_pad),
-                         M.n_pad * M.k_pad, nullptr);
+  split_one_row<KIND, BETA>(A, r, M.n, static_cast<int>(M.n), lda, M.s, exps, planes, static_cast<int>(M.k_pad),
+                            M.n_pad * M.k_pad, nullptr);
 }
 
 __global__ void transpose_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
@@ -438,12 +438,13 @@ cudaError_t launch_split_grouped(const BatchMat* mats, const int64_t* row_start,
                                  int which, int beta, cudaStream_t st) {
   if (total_rows <= 0) return cudaSuccess;
   ProfScope prof(DMP_PROF_SPLIT, st);  // batch rows are at most a few thousand long (k_pad << kMaxRow)
+  const unsigned grid = static_cast<unsigned>(total_rows);
   if (beta == 7) {
-    split_grouped_kernel<7><<<static_cast<unsigned>(total_rows), kSplitThreads, 0, st>>>(mats, row_start, nmats,
-                                                                                         which);
+    split_grouped_kernel<3, 7><<<grid, kSplitThreads, 0, st>>>(mats, row_start, nmats, which);
   } else if (beta == 8) {
-    split_grouped_kernel<8><<<static_cast<unsigned>(total_rows), kSplitThreads, 0, st>>>(mats, row_start, nmats,
-                                                                                         which);
+    split_grouped_kernel<3, 8><<<grid, kSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+  } else if (beta == 5) {
+    split_grouped_kernel<4, 5><<<grid, kSplitThreads, 0, st>>>(mats, row_start, nmats, which);
   } else {
     return cudaErrorInvalidValue;
   }

@@ -20,7 +20,7 @@ def _proj(h):
     return V @ V.T
 
 
-@pytest.mark.parametrize("mode,s", [("int8", 7), ("bf16", 6)])
+@pytest.mark.parametrize("mode,s", [("int8", 7), ("bf16", 6), ("e4m3", 10)])
 def test_small_mixed_batch_matches_single_and_oracle(dmp, mode, s):
     sizes = [(128, 32), (160, 40), (256, 64), (300, 75), (448, 112), (520, 130)]
     hs = [make_hamiltonian(n, o, seed=700 + n) for n, o in sizes]
@@ -36,7 +36,7 @@ def test_small_mixed_batch_matches_single_and_oracle(dmp, mode, s):
         assert np.array_equal(Pn, Pn.T)
     # one of them against the oracle run in the same mode
     h = hs[3]
-    beta, rounding = (7, "trunc") if mode == "int8" else (8, "nearest")
+    beta, rounding = {"int8": (7, "trunc"), "bf16": (8, "nearest"), "e4m3": (5, "nearest")}[mode]
     ref = pu.purify(h.H, h.n_occ, tol=1e-10, product=partial(oz.ozaki_gemm, s=s, beta=beta, rounding=rounding))
     assert np.max(np.abs(Ps[3].cpu().numpy() - ref["P"])) <= 1e-8
 

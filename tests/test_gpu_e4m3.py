@@ -187,7 +187,7 @@ def test_rejected_combinations(dmp):
     with pytest.raises(RuntimeError):
         dmp.ozaki_gemm(A, A, "e4m3", 5, "imma")  # E4M3 digits run on the tensor-core executor only
     with pytest.raises(RuntimeError):
-        dmp.purify_batched([A, A], [2, 2], mode="e4m3", slices=7)
+        dmp.purify(A, 2, mode="e4m3", slices=5, executor="imma")
 
 
 def test_nonfinite_rows_and_columns(dmp):
