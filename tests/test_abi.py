@@ -96,3 +96,34 @@ def test_argument_errors_without_gpu(built):
     info = dmp.Info()
     rc = L.dm_purify(None, 16, 16, 4, ctypes.byref(o), None, 16, ctypes.byref(info), None, 0, None, 0, None)
     assert rc == dmp.ERR_INVALID_ARG
+
+
+def test_option_validation_needs_no_gpu(built):
+    """Argument checks of the workspace queries (host-side only): slice ranges
+    per mode, executor and method restrictions, and the digit bytes per mode."""
+    import ctypes as ct
+
+    from paper_2407_13299_gb300 import dmp
+
+    def ws(n, **kw):
+        b = ct.c_size_t(0)
+        return dmp.lib().dmp_workspace_size(n, ct.byref(dmp.make_opts(**kw)), ct.byref(b)), b.value
+
+    assert ws(512, mode="e4m3", slices=12, executor="tc")[0] == dmp.OK
+    assert ws(512, mode="e4m3", slices=13, executor="tc")[0] == dmp.ERR_INVALID_ARG
+    assert ws(512, mode="bf16", slices=10, executor="tc")[0] == dmp.ERR_INVALID_ARG
+    assert ws(512, mode="bf16", slices=4, executor="imma")[0] == dmp.ERR_UNSUPPORTED
+    assert ws(512, mode="e4m3", slices=4, executor="imma")[0] == dmp.ERR_UNSUPPORTED
+    assert ws(512, mode="int8", slices=5, late_slices=4, late_idem=1.0, method="trs4")[0] == dmp.ERR_UNSUPPORTED
+    assert ws(512, mode="int8", slices=5, late_slices=11, late_idem=1.0)[0] == dmp.ERR_INVALID_ARG
+    # one byte per E4M3 digit against two per bf16-carried digit: the E4M3
+    # workspace is the smaller one at equal s
+    _, b_e4 = ws(2048, mode="e4m3", slices=8, executor="tc")
+    _, b_i8 = ws(2048, mode="int8", slices=8, executor="tc")
+    assert b_e4 < b_i8
+    n = (ct.c_int64 * 2)(256, 384)
+    b = ct.c_size_t(0)
+    assert dmp.lib().dmp_batched_workspace_size(2, n, ct.byref(dmp.make_opts("fp64")), ct.byref(b)) == \
+        dmp.ERR_UNSUPPORTED
+    assert dmp.lib().dmp_batched_workspace_size(2, n, ct.byref(dmp.make_opts("e4m3", 8, "tc")), ct.byref(b)) == \
+        dmp.OK
