@@ -632,6 +632,17 @@ def run_ours(args):
                          f"{info['iters']} iterations"
                          + (f", plus the refinement step's 2 products (s={refine})" if refine > 0 else "") +
                          "; median"}
+        # a second CPU line, labelled as such: the same loop with plain FP64 products
+        # on the host BLAS (numpy), from one timed n x n by n x (n/8) product
+        import numpy as np
+        blk = max(n // 8, 1)
+        t0 = time.perf_counter()
+        np.dot(H_np, H_np[:, :blk])
+        t_blk = time.perf_counter() - t0
+        products = 2 * info["iters"] + 1 + (2 if refine != 0 else 0)
+        cpu["fp64_blas"] = {"value": t_blk * (n / blk) * products, "unit": UNIT, "kind": "numpy FP64 BLAS",
+                            "sample": f"one {n}x{n} by {n}x{blk} FP64 product on the host, scaled to "
+                                      f"{products} full products (the purification's product count)"}
 
     if rank == 0:
         line = {
