@@ -65,6 +65,8 @@ def parse_args():
                          "with or without it), off, or the slice count of its products (-1: FP64)")
     ap.add_argument("--workload", default="purify", choices=["purify", "batch64"],
                     help="purify: the n=8192 benchmark; batch64: the 64-matrix batched workload")
+    ap.add_argument("--batch-mode", default="int8", choices=["int8", "bf16", "e4m3"],
+                    help="slice mode of the batch64 workload")
     ap.add_argument("--gen", default="device", choices=["device", "host"],
                     help="where the QR of the input generator runs (host: numpy, for profiler runs)")
     return ap.parse_args()
@@ -694,35 +696,37 @@ def run_batch64(args):
     hs = [make_hamiltonian(n, o, occ=(-2.0, -0.1), virt=(0.1, 2.0), seed=sd) for n, o, sd in sizes]
     Hs = [torch.from_numpy(h.H).cuda() for h in hs]
     occ = [o for _, o, _ in sizes]
-    opts = dmp.make_opts("int8", 7, "tc")
+    mode = args.batch_mode
+    opts = dmp.make_opts(mode, 7, "tc")
     opts.slices = 0
     ws = dmp.workspace(dmp.batched_workspace_bytes([h.n for h in hs], opts))
     Ps = [torch.empty_like(H) for H in Hs]
-    _, infos, _ = dmp.purify_batched(Hs, occ, slices=0, Ps=Ps, ws=ws)  # tunes and builds the graph
+    _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)  # tunes and builds the graph
     s = infos[0]["slices_used"]
     for _ in range(args.warmup):
-        dmp.purify_batched(Hs, occ, slices=0, Ps=Ps, ws=ws)
+        dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(args.steps):
-        _, infos, _ = dmp.purify_batched(Hs, occ, slices=0, Ps=Ps, ws=ws)
+        _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)
     b.record()
     torch.cuda.synchronize()
     t_batch = a.elapsed_time(b) / 1e3 / args.steps
-    wss = dmp.workspace(dmp.purify_workspace_bytes(max(h.n for h in hs), dmp.make_opts("int8", s, "tc")))
+    wss = dmp.workspace(dmp.purify_workspace_bytes(max(h.n for h in hs), dmp.make_opts(mode, s, "tc")))
     for H, o, P in zip(Hs, occ, Ps):
-        dmp.purify(H, o, mode="int8", slices=s, executor="tc", P=P, ws=wss)
+        dmp.purify(H, o, mode=mode, slices=s, executor="tc", P=P, ws=wss)
     torch.cuda.synchronize()
     a.record()
     for H, o, P in zip(Hs, occ, Ps):
-        dmp.purify(H, o, mode="int8", slices=s, executor="tc", P=P, ws=wss)
+        dmp.purify(H, o, mode=mode, slices=s, executor="tc", P=P, ws=wss)
     b.record()
     torch.cuda.synchronize()
     t_seq = a.elapsed_time(b) / 1e3
     errs = [abs(i["energy"] - float(np.sum(h.e[:h.n_occ]))) / abs(float(np.sum(h.e[:h.n_occ])))
             for i, h in zip(infos, hs)]
-    print(json.dumps({"workload": "batch64: 64 H, n = 32 U{4..48}, n_occ = n/4, gap 0.2, Ozaki-INT8",
+    print(json.dumps({"workload": "batch64: 64 H, n = 32 U{4..48}, n_occ = n/4, gap 0.2",
+                      "mode": f"ozaki-{mode}",
                       "slices": s, "batched_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
                       "max_rel_energy_error": max(errs), "iters_max": max(i["iters"] for i in infos),
                       "steps": args.steps, "warmup": args.warmup}), flush=True)
