@@ -63,8 +63,9 @@ enum { DMP_FP64 = 0, DMP_OZAKI_INT8 = 1, DMP_OZAKI_BF16 = 2, DMP_OZAKI_E4M3 = 3 
  * DMP_EXEC_TC    digits carried in bfloat16 (E4M3 for DMP_OZAKI_E4M3) on the
  *                5th-generation tensor cores (tcgen05), fp32 accumulation in
  *                tensor memory, drained to exact integers every K chunk that
- *                keeps partial sums < 2^24.
- * Both give bit-identical level sums; DMP_EXEC_AUTO picks the faster.
+ *                keeps partial sums at most 2^24 in magnitude.
+ * In the INT8 mode both give bit-identical level sums (the BF16 and E4M3
+ * modes run on DMP_EXEC_TC only); DMP_EXEC_AUTO picks DMP_EXEC_TC.
  */
 enum { DMP_EXEC_AUTO = 0, DMP_EXEC_IMMA = 1, DMP_EXEC_TC = 2 };
 
