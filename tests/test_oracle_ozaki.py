@@ -527,3 +527,47 @@ def test_recombination_8bit_groups_of_three_correctly_rounded(s):
     for r in range(6):
         for c in range(5):
             assert C[r, c] == float(_exact_level_value(S, s, beta, r, c))
+
+
+# ----------------------------------------------------------------- exact equivariances
+
+@pytest.mark.parametrize("beta,rounding", [(7, "trunc"), (8, "nearest"), (5, "nearest")])
+def test_power_of_two_scaling_is_exact(beta, rounding):
+    """Scaling A by 2^k scales every row exponent by k and leaves the digits
+    unchanged, so C scales by exactly 2^k (a wrong exponent offset breaks this)."""
+    A = _mixed_matrix(6, 9, seed=401)
+    B = _mixed_matrix(9, 5, seed=402)
+    C = oz.ozaki_gemm(A, B, 4, beta, rounding=rounding)
+    for k in (-37, 1, 12):
+        Ck = oz.ozaki_gemm(np.ldexp(A, k), B, 4, beta, rounding=rounding)
+        assert np.array_equal(Ck, np.ldexp(C, k)), k
+        Cb = oz.ozaki_gemm(A, np.ldexp(B, k), 4, beta, rounding=rounding)
+        assert np.array_equal(Cb, np.ldexp(C, k)), k
+
+
+@pytest.mark.parametrize("beta,rounding", [(7, "trunc"), (8, "nearest"), (5, "nearest")])
+def test_row_and_column_permutations_commute_exactly(beta, rounding):
+    """Row scaling and digits depend on each row alone (columns of B alone), so
+    permuting rows of A or columns of B permutes C bit for bit."""
+    rng = _rng(403)
+    A = _mixed_matrix(7, 8, seed=404)
+    B = _mixed_matrix(8, 6, seed=405)
+    C = oz.ozaki_gemm(A, B, 5, beta, rounding=rounding)
+    pr, pc = rng.permutation(7), rng.permutation(6)
+    assert np.array_equal(oz.ozaki_gemm(A[pr], B, 5, beta, rounding=rounding), C[pr])
+    assert np.array_equal(oz.ozaki_gemm(A, B[:, pc], 5, beta, rounding=rounding), C[:, pc])
+
+
+@pytest.mark.parametrize("beta,rounding", [(7, "trunc"), (8, "nearest"), (5, "nearest")])
+def test_square_of_a_symmetric_matrix_is_exactly_symmetric(beta, rounding):
+    """For symmetric P the column split of P is its row split, the level sums of
+    P P are exactly symmetric integers and so is the recombined product (the
+    GPU therefore computes only the upper triangle of P^2 and mirrors it)."""
+    rng = _rng(406)
+    X = rng.standard_normal((12, 12)) * np.exp2(rng.integers(-8, 4, size=(12, 12)))
+    P = 0.5 * (X + X.T)
+    C, parts = oz.ozaki_gemm(P, P, 6, beta, return_parts=True, rounding=rounding)
+    assert np.array_equal(parts["e"], parts["f"])
+    for L, S in parts["S"].items():
+        assert np.array_equal(S, S.T), L
+    assert np.array_equal(C, C.T)
