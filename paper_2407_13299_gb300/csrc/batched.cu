@@ -11,6 +11,9 @@
 // every matrix has stopped, so the whole loop runs as one graph launch with no
 // host round trip. Graphs are cached per argument set.
 //
+// Slice modes: INT8, BF16 (nearest 8-bit digits) and E4M3 (nearest 5-bit
+// digits, one-byte planes, 256-column tiles only).
+//
 // The autotuner picks the tile width (128 or 256 columns) by timing the P^2
 // product of the batch with both, and, when opts->slices is 0, the slice count:
 // the smallest s whose band energy on the largest matrix agrees with that of

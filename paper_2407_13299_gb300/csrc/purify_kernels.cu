@@ -8,6 +8,10 @@
 // triangle and doubles the strictly-upper part.
 //
 // Reductions are deterministic: fixed grid, fixed per-thread order, fixed tree.
+//
+// Also here: the elementwise SP2 step and TRS4 factor, the refinement weights
+// and energy, and the FP32-storage rounding of every matrix these kernels
+// store (stored_value, DMP_FLAG_FP32_STORAGE).
 
 #include <algorithm>
 
