@@ -127,3 +127,21 @@ def test_option_validation_needs_no_gpu(built):
         dmp.ERR_UNSUPPORTED
     assert dmp.lib().dmp_batched_workspace_size(2, n, ct.byref(dmp.make_opts("e4m3", 8, "tc")), ct.byref(b)) == \
         dmp.OK
+
+
+def test_no_fallback_without_the_library(tmp_path, monkeypatch):
+    """Without the compiled library every call fails loudly; nothing falls back
+    to a host implementation."""
+    import numpy as np
+    import torch
+
+    from paper_2407_13299_gb300 import dmp
+
+    monkeypatch.setattr(dmp, "LIB_PATH", str(tmp_path / "missing" / "libdmp.so"))
+    monkeypatch.setattr(dmp, "_lib", None)
+    with pytest.raises(ImportError):
+        dmp.lib()
+    with pytest.raises((ImportError, TypeError)):
+        dmp.ozaki_gemm(torch.from_numpy(np.eye(4)), torch.from_numpy(np.eye(4)), "int8", 3)
+    with pytest.raises(ImportError):
+        dmp.purify_workspace_bytes(64, dmp.make_opts("int8", 5))
