@@ -21,8 +21,10 @@ Modules
   adjoint  -- reverse mode through the purification iterations
   variants -- SP2 and TRS4 purification (TRS4 is the algorithm the paper runs
               through NTPoly, Sec. "Implementation Details")
+  foe      -- Chebyshev Fermi-operator expansion at finite electronic
+              temperature (the finite-temperature method of Sec. "Introduction")
 
 Parity status per function is stated in each module header.
 """
 
-from . import adjoint, ozaki, purify, variants  # noqa: F401
+from . import adjoint, foe, ozaki, purify, variants  # noqa: F401
