@@ -36,6 +36,9 @@ Reading implemented here (the GPU path implements the same reading):
 
 No damping kernel is applied to the coefficients (the cited expansion has none).
 
+Symmetric products: `symmetric_output` forms a product's upper triangle and
+mirrors it (the products H_s T_k are symmetric in exact arithmetic).
+
 Parity: pinned. The tests check the coefficients of polynomials (exact
 Chebyshev coefficients), the truncated series against the Fermi function on a
 grid, the matrix recurrence against a dense eigensolver with the same
@@ -96,6 +99,23 @@ def scaling(H, bounds=None):
     if not b > 0.0:
         b = 1.0
     return a, b, h_min, h_max
+
+
+def symmetric_output(product):
+    """The product with symmetric output: the upper triangle of A B, mirrored.
+
+    H_s T_k is symmetric in exact arithmetic (T_k is a polynomial in H_s); a
+    computed product is not quite. Keeping the upper triangle and mirroring it
+    keeps every T_k, and P, exactly symmetric. This is the reading the GPU path
+    takes for its symmetric products, so parity tests run the recurrence with
+    it; the default recurrence forms the products as written.
+    """
+
+    def sym(A, B):
+        C = product(A, B)
+        return np.triu(C) + np.triu(C, 1).T
+
+    return sym
 
 
 def recurrence(Hs, M: int, product=None, coeffs=None):

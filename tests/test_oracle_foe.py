@@ -186,6 +186,26 @@ def test_ozaki_products_converge_to_fp64(mode):
     assert errs[2] < 1e-8
 
 
+def test_symmetric_output_product():
+    """The mirrored product keeps the upper triangle of A B exactly, and the
+    recurrence built on it returns an exactly symmetric P that differs from the
+    plain one at the Ozaki error level only."""
+    rng = np.random.default_rng(4)
+    A, B = rng.standard_normal((40, 40)), rng.standard_normal((40, 40))
+    C = fo.symmetric_output(fo.fp64_product)(A, B)
+    iu = np.triu_indices(40)
+    assert np.array_equal(C[iu], (A @ B)[iu]) and np.array_equal(C, C.T)
+    h = _metallic(n=64, seed=9)
+    prod = partial(oz.ozaki_gemm, s=5, beta=7)
+    ref64, _ = fo.foe(h.H, 0.1, 60, mu=0.0, bounds=BOUNDS)
+    P, _ = fo.foe(h.H, 0.1, 60, mu=0.0, bounds=BOUNDS, product=prod)
+    Ps, _ = fo.foe(h.H, 0.1, 60, mu=0.0, bounds=BOUNDS, product=fo.symmetric_output(prod))
+    assert np.array_equal(Ps, Ps.T)
+    d = np.max(np.abs(P - ref64))
+    assert 0 < d < 1e-8
+    assert np.max(np.abs(Ps - ref64)) < 4 * d
+
+
 def test_argument_errors():
     H = np.eye(4)
     with pytest.raises(ValueError):
