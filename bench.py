@@ -67,6 +67,8 @@ def parse_args():
                     help="purify: the n=8192 benchmark; batch64: the 64-matrix batched workload")
     ap.add_argument("--batch-mode", default="int8", choices=["int8", "bf16", "e4m3"],
                     help="slice mode of the batch64 workload")
+    ap.add_argument("--foe", choices=("on", "off"), default="on",
+                    help="also time the finite-temperature expansion (dm_foe) on the same H, once")
     ap.add_argument("--gen", default="device", choices=["device", "host"],
                     help="where the QR of the input generator runs (host: numpy, for profiler runs)")
     return ap.parse_args()
@@ -600,6 +602,53 @@ def run_ours(args):
                       "value": a.elapsed_time(b) / 2e3, "unit": UNIT, "iters": li["iters"],
                       "late_iters": li["late_iters"], "rel_energy_error": abs(li["energy"] - E_star) / abs(E_star)}
 
+    # ---- the finite-temperature expansion on the same H (the Fermi-operator
+    # expansion Sec. "Introduction" names for metallic systems): kT = 0.05,
+    # M = 200 Chebyshev terms, the spectrum's enclosure as the scaling interval,
+    # mu solved so that tr(P) = n_occ (two passes of the recurrence, 2 (M - 2)
+    # products H_s T_k). Reported, not the headline. The errors are against the
+    # exact f(H) of the known spectrum: its trace and energy at the returned mu.
+    finite_t = None
+    if args.foe == "on" and not args.slices:
+        import numpy as np
+
+        f_kT, f_terms, f_slices = 0.05, 200, 6
+        f_bounds = (min(w["occ"][0], w["virt"][0]), max(w["occ"][1], w["virt"][1]))
+        ws_f = dmp.workspace(dmp.foe_workspace_bytes(n, dmp.make_opts("int8", f_slices, args.executor)), dev)
+        P_f = torch.empty_like(H)
+        f_kw = dict(n_occ=n_occ, bounds=f_bounds, mode="int8", slices=f_slices, executor=args.executor, P=P_f,
+                    ws=ws_f)
+        dmp.foe(H, f_kT, f_terms, **f_kw)
+        torch.cuda.synchronize()
+        dmp.profile_enable(True)
+        dmp.profile_reset()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, fi = dmp.foe(H, f_kT, f_terms, **f_kw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        dmp.profile_enable(False)
+        f_prod_ms, f_prod_n = dmp.profile_read(dmp.PROF_PRODUCT)
+        z = (h.e - fi["mu"]) / f_kT
+        occ_exact = np.where(z > 0, np.exp(-np.abs(z)) / (1.0 + np.exp(-np.abs(z))), 1.0 / (1.0 + np.exp(-np.abs(z))))
+        E_f = float(np.sum(occ_exact * h.e))
+        Q_d = torch.as_tensor(h.Q).to(dev)
+        rows = torch.arange(0, n, max(n // 64, 1), device=dev)
+        exact_rows = (Q_d[rows] * torch.as_tensor(occ_exact, device=dev)[None, :]) @ Q_d.T
+        f_flops = fi["products"] * pairs(f_slices) * unit_flops
+        finite_t = {"value": a.elapsed_time(b) / 1e3, "unit": UNIT, "kT": f_kT, "n_terms": f_terms,
+                    "mode": "ozaki-int8", "slices": f_slices, "enclosure": list(f_bounds), "n_occ": n_occ,
+                    "mu": fi["mu"], "products": fi["products"], "tail": fi["tail"],
+                    "trace_error": abs(fi["trace"] - float(np.sum(occ_exact))),
+                    "rel_energy_error": abs(fi["energy"] - E_f) / abs(E_f),
+                    "max_abs_error_sampled_rows": float((P_f[rows] - exact_rows).abs().max()),
+                    "products_ms": f_prod_ms, "product_launches": f_prod_n,
+                    "product_tflops": f_flops / (f_prod_ms / 1e3) / 1e12 if f_prod_ms > 0 else None,
+                    "note": "Chebyshev Fermi-operator expansion (dm_foe); errors against the exact f(H) of the "
+                            "known spectrum at the returned mu (sampled: every 128th row)"}
+        del ws_f, P_f, Q_d
+
     # ---- FP64 purification on the same GPU (once)
     fp64 = None
     if args.fp64 == "full":
@@ -660,6 +709,7 @@ def run_ours(args):
                            abs(info["energy_unrefined"] - E_star) / abs(E_star),
                        "idempotency": info["idem"], "without_refinement": plain, "targets": targets,
                        "other_methods": methods, "fp32_storage": storage32, "late_schedule": late_sched,
+                       "finite_temperature": finite_t,
                        "l2": (f"inputs larger than L2 (H {n * n * 8 / 2**20:.0f} MiB, digit planes "
                               f"{2 * s * n * n * (1 if mode == 'e4m3' else 2) / 2**30:.2f} GiB)"),
                        "slice_tuning": tune,

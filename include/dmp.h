@@ -335,6 +335,77 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
                        const void* tape, size_t tape_bytes, const double* dLdP, double* dLdH,
                        void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- finite temperature
+ * Fermi-operator expansion: the finite-temperature method the paper names for
+ * metallic systems, where purification does not apply (Sec. "Introduction":
+ * the Fermi Operator Expansion of Goedecker and Teter, Phys. Rev. B 51, 9455;
+ * the paper's own experiments with it are in its Supplementary Information).
+ */
+enum { DMP_FOE_MAX_TERMS = 16384 };
+
+/* Parameters of dm_foe. */
+typedef struct {
+  double kT;           /* electronic temperature, in the energy units of H; > 0       */
+  double mu;           /* chemical potential, used when n_occ == 0                    */
+  int64_t n_occ;       /* 0: mu as given; 0 < n_occ < n: mu is solved so that
+                          tr(P) = n_occ (the recurrence then runs twice)              */
+  int32_t n_terms;     /* Chebyshev terms M in [2, DMP_FOE_MAX_TERMS]                 */
+  int32_t reserved;    /* 0                                                          */
+  double e_min, e_max; /* enclosure of the spectrum of H that scales it into [-1, 1];
+                          e_min >= e_max (e.g. both 0) selects the Gershgorin bounds  */
+} dmp_foe_params;
+
+/* Report of dm_foe, filled when the host pointer is non-NULL. */
+typedef struct {
+  int32_t status;      /* DMP_OK or a negative error                                */
+  int32_t n_terms;     /* M                                                          */
+  int32_t products;    /* matrix products formed: M - 2 per pass                     */
+  int32_t slices_used; /* s (0 in FP64 mode)                                         */
+  double mu;           /* chemical potential of the result                           */
+  double trace;        /* tr(P)                                                      */
+  double energy;       /* tr(P H)                                                    */
+  double band_energy;  /* 2 tr(P H)                                                  */
+  double e_min, e_max; /* the enclosure that scaled H                                */
+  double tail;         /* |c_{M-2}| + |c_{M-1}|: size of the last two coefficients, a
+                          guide to the truncation error of the expansion              */
+} dmp_foe_info;
+
+/* Bytes of workspace dm_foe needs for this n and these options (any M). */
+int dm_foe_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
+
+/*
+ * dm_foe: P = f(H), f(e) = 1 / (1 + exp((e - mu) / kT)) (occupations in [0, 1];
+ * the paper's K = 2P), by a Chebyshev expansion whose matrix products are
+ * formed in opts->mode:
+ *   a = (e_max + e_min) / 2, b = (e_max - e_min) / 2 (b = 1 if the enclosure
+ *   is a point), H_s = (H - a I) / b;
+ *   c_k = (2 / N) sum_j f(a + b x_j) cos(k theta_j), k < M, on the N = 2M
+ *   Gauss-Chebyshev nodes theta_j = pi (j + 1/2) / N, x_j = cos(theta_j);
+ *   P = (c_0 / 2) I + sum_{k=1}^{M-1} c_k T_k(H_s), T_0 = I, T_1 = H_s,
+ *   T_{k+1} = 2 H_s T_k - T_{k-1}: M - 2 products H_s T_k (symmetric: the
+ *   upper triangle is formed and mirrored), H_s split once per call.
+ * With params->n_occ > 0, a first pass of the recurrence collects tr T_k and
+ * mu solves sum_k c_k(mu) tr T_k = n_occ by 100 bisection halvings of
+ * [e_min - 40 kT, e_max + 40 kT]; the second pass forms P.
+ * The truncation error falls roughly like exp(-M pi kT / b): M must grow with
+ * b / kT, so a tight enclosure matters (Gershgorin bounds of a dense H can be
+ * several times wider than its spectrum). An enclosure that misses part of the
+ * spectrum makes the series diverge there.
+ * Options used: mode, slices, executor; refine_slices, late_slices, method and
+ * DMP_FLAG_FP32_STORAGE must be zero/unset (else DMP_ERR_UNSUPPORTED).
+ *   H      n x n, leading dimension ldh; only the upper triangle is read.
+ *   P      n x n output, leading dimension ldp (may not alias H or ws).
+ *   ws     device workspace of dm_foe_workspace_size bytes.
+ * Errors: DMP_ERR_INVALID_ARG (null pointer, n < 2, ld < n, kT not positive and
+ * finite, mu not finite with n_occ == 0, n_occ outside [0, n), M outside
+ * [2, DMP_FOE_MAX_TERMS], a non-finite enclosure), DMP_ERR_NONFINITE (H holds a
+ * NaN/Inf), DMP_ERR_UNSUPPORTED (options above, or the level-sum limit of
+ * ozaki_gemm for k = n), DMP_ERR_WORKSPACE, DMP_ERR_TIMEOUT, DMP_ERR_CUDA.
+ * The call synchronises `stream` after the Gershgorin pass and before it returns.
+ */
+int dm_foe(const double* H, int64_t n, int64_t ldh, const dmp_foe_params* params, const dmp_opts* opts,
+           double* P, int64_t ldp, dmp_foe_info* info, void* ws, size_t ws_bytes, void* stream);
+
 /* Kernel timing. While enabled, every kernel launch of the library is
  * bracketed by two CUDA events recorded on the launching stream, tagged with
  * its class: DMP_PROF_PRODUCT (slice-pair / FP64 product kernels), DMP_PROF_SPLIT

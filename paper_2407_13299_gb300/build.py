@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdmp.so")
 
-SOURCES = ["api.cu", "split.cu", "gemm_imma.cu", "gemm_tc.cu", "gemm_f64.cu", "purify_kernels.cu", "profile.cu", "noalloc.cu", "adjoint.cu", "batched.cu"]
+SOURCES = ["api.cu", "split.cu", "gemm_imma.cu", "gemm_tc.cu", "gemm_f64.cu", "purify_kernels.cu", "profile.cu", "noalloc.cu", "adjoint.cu", "batched.cu", "foe.cu"]
 HEADERS = [os.path.join(CSRC, "dmp_internal.cuh"), os.path.join(ROOT, "include", "dmp.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -221,6 +221,57 @@ BackwardLayout backward_layout(int64_t n, const Opts& o) {
   return B;
 }
 
+// dm_foe workspace: the run state and Gershgorin buffers, the expansion's
+// scalars, coefficients, traces and node arrays (sized for the largest M), and
+// four n x n matrices (H_s, two recurrence terms, the product Y), plus the
+// digit planes of H_s (split once) and of the current term.
+struct FoeLayout {
+  size_t state, rowbuf, scal, coeffs, traces, w, gx, partials, err, Hs, Ta, Tb, Y, expsH, expsT, planesH, planesT,
+      scratch, total;
+  int64_t n_pad, k_pad;
+};
+
+FoeLayout foe_layout(int64_t n, const Opts& o) {
+  FoeLayout F;
+  Carver c;
+  const size_t nn = static_cast<size_t>(n) * n * sizeof(double);
+  F.n_pad = round_up(n, o.mode == DMP_FP64 ? kTileM : row_pad(o.executor));
+  F.k_pad = k_pad_of(o, n);
+  F.state = c.take(sizeof(PurifyState));
+  F.rowbuf = c.take(gershgorin_rowbuf_bytes(n));
+  F.scal = c.take(sizeof(FoeScalars));
+  F.coeffs = c.take(static_cast<size_t>(kFoeMaxTerms) * sizeof(double));
+  F.traces = c.take(static_cast<size_t>(kFoeMaxTerms) * sizeof(double));
+  F.w = c.take(static_cast<size_t>(2 * kFoeMaxTerms) * sizeof(double));
+  F.gx = c.take(static_cast<size_t>(2 * kFoeMaxTerms) * sizeof(double));
+  F.partials = c.take(static_cast<size_t>(kMeasureBlocks) * 10 * sizeof(double));
+  F.err = c.take(sizeof(int32_t));
+  F.Hs = c.take(nn);
+  F.Ta = c.take(nn);
+  F.Tb = c.take(nn);
+  F.Y = c.take(nn);
+  if (o.mode != DMP_FP64) {
+    const size_t plane = static_cast<size_t>(o.s) * F.n_pad * F.k_pad * elem_bytes(o);
+    F.expsH = c.take(static_cast<size_t>(F.n_pad) * sizeof(int32_t));
+    F.expsT = c.take(static_cast<size_t>(F.n_pad) * sizeof(int32_t));
+    F.planesH = c.take(plane);
+    F.planesT = c.take(plane);
+  } else {
+    F.expsH = F.expsT = F.planesH = F.planesT = 0;
+  }
+  F.scratch = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_scratch_bytes()) : 0;
+  F.total = c.cur;
+  return F;
+}
+
+// Options dm_foe accepts: the product mode, slices and executor only.
+int foe_opts(const dmp_opts* opts, Opts& o) {
+  const int rc = normalize(opts, o);
+  if (rc != DMP_OK) return rc;
+  if (o.refine != 0 || o.late_s != 0 || o.method != DMP_METHOD_PM || o.store32) return DMP_ERR_UNSUPPORTED;
+  return DMP_OK;
+}
+
 }  // namespace
 }  // namespace dmp
 
@@ -825,6 +876,150 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
   DMP_CUDA(cudaMemcpyAsync(p0s, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
   DMP_CUDA(launch_p0_adjoint(G, H, n, n, part, p0s, dLdH, n, st));
   DMP_CUDA(cudaStreamSynchronize(st));
+  return DMP_OK;
+}
+
+int dm_foe_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes) {
+  Opts o;
+  const int rc = foe_opts(opts, o);
+  if (rc != DMP_OK) return rc;
+  if (n < 2 || bytes == nullptr) return DMP_ERR_INVALID_ARG;
+  *bytes = foe_layout(n, o).total;
+  return DMP_OK;
+}
+
+int dm_foe(const double* H, int64_t n, int64_t ldh, const dmp_foe_params* params, const dmp_opts* opts,
+           double* P, int64_t ldp, dmp_foe_info* info, void* ws, size_t ws_bytes, void* stream) {
+  Opts o;
+  int rc = foe_opts(opts, o);
+  if (rc != DMP_OK) return rc;
+  if (H == nullptr || P == nullptr || ws == nullptr || params == nullptr) return DMP_ERR_INVALID_ARG;
+  if (n < 2 || ldh < n || ldp < n) return DMP_ERR_INVALID_ARG;
+  const dmp_foe_params fp = *params;
+  const int M = fp.n_terms;
+  const bool canonical = fp.n_occ > 0;
+  if (!(fp.kT > 0.0) || !std::isfinite(fp.kT)) return DMP_ERR_INVALID_ARG;
+  if (fp.n_occ < 0 || fp.n_occ >= n) return DMP_ERR_INVALID_ARG;
+  if (!canonical && !std::isfinite(fp.mu)) return DMP_ERR_INVALID_ARG;
+  if (M < 2 || M > kFoeMaxTerms || fp.reserved != 0) return DMP_ERR_INVALID_ARG;
+  if (!std::isfinite(fp.e_min) || !std::isfinite(fp.e_max)) return DMP_ERR_INVALID_ARG;
+  if (o.mode != DMP_FP64 && !levels_fit_int32(n, o.s, o.mode)) return DMP_ERR_UNSUPPORTED;
+  const FoeLayout L = foe_layout(n, o);
+  if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  PurifyState* state = reinterpret_cast<PurifyState*>(at(ws, L.state));
+  double* rowbuf = reinterpret_cast<double*>(at(ws, L.rowbuf));
+  FoeScalars* sc = reinterpret_cast<FoeScalars*>(at(ws, L.scal));
+  double* coeffs = reinterpret_cast<double*>(at(ws, L.coeffs));
+  double* traces = reinterpret_cast<double*>(at(ws, L.traces));
+  double* w = reinterpret_cast<double*>(at(ws, L.w));
+  double* gx = reinterpret_cast<double*>(at(ws, L.gx));
+  double* partials = reinterpret_cast<double*>(at(ws, L.partials));
+  int* err = reinterpret_cast<int*>(at(ws, L.err));
+  double* Hs = reinterpret_cast<double*>(at(ws, L.Hs));
+  double* Ta = reinterpret_cast<double*>(at(ws, L.Ta));
+  double* Tb = reinterpret_cast<double*>(at(ws, L.Tb));
+  double* Y = reinterpret_cast<double*>(at(ws, L.Y));
+  int32_t* expsH = o.mode != DMP_FP64 ? reinterpret_cast<int32_t*>(at(ws, L.expsH)) : nullptr;
+  int32_t* expsT = o.mode != DMP_FP64 ? reinterpret_cast<int32_t*>(at(ws, L.expsT)) : nullptr;
+  void* planesH = o.mode != DMP_FP64 ? at(ws, L.planesH) : nullptr;
+  void* planesT = o.mode != DMP_FP64 ? at(ws, L.planesT) : nullptr;
+  double* scratch = L.scratch ? reinterpret_cast<double*>(at(ws, L.scratch)) : nullptr;
+  DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+
+  PurifyState init;
+  std::memset(&init, 0, sizeof(init));
+  DMP_CUDA(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  // Gershgorin bounds and the NaN/Inf check of H (the canonical initial guess
+  // this pass also writes into P is overwritten below)
+  DMP_CUDA(launch_gershgorin_init(H, n, ldh, canonical ? fp.n_occ : n / 2, rowbuf, state, P, ldp, st));
+  DMP_CUDA(launch_foe_scale(state, fp.e_min, fp.e_max, fp.e_min < fp.e_max ? 1 : 0, sc, st));
+  int32_t nonfinite = 0;
+  DMP_CUDA(cudaMemcpyAsync(&nonfinite, &sc->nonfinite, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaStreamSynchronize(st));
+  if (nonfinite) {
+    if (info != nullptr) {
+      std::memset(info, 0, sizeof(*info));
+      info->status = DMP_ERR_NONFINITE;
+    }
+    return DMP_ERR_NONFINITE;
+  }
+
+  int products = 0;
+  bool h_split = false;
+  // One pass of T_{k+1} = 2 H_s T_k - T_{k-1}: with `acc` it forms P from the
+  // coefficients, else it records tr T_k.
+  auto pass = [&](bool acc) -> int {
+    DMP_CUDA(launch_foe_init(H, ldh, n, sc, acc ? coeffs : nullptr, Hs, Ta, Tb, P, ldp, st));
+    if (!acc) {
+      DMP_CUDA(launch_foe_trace(Ta, n, n, traces, st));
+      DMP_CUDA(launch_foe_trace(Tb, n, n, traces + 1, st));
+    }
+    if (o.mode != DMP_FP64 && !h_split && M > 2) {
+      // H_s is the same in both passes: its digit planes serve every product
+      DMP_CUDA(launch_split_rows(Hs, n, n, n, o.s, o.beta, expsH, planesH, L.n_pad, L.k_pad, elem_kind(o), nullptr,
+                                 nullptr, st));
+      h_split = true;
+    }
+    EpiArgs e{};
+    e.kind = EPI_SYM_STORE;
+    e.C = Y;
+    e.ldc = n;
+    double* prev = Ta;
+    double* cur = Tb;
+    for (int k = 1; k <= M - 2; ++k) {
+      if (o.mode == DMP_FP64) {
+        DMP_CUDA(launch_gemm_f64(Hs, n, cur, n, n, n, n, 1, e, nullptr, st));
+      } else {
+        DMP_CUDA(launch_split_rows(cur, n, n, n, o.s, o.beta, expsT, planesT, L.n_pad, L.k_pad, elem_kind(o), nullptr,
+                                   nullptr, st));
+        DMP_CUDA(launch_product(o, planesH, planesT, expsH, expsT, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e, nullptr, err,
+                                scratch, st));
+      }
+      ++products;
+      DMP_CUDA(launch_foe_step(Y, prev, acc ? P : nullptr, ldp, coeffs + k + 1, n, st));
+      if (!acc) DMP_CUDA(launch_foe_trace(prev, n, n, traces + k + 1, st));
+      std::swap(prev, cur);
+    }
+    return DMP_OK;
+  };
+
+  if (canonical) {
+    rc = pass(false);
+    if (rc != DMP_OK) return rc;
+    DMP_CUDA(launch_foe_coefficients(sc, fp.kT, 0.0, static_cast<double>(fp.n_occ), traces, M, w, gx, coeffs, st));
+  } else {
+    DMP_CUDA(launch_foe_coefficients(sc, fp.kT, fp.mu, 0.0, nullptr, M, w, gx, coeffs, st));
+  }
+  rc = pass(true);
+  if (rc != DMP_OK) return rc;
+  DMP_CUDA(launch_energy(P, ldp, H, ldh, n, partials, state, st));
+  DMP_CUDA(launch_foe_trace(P, ldp, n, &sc->trace, st));
+
+  FoeScalars fin;
+  double energy = 0.0;
+  double last[2] = {0.0, 0.0};
+  int32_t err_end = 0;
+  DMP_CUDA(cudaMemcpyAsync(&fin, sc, sizeof(fin), cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaMemcpyAsync(&energy, &state->energy_refined, sizeof(double), cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaMemcpyAsync(last, coeffs + (M - 2), 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaMemcpyAsync(&err_end, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaStreamSynchronize(st));
+  if (err_end) return DMP_ERR_TIMEOUT;
+  if (info != nullptr) {
+    info->status = DMP_OK;
+    info->n_terms = M;
+    info->products = products;
+    info->slices_used = o.s;
+    info->mu = fin.mu;
+    info->trace = fin.trace;
+    info->energy = energy;
+    info->band_energy = 2.0 * energy;
+    info->e_min = fin.e_min;
+    info->e_max = fin.e_max;
+    info->tail = std::fabs(last[0]) + std::fabs(last[1]);
+  }
   return DMP_OK;
 }
 

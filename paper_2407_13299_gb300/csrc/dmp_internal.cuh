@@ -161,6 +161,30 @@ cudaError_t launch_copy_matrix(const double* src, int64_t lds, double* dst, int6
 
 constexpr int kMeasureBlocks = 608;  // 4 x 152 SMs; fixed so sums are reproducible
 
+// Chebyshev Fermi-operator expansion (csrc/foe.cu). Scalars on the device:
+// the enclosure [e_min, e_max] that scales H, its centre a and half-width b,
+// the chemical potential and the trace of the result.
+struct FoeScalars {
+  double a, b, mu, e_min, e_max, trace;
+  int32_t nonfinite;  // H held a NaN/Inf (copied from the Gershgorin pass)
+};
+constexpr int kFoeMaxTerms = 16384;  // DMP_FOE_MAX_TERMS
+// Enclosure: the given one when use_given, else the Gershgorin bounds in `state`.
+cudaError_t launch_foe_scale(const PurifyState* state, double e_min, double e_max, int use_given, FoeScalars* sc,
+                             cudaStream_t st);
+// mu (solved from n_occ and the traces tr T_k when `traces` is non-null, else
+// the given mu), then the M coefficients. w and gx hold 2M doubles each.
+cudaError_t launch_foe_coefficients(FoeScalars* sc, double kT, double mu, double n_occ, const double* traces, int M,
+                                    double* w, double* gx, double* coeffs, cudaStream_t st);
+// H_s, T_0 = I, T_1 = H_s (leading dimension n) and, with coeffs, P = c_0/2 I + c_1 H_s.
+cudaError_t launch_foe_init(const double* H, int64_t ldh, int64_t n, const FoeScalars* sc, const double* coeffs,
+                            double* Hs, double* T0, double* T1, double* P, int64_t ldp, cudaStream_t st);
+// Tprev <- 2 Y - Tprev; with P non-null, P += (*coeff) Tprev.
+cudaError_t launch_foe_step(const double* Y, double* Tprev, double* P, int64_t ldp, const double* coeff, int64_t n,
+                            cudaStream_t st);
+// *out = tr A (fixed order).
+cudaError_t launch_foe_trace(const double* A, int64_t lda, int64_t n, double* out, cudaStream_t st);
+
 }  // namespace dmp
 
 namespace dmp {

@@ -51,6 +51,24 @@ class Info(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class FoeParams(ctypes.Structure):
+    _fields_ = [("kT", ctypes.c_double), ("mu", ctypes.c_double), ("n_occ", ctypes.c_int64),
+                ("n_terms", ctypes.c_int32), ("reserved", ctypes.c_int32), ("e_min", ctypes.c_double),
+                ("e_max", ctypes.c_double)]
+
+
+class FoeInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_terms", ctypes.c_int32), ("products", ctypes.c_int32),
+                ("slices_used", ctypes.c_int32), ("mu", ctypes.c_double), ("trace", ctypes.c_double),
+                ("energy", ctypes.c_double), ("band_energy", ctypes.c_double), ("e_min", ctypes.c_double),
+                ("e_max", ctypes.c_double), ("tail", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+FOE_MAX_TERMS = 16384
+
 _lib = None
 
 _i64 = ctypes.c_int64
@@ -80,6 +98,9 @@ SIGNATURES = {
     "dmp_backward_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
     "dm_purify_backward": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(Opts), _vp, _sz, _vp, _vp, _vp,
                                           _sz, _vp]),
+    "dm_foe_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
+    "dm_foe": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(FoeParams), ctypes.POINTER(Opts), _vp, _i64,
+                              ctypes.POINTER(FoeInfo), _vp, _sz, _vp]),
     "dmp_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "dmp_profile_reset": (ctypes.c_int, []),
     "dmp_profile_read": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
@@ -240,6 +261,38 @@ def purify_host(H_host: torch.Tensor, n_occ: int, out: torch.Tensor | None = Non
         timings["in_and_purify"] = t1 - t0
         timings["out"] = time.perf_counter() - t1
     return out, info
+
+
+def foe_workspace_bytes(n: int, opts: Opts) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().dm_foe_workspace_size(n, ctypes.byref(opts), ctypes.byref(b)), "dm_foe_workspace_size")
+    return b.value
+
+
+def foe(H: torch.Tensor, kT: float, n_terms: int, mu: float | None = None, n_occ: int | None = None,
+        bounds=None, mode="int8", slices=7, executor="auto", P=None, ws=None, stream=None):
+    """dm_foe: the Chebyshev Fermi-operator expansion P = f(H) at electronic
+    temperature kT on a float64 CUDA tensor H. Give mu (grand-canonical) or
+    n_occ (mu solved so that tr(P) = n_occ). `bounds` = (e_min, e_max) is a
+    spectral enclosure to scale H by (default: the Gershgorin bounds). Returns
+    (P, info dict)."""
+    _require_cuda(H)
+    if (mu is None) == (n_occ is None):
+        raise ValueError("give exactly one of mu and n_occ")
+    n = H.shape[0]
+    opts = make_opts(mode, slices, executor)
+    lo, hi = (0.0, 0.0) if bounds is None else (float(bounds[0]), float(bounds[1]))
+    params = FoeParams(float(kT), 0.0 if mu is None else float(mu), 0 if n_occ is None else int(n_occ),
+                       int(n_terms), 0, lo, hi)
+    if P is None:
+        P = torch.empty_like(H)
+    if ws is None:
+        ws = workspace(foe_workspace_bytes(n, opts), H.device)
+    info = FoeInfo()
+    code = lib().dm_foe(H.data_ptr(), n, H.stride(0), ctypes.byref(params), ctypes.byref(opts), P.data_ptr(),
+                        P.stride(0), ctypes.byref(info), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _check(code, "dm_foe")
+    return P, info.as_dict()
 
 
 def gemm_workspace_bytes(m, n, k, mode="int8", slices=7, executor="auto") -> int:

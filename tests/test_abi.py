@@ -48,12 +48,14 @@ def test_binding_covers_the_header(built):
 
 
 def test_struct_layouts_match_header(built, tmp_path):
-    """Every field offset and the size of dmp_opts and dmp_info, as a C compiler
+    """Every field offset and the size of each struct of the ABI, as a C compiler
     lays them out from include/dmp.h, equal the binding's ctypes layout."""
     from paper_2407_13299_gb300 import dmp
 
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dmp.h"', "int main(void) {"]
-    for cname, cls in (("dmp_opts", dmp.Opts), ("dmp_info", dmp.Info)):
+    structs = (("dmp_opts", dmp.Opts), ("dmp_info", dmp.Info), ("dmp_foe_params", dmp.FoeParams),
+               ("dmp_foe_info", dmp.FoeInfo))
+    for cname, cls in structs:
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
         for field, _ in cls._fields_:
             lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
@@ -64,7 +66,7 @@ def test_struct_layouts_match_header(built, tmp_path):
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                             check=True).stdout.splitlines())
-    for cname, cls in (("dmp_opts", dmp.Opts), ("dmp_info", dmp.Info)):
+    for cname, cls in structs:
         assert int(got[f"{cname} size"]) == ctypes.sizeof(cls)
         for field, _ in cls._fields_:
             assert int(got[f"{cname} {field}"]) == getattr(cls, field).offset, (cname, field)
@@ -127,6 +129,51 @@ def test_option_validation_needs_no_gpu(built):
         dmp.ERR_UNSUPPORTED
     assert dmp.lib().dmp_batched_workspace_size(2, n, ct.byref(dmp.make_opts("e4m3", 8, "tc")), ct.byref(b)) == \
         dmp.OK
+
+
+def test_foe_validation_needs_no_gpu(built):
+    """dm_foe's argument and option checks run on the host before any CUDA
+    call (the device pointers below are never dereferenced)."""
+    import ctypes as ct
+
+    from paper_2407_13299_gb300 import dmp
+
+    L = dmp.lib()
+    b = ct.c_size_t(0)
+    for kw, want in ((dict(mode="int8", slices=5), dmp.OK), (dict(mode="fp64"), dmp.OK),
+                     (dict(mode="e4m3", slices=8, executor="tc"), dmp.OK),
+                     (dict(mode="int8", slices=5, refine=7), dmp.ERR_UNSUPPORTED),
+                     (dict(mode="int8", slices=5, method="sp2"), dmp.ERR_UNSUPPORTED),
+                     (dict(mode="int8", slices=5, fp32_storage=True), dmp.ERR_UNSUPPORTED),
+                     (dict(mode="int8", slices=5, late_slices=4, late_idem=1e-3), dmp.ERR_UNSUPPORTED)):
+        assert L.dm_foe_workspace_size(512, ct.byref(dmp.make_opts(**kw)), ct.byref(b)) == want, kw
+    o = dmp.make_opts("int8", 5)
+    assert L.dm_foe_workspace_size(1024, ct.byref(o), ct.byref(b)) == dmp.OK
+    assert b.value >= 4 * 1024 * 1024 * 8  # H_s, two recurrence terms and the product
+    need = b.value
+
+    def call(n=1024, ws_bytes=None, **kw):
+        p = dict(kT=0.05, mu=0.0, n_occ=0, n_terms=64, reserved=0, e_min=0.0, e_max=0.0)
+        p.update(kw)
+        params = dmp.FoeParams(**p)
+        info = dmp.FoeInfo()
+        fake = 1 << 40  # never dereferenced: every case below fails its checks first
+        return L.dm_foe(fake, n, n, ct.byref(params), ct.byref(o), fake, n, ct.byref(info), fake,
+                        need if ws_bytes is None else ws_bytes, None)
+
+    assert L.dm_foe(None, 16, 16, None, ct.byref(o), None, 16, None, None, 0, None) == dmp.ERR_INVALID_ARG
+    assert call(kT=0.0) == dmp.ERR_INVALID_ARG
+    assert call(kT=float("inf")) == dmp.ERR_INVALID_ARG
+    assert call(mu=float("nan")) == dmp.ERR_INVALID_ARG
+    assert call(n_terms=1) == dmp.ERR_INVALID_ARG
+    assert call(n_terms=dmp.FOE_MAX_TERMS + 1) == dmp.ERR_INVALID_ARG
+    assert call(n_occ=1024) == dmp.ERR_INVALID_ARG
+    assert call(n_occ=-1) == dmp.ERR_INVALID_ARG
+    assert call(e_min=float("nan")) == dmp.ERR_INVALID_ARG
+    assert call(reserved=1) == dmp.ERR_INVALID_ARG
+    assert call(n=1) == dmp.ERR_INVALID_ARG
+    assert call(ws_bytes=need - 1) == dmp.ERR_WORKSPACE
+    assert call(n=200000) == dmp.ERR_UNSUPPORTED  # level sums of k = n would overflow int32
 
 
 def test_no_fallback_without_the_library(tmp_path, monkeypatch):
