@@ -36,6 +36,24 @@ Reading implemented here (the GPU path implements the same reading):
 
 No damping kernel is applied to the coefficients (the cited expansion has none).
 
+Second scheme, `scheme="ps"`: the same truncated series evaluated with about
+2 sqrt(M) products instead of M - 2, after Liang, Saravanan, Shao, Baer, Bell
+and Head-Gordon (J. Chem. Phys. 119, 4117 (2003), "Improved Fermi operator
+expansion methods"), a Paterson-Stockmeyer evaluation in the Chebyshev basis.
+With q = ceil(sqrt(M)) and y = T_q(H_s):
+* baby steps T_0 .. T_q by the recurrence (q - 1 products, all kept);
+* T_{qm + j} = 2 T_m(y) T_j - T_{qm - j} (the product rule
+  2 T_a T_b = T_{a+b} + T_{|a-b|} and T_{qm} = T_m(T_q)) rewrites the series
+  as sum_{m<r} T_m(y) B_m with B_m = sum_{j<q} w_{m,j} T_j, r = ceil(M/q): the
+  blocks are folded from the top, each term c_{qm+j} (m >= 1, j >= 1) giving
+  2 c to w_{m,j} and -c to the coefficient of T_{qm-j} one block lower;
+* Clenshaw's recurrence in y, b_m = B_m + 2 y b_{m+1} - b_{m+2},
+  P = B_0 + y b_1 - b_2 (r - 1 products);
+* canonical use: the traces come from the giant steps T_{qm} = T_m(y)
+  (r - 2 more products) and tr T_{qm+j} = 2 <T_{qm}, T_j>_F - tr T_{qm-j}
+  (T's symmetric, so tr(AB) is the Frobenius product).
+In exact arithmetic both schemes give the same P.
+
 Symmetric products: `symmetric_output` forms a product's upper triangle and
 mirrors it (the products H_s T_k are symmetric in exact arithmetic).
 
@@ -46,7 +64,10 @@ polynomial (numpy's Chebyshev evaluation on the eigenvalues) and with the
 Fermi function itself, the closed form for a multiple of the identity, the
 particle-hole identity P(2 mu I - H) = I - P(H), permutation equivariance,
 tr(P) = n_occ in canonical use, and the approach to the zero-temperature
-projector as kT falls.
+projector as kT falls. For the Paterson-Stockmeyer scheme: the folded weights
+reproduce the series on scalars (numpy's Chebyshev evaluation, every block
+layout), P agrees with the recurrence and the eigensolver to rounding, the
+traces of the giant steps equal the recurrence's, and the product counts.
 """
 
 from __future__ import annotations
@@ -144,6 +165,97 @@ def recurrence(Hs, M: int, product=None, coeffs=None):
     return np.array(traces), P, products
 
 
+def ps_blocks(M: int):
+    """(q, r): the baby-step count q = ceil(sqrt(M)) and the block count r = ceil(M / q)."""
+    q = 1
+    while q * q < M:
+        q += 1
+    return q, -(-M // q)
+
+
+def ps_fold(coeffs, q: int):
+    """The weights w[m][j] of B_m = sum_{j<q} w[m][j] T_j with P = sum_m T_m(y) B_m.
+
+    a_k starts as the series coefficient of T_k (c_0 / 2 for k = 0). Blocks are
+    folded from the top: T_{qm} = T_m(y) T_0, and for j >= 1
+    T_{qm+j} = 2 T_m(y) T_j - T_{qm-j}, so a_{qm+j} adds 2 a_{qm+j} to w[m][j]
+    and -a_{qm+j} to a_{qm-j}, a term of block m - 1 (not yet folded).
+    """
+    M = len(coeffs)
+    r = -(-M // q)
+    a = np.zeros(r * q)
+    a[:M] = coeffs
+    a[0] = 0.5 * coeffs[0]
+    w = np.zeros((r, q))
+    for m in range(r - 1, 0, -1):
+        w[m, 0] = a[q * m]
+        for j in range(1, q):
+            d = a[q * m + j]
+            w[m, j] = 2.0 * d
+            a[q * m - j] -= d
+    w[0, :] = a[:q]
+    return w
+
+
+def _combine(wrow, T):
+    acc = np.zeros_like(T[0])
+    for j, wj in enumerate(wrow):
+        acc = acc + wj * T[j]
+    return acc
+
+
+def ps_baby_steps(Hs, q: int, product):
+    """T_0 .. T_q by the recurrence: q - 1 products."""
+    T = [np.eye(Hs.shape[0]), Hs.copy()]
+    for j in range(1, q):
+        T.append(2.0 * product(Hs, T[j]) - T[j - 1])
+    return T
+
+
+def ps_traces(T, q: int, M: int, product):
+    """tr T_k, k < M, from the baby steps and the giant steps T_{qm} = T_m(y):
+    tr T_{qm+j} = 2 <T_{qm}, T_j>_F - tr T_{qm-j}. Returns (traces, products)."""
+    traces = np.zeros(M)
+    for k in range(min(q, M)):
+        traces[k] = np.trace(T[k])
+    y = T[q]
+    G_prev, G = T[0], y
+    products = 0
+    m = 1
+    while q * m < M:
+        if m >= 2:
+            G_next = 2.0 * product(y, G) - G_prev
+            products += 1
+            G_prev, G = G, G_next
+        traces[q * m] = np.trace(G)
+        for j in range(1, q):
+            if q * m + j < M:
+                traces[q * m + j] = 2.0 * float(np.sum(G * T[j])) - traces[q * m - j]
+        m += 1
+    return traces, products
+
+
+def ps_evaluate(T, w, product):
+    """Clenshaw in y = T_q: b_m = B_m + 2 y b_{m+1} - b_{m+2}, P = B_0 + y b_1 - b_2.
+    Returns (P, products)."""
+    r = w.shape[0]
+    q = w.shape[1]
+    if r == 1:
+        return _combine(w[0], T), 0
+    y = T[q]
+    products = 0
+    b1 = _combine(w[r - 1], T)
+    b2 = np.zeros_like(b1)
+    for m in range(r - 2, 0, -1):
+        Y = product(y, b1)
+        products += 1
+        bm = (_combine(w[m], T) + 2.0 * Y) - b2
+        b2, b1 = b1, bm
+    Y = product(y, b1)
+    products += 1
+    return (_combine(w[0], T) + Y) - b2, products
+
+
 def expansion_trace(traces, a: float, b: float, mu: float, kT: float, M: int) -> float:
     """sum_k c_k(mu) tr T_k, the trace of the expansion at chemical potential mu."""
     c = chebyshev_coefficients(lambda x: fermi(a + b * x, mu, kT), M)
@@ -164,7 +276,7 @@ def solve_mu(traces, a: float, b: float, h_min: float, h_max: float, kT: float, 
 
 
 def foe(H, kT: float, n_terms: int, mu: float | None = None, n_occ: int | None = None, product=None,
-        bounds=None):
+        bounds=None, scheme: str = "recurrence"):
     """Chebyshev Fermi-operator expansion of H.
 
     Exactly one of mu (grand-canonical) and n_occ (canonical: mu from the
@@ -172,9 +284,12 @@ def foe(H, kT: float, n_terms: int, mu: float | None = None, n_occ: int | None =
     Gershgorin bounds, the coefficients, the traces of T_k (canonical use), the
     number of matrix products, tr(P) and the energy tr(P H). `bounds` =
     (h_min, h_max) is a spectral enclosure to scale H by instead of the
-    Gershgorin bounds.
+    Gershgorin bounds. `scheme` is "recurrence" (M - 2 products per pass) or
+    "ps" (the Paterson-Stockmeyer evaluation of the header).
     """
     H = np.asarray(H, dtype=np.float64)
+    if scheme not in ("recurrence", "ps"):
+        raise ValueError("scheme must be 'recurrence' or 'ps'")
     if (mu is None) == (n_occ is None):
         raise ValueError("give exactly one of mu and n_occ")
     if not kT > 0.0:
@@ -187,6 +302,21 @@ def foe(H, kT: float, n_terms: int, mu: float | None = None, n_occ: int | None =
     Hs = (H - a * np.eye(n)) / b
     products = 0
     traces = None
+    if scheme == "ps":
+        prod = product or fp64_product
+        q, r = ps_blocks(M)
+        T = ps_baby_steps(Hs, q if r > 1 else q - 1, prod)
+        products += len(T) - 2
+        if n_occ is not None:
+            traces, used = ps_traces(T, q, M, prod)
+            products += used
+            mu = solve_mu(traces, a, b, h_min, h_max, kT, M, float(n_occ))
+        coeffs = chebyshev_coefficients(lambda x: fermi(a + b * x, mu, kT), M)
+        P, used = ps_evaluate(T, ps_fold(coeffs, q), prod)
+        products += used
+        info = dict(mu=float(mu), a=a, b=b, h_min=h_min, h_max=h_max, coeffs=coeffs, traces=traces,
+                    products=products, trace=float(np.trace(P)), energy=float(np.sum(P * H)), q=q, r=r)
+        return P, info
     if n_occ is not None:
         traces, _, used = recurrence(Hs, M, product)
         products += used

@@ -206,6 +206,62 @@ def test_symmetric_output_product():
     assert np.max(np.abs(Ps - ref64)) < 4 * d
 
 
+def test_ps_fold_reproduces_the_series_on_scalars():
+    """sum_m T_m(T_q(x)) B_m(x) with the folded weights equals the series
+    sum_k c_k' T_k(x) (numpy's Chebyshev evaluation) for every block layout."""
+    x = np.linspace(-1, 1, 501)
+    rng = np.random.default_rng(11)
+    for M in (2, 3, 7, 16, 17, 50, 199):
+        c = rng.standard_normal(M)
+        q, r = fo.ps_blocks(M)
+        assert q * q >= M > (q - 1) * (q - 1) and (r - 1) * q < M <= r * q
+        w = fo.ps_fold(c, q)
+        y = cheb.chebval(x, np.eye(q + 1)[q])  # T_q(x)
+        Tj = np.array([cheb.chebval(x, np.eye(q)[j]) for j in range(q)])
+        val = sum(cheb.chebval(y, np.eye(r)[m]) * (w[m] @ Tj) for m in range(r))
+        assert np.max(np.abs(val - cheb.chebval(x, _series(c)))) < 1e-12 * np.sum(np.abs(c))
+
+
+@pytest.mark.parametrize("M", [2, 3, 5, 17, 60, 200])
+def test_ps_matches_the_recurrence(M):
+    """Both schemes evaluate the same truncated series: in FP64 they agree to
+    rounding, the scheme uses (q - 1) + (r - 1) products (q - 2 for r = 1),
+    and it matches the eigensolver polynomial."""
+    h = _metallic()
+    P, info = fo.foe(h.H, 0.1, M, mu=0.05, bounds=BOUNDS)
+    Pp, ip = fo.foe(h.H, 0.1, M, mu=0.05, bounds=BOUNDS, scheme="ps")
+    assert np.max(np.abs(Pp - P)) < 1e-14
+    q, r = fo.ps_blocks(M)
+    assert ip["products"] == ((q - 1) + (r - 1) if r > 1 else q - 2)
+    assert np.max(np.abs(Pp - _eigen_polynomial(h.H, ip))) < 1e-13
+
+
+def test_ps_canonical():
+    """Traces from the giant steps and Frobenius products equal the
+    recurrence's traces, so mu and P agree as well; 2 (q - 1) + 2 r - 3 products."""
+    h = make_hamiltonian(96, 30, occ=(-2.0, -0.3), virt=(0.3, 2.0), seed=71)
+    P, info = fo.foe(h.H, 0.05, 200, n_occ=30, bounds=BOUNDS)
+    Pp, ip = fo.foe(h.H, 0.05, 200, n_occ=30, bounds=BOUNDS, scheme="ps")
+    assert np.max(np.abs(ip["traces"] - info["traces"])) < 1e-12
+    assert abs(ip["mu"] - info["mu"]) < 1e-12
+    assert np.max(np.abs(Pp - P)) < 1e-13 and abs(np.trace(Pp) - 30) < 1e-9
+    q, r = fo.ps_blocks(200)
+    assert ip["products"] == (q - 1) + (r - 2) + (r - 1) == 39
+
+
+@pytest.mark.parametrize("mode", ["int8", "e4m3"])
+def test_ps_with_ozaki_products(mode):
+    """With Ozaki products the scheme's error stays at the recurrence's level."""
+    h = _metallic(n=64, seed=8)
+    beta, rounding = oz.BETA[mode], oz.ROUNDING[mode]
+    ref, _ = fo.foe(h.H, 0.1, 120, mu=0.0, bounds=BOUNDS)
+    for s in (5, 7):
+        prod = fo.symmetric_output(partial(oz.ozaki_gemm, s=s, beta=beta, rounding=rounding))
+        P, _ = fo.foe(h.H, 0.1, 120, mu=0.0, bounds=BOUNDS, product=prod)
+        Pp, _ = fo.foe(h.H, 0.1, 120, mu=0.0, bounds=BOUNDS, product=prod, scheme="ps")
+        assert np.max(np.abs(Pp - ref)) <= 3 * np.max(np.abs(P - ref)) + 1e-14
+
+
 def test_argument_errors():
     H = np.eye(4)
     with pytest.raises(ValueError):
@@ -216,3 +272,5 @@ def test_argument_errors():
         fo.foe(H, 0.0, 10, mu=0.0)
     with pytest.raises(ValueError):
         fo.foe(H, 0.1, 1, mu=0.0)
+    with pytest.raises(ValueError):
+        fo.foe(H, 0.1, 10, mu=0.0, scheme="horner")
