@@ -343,6 +343,20 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
  */
 enum { DMP_FOE_MAX_TERMS = 16384 };
 
+/* Evaluation of the series (dmp_foe_params.scheme).
+ * DMP_FOE_RECURRENCE            the three-term recurrence: M - 2 products per pass.
+ * DMP_FOE_PATERSON_STOCKMEYER   the Paterson-Stockmeyer evaluation of Liang et al.
+ *                               (J. Chem. Phys. 119, 4117 (2003)): q = ceil(sqrt(M))
+ *                               baby steps T_1 .. T_q kept, the series folded into
+ *                               sum_{m<r} T_m(y) B_m (y = T_q, r = ceil(M/q), B_m a
+ *                               combination of T_0 .. T_{q-1}) and summed by
+ *                               Clenshaw's recurrence in y: (q - 1) + (r - 1)
+ *                               products, plus r - 2 giant steps T_m(y) whose traces
+ *                               (tr T_{qm+j} = 2 <T_{qm}, T_j>_F - tr T_{qm-j})
+ *                               replace the first pass when mu is solved. Holds q
+ *                               n x n matrices more than the recurrence. */
+enum { DMP_FOE_RECURRENCE = 0, DMP_FOE_PATERSON_STOCKMEYER = 1 };
+
 /* Parameters of dm_foe. */
 typedef struct {
   double kT;           /* electronic temperature, in the energy units of H; > 0       */
@@ -350,7 +364,7 @@ typedef struct {
   int64_t n_occ;       /* 0: mu as given; 0 < n_occ < n: mu is solved so that
                           tr(P) = n_occ (the recurrence then runs twice)              */
   int32_t n_terms;     /* Chebyshev terms M in [2, DMP_FOE_MAX_TERMS]                 */
-  int32_t reserved;    /* 0                                                          */
+  int32_t scheme;      /* DMP_FOE_RECURRENCE (0) or DMP_FOE_PATERSON_STOCKMEYER       */
   double e_min, e_max; /* enclosure of the spectrum of H that scales it into [-1, 1];
                           e_min >= e_max (e.g. both 0) selects the Gershgorin bounds  */
 } dmp_foe_params;
@@ -359,7 +373,7 @@ typedef struct {
 typedef struct {
   int32_t status;      /* DMP_OK or a negative error                                */
   int32_t n_terms;     /* M                                                          */
-  int32_t products;    /* matrix products formed: M - 2 per pass                     */
+  int32_t products;    /* matrix products formed (see the schemes above)             */
   int32_t slices_used; /* s (0 in FP64 mode)                                         */
   double mu;           /* chemical potential of the result                           */
   double trace;        /* tr(P)                                                      */
@@ -370,8 +384,9 @@ typedef struct {
                           guide to the truncation error of the expansion              */
 } dmp_foe_info;
 
-/* Bytes of workspace dm_foe needs for this n and these options (any M). */
-int dm_foe_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
+/* Bytes of workspace dm_foe needs for this n, these parameters (only n_terms
+ * and scheme matter) and these options. */
+int dm_foe_workspace_size(int64_t n, const dmp_foe_params* params, const dmp_opts* opts, size_t* bytes);
 
 /*
  * dm_foe: P = f(H), f(e) = 1 / (1 + exp((e - mu) / kT)) (occupations in [0, 1];
@@ -382,11 +397,13 @@ int dm_foe_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
  *   c_k = (2 / N) sum_j f(a + b x_j) cos(k theta_j), k < M, on the N = 2M
  *   Gauss-Chebyshev nodes theta_j = pi (j + 1/2) / N, x_j = cos(theta_j);
  *   P = (c_0 / 2) I + sum_{k=1}^{M-1} c_k T_k(H_s), T_0 = I, T_1 = H_s,
- *   T_{k+1} = 2 H_s T_k - T_{k-1}: M - 2 products H_s T_k (symmetric: the
- *   upper triangle is formed and mirrored), H_s split once per call.
- * With params->n_occ > 0, a first pass of the recurrence collects tr T_k and
- * mu solves sum_k c_k(mu) tr T_k = n_occ by 100 bisection halvings of
- * [e_min - 40 kT, e_max + 40 kT]; the second pass forms P.
+ *   T_{k+1} = 2 H_s T_k - T_{k-1}, or the Paterson-Stockmeyer scheme above;
+ *   every product is symmetric (its upper triangle is formed and mirrored) and
+ *   H_s (and y = T_q) is split once per call.
+ * With params->n_occ > 0, the traces tr T_k come first (a first pass of the
+ * recurrence, or the giant steps of the Paterson-Stockmeyer scheme) and mu
+ * solves sum_k c_k(mu) tr T_k = n_occ by 100 bisection halvings of
+ * [e_min - 40 kT, e_max + 40 kT]; then P is formed.
  * The truncation error falls roughly like exp(-M pi kT / b): M must grow with
  * b / kT, so a tight enclosure matters (Gershgorin bounds of a dense H can be
  * several times wider than its spectrum). An enclosure that misses part of the
@@ -398,7 +415,8 @@ int dm_foe_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
  *   ws     device workspace of dm_foe_workspace_size bytes.
  * Errors: DMP_ERR_INVALID_ARG (null pointer, n < 2, ld < n, kT not positive and
  * finite, mu not finite with n_occ == 0, n_occ outside [0, n), M outside
- * [2, DMP_FOE_MAX_TERMS], a non-finite enclosure), DMP_ERR_NONFINITE (H holds a
+ * [2, DMP_FOE_MAX_TERMS], an unknown scheme, a non-finite enclosure),
+ * DMP_ERR_NONFINITE (H holds a
  * NaN/Inf), DMP_ERR_UNSUPPORTED (options above, or the level-sum limit of
  * ozaki_gemm for k = n), DMP_ERR_WORKSPACE, DMP_ERR_TIMEOUT, DMP_ERR_CUDA.
  * The call synchronises `stream` after the Gershgorin pass and before it returns.

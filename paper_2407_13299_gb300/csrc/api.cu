@@ -221,32 +221,52 @@ BackwardLayout backward_layout(int64_t n, const Opts& o) {
   return B;
 }
 
+// Baby steps of the Paterson-Stockmeyer scheme: q = ceil(sqrt(M)); r = ceil(M / q) blocks.
+int ps_q(int M) {
+  int q = 1;
+  while (q * q < M) ++q;
+  return q;
+}
+constexpr int kFoeMaxQ = 128;  // ps_q(DMP_FOE_MAX_TERMS)
+
 // dm_foe workspace: the run state and Gershgorin buffers, the expansion's
 // scalars, coefficients, traces and node arrays (sized for the largest M), and
-// four n x n matrices (H_s, two recurrence terms, the product Y), plus the
-// digit planes of H_s (split once) and of the current term.
+// n x n matrices: for the three-term recurrence H_s, two recurrence terms and
+// the product Y; for the Paterson-Stockmeyer scheme the q baby steps T_1 .. T_q
+// (H_s = T_1), Y and two Clenshaw (or giant-step) terms. Digit planes of H_s
+// (split once), of the current right operand, and of y = T_q (scheme 1).
 struct FoeLayout {
-  size_t state, rowbuf, scal, coeffs, traces, w, gx, partials, err, Hs, Ta, Tb, Y, expsH, expsT, planesH, planesT,
-      scratch, total;
+  size_t state, rowbuf, scal, coeffs, traces, w, gx, fold, psw, ip, dots, partials, err, Hs, Ta, Tb, Y, Tps, expsH,
+      expsT, expsY, planesH, planesT, planesY, scratch, total;
   int64_t n_pad, k_pad;
 };
 
-FoeLayout foe_layout(int64_t n, const Opts& o) {
-  FoeLayout F;
+FoeLayout foe_layout(int64_t n, const Opts& o, int scheme, int M) {
+  FoeLayout F{};
   Carver c;
   const size_t nn = static_cast<size_t>(n) * n * sizeof(double);
+  const size_t terms = static_cast<size_t>(2 * kFoeMaxTerms) * sizeof(double);
   F.n_pad = round_up(n, o.mode == DMP_FP64 ? kTileM : row_pad(o.executor));
   F.k_pad = k_pad_of(o, n);
   F.state = c.take(sizeof(PurifyState));
   F.rowbuf = c.take(gershgorin_rowbuf_bytes(n));
   F.scal = c.take(sizeof(FoeScalars));
-  F.coeffs = c.take(static_cast<size_t>(kFoeMaxTerms) * sizeof(double));
-  F.traces = c.take(static_cast<size_t>(kFoeMaxTerms) * sizeof(double));
-  F.w = c.take(static_cast<size_t>(2 * kFoeMaxTerms) * sizeof(double));
-  F.gx = c.take(static_cast<size_t>(2 * kFoeMaxTerms) * sizeof(double));
+  F.coeffs = c.take(terms);
+  F.traces = c.take(terms);
+  F.w = c.take(terms);
+  F.gx = c.take(terms);
+  F.fold = c.take(terms);
+  F.psw = c.take(terms);
+  F.ip = c.take(terms);
+  F.dots = c.take(static_cast<size_t>(kFoeDotBlocks) * kFoeMaxQ * sizeof(double));
   F.partials = c.take(static_cast<size_t>(kMeasureBlocks) * 10 * sizeof(double));
   F.err = c.take(sizeof(int32_t));
-  F.Hs = c.take(nn);
+  if (scheme == DMP_FOE_PATERSON_STOCKMEYER) {
+    F.Tps = c.take(static_cast<size_t>(ps_q(M)) * nn);
+    F.Hs = F.Tps;
+  } else {
+    F.Hs = c.take(nn);
+  }
   F.Ta = c.take(nn);
   F.Tb = c.take(nn);
   F.Y = c.take(nn);
@@ -256,8 +276,10 @@ FoeLayout foe_layout(int64_t n, const Opts& o) {
     F.expsT = c.take(static_cast<size_t>(F.n_pad) * sizeof(int32_t));
     F.planesH = c.take(plane);
     F.planesT = c.take(plane);
-  } else {
-    F.expsH = F.expsT = F.planesH = F.planesT = 0;
+    if (scheme == DMP_FOE_PATERSON_STOCKMEYER) {
+      F.expsY = c.take(static_cast<size_t>(F.n_pad) * sizeof(int32_t));
+      F.planesY = c.take(plane);
+    }
   }
   F.scratch = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_scratch_bytes()) : 0;
   F.total = c.cur;
@@ -879,12 +901,16 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
   return DMP_OK;
 }
 
-int dm_foe_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes) {
+int dm_foe_workspace_size(int64_t n, const dmp_foe_params* params, const dmp_opts* opts, size_t* bytes) {
   Opts o;
   const int rc = foe_opts(opts, o);
   if (rc != DMP_OK) return rc;
-  if (n < 2 || bytes == nullptr) return DMP_ERR_INVALID_ARG;
-  *bytes = foe_layout(n, o).total;
+  if (n < 2 || bytes == nullptr || params == nullptr) return DMP_ERR_INVALID_ARG;
+  const int M = params->n_terms;
+  const int scheme = params->scheme;
+  if (M < 2 || M > kFoeMaxTerms) return DMP_ERR_INVALID_ARG;
+  if (scheme != DMP_FOE_RECURRENCE && scheme != DMP_FOE_PATERSON_STOCKMEYER) return DMP_ERR_INVALID_ARG;
+  *bytes = foe_layout(n, o, scheme, M).total;
   return DMP_OK;
 }
 
@@ -898,34 +924,38 @@ int dm_foe(const double* H, int64_t n, int64_t ldh, const dmp_foe_params* params
   const dmp_foe_params fp = *params;
   const int M = fp.n_terms;
   const bool canonical = fp.n_occ > 0;
+  const bool ps = fp.scheme == DMP_FOE_PATERSON_STOCKMEYER;
   if (!(fp.kT > 0.0) || !std::isfinite(fp.kT)) return DMP_ERR_INVALID_ARG;
   if (fp.n_occ < 0 || fp.n_occ >= n) return DMP_ERR_INVALID_ARG;
   if (!canonical && !std::isfinite(fp.mu)) return DMP_ERR_INVALID_ARG;
-  if (M < 2 || M > kFoeMaxTerms || fp.reserved != 0) return DMP_ERR_INVALID_ARG;
+  if (M < 2 || M > kFoeMaxTerms) return DMP_ERR_INVALID_ARG;
+  if (fp.scheme != DMP_FOE_RECURRENCE && !ps) return DMP_ERR_INVALID_ARG;
   if (!std::isfinite(fp.e_min) || !std::isfinite(fp.e_max)) return DMP_ERR_INVALID_ARG;
   if (o.mode != DMP_FP64 && !levels_fit_int32(n, o.s, o.mode)) return DMP_ERR_UNSUPPORTED;
-  const FoeLayout L = foe_layout(n, o);
+  const FoeLayout L = foe_layout(n, o, fp.scheme, M);
   if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
+  auto dbl = [&](size_t off) { return reinterpret_cast<double*>(at(ws, off)); };
   PurifyState* state = reinterpret_cast<PurifyState*>(at(ws, L.state));
-  double* rowbuf = reinterpret_cast<double*>(at(ws, L.rowbuf));
+  double* rowbuf = dbl(L.rowbuf);
   FoeScalars* sc = reinterpret_cast<FoeScalars*>(at(ws, L.scal));
-  double* coeffs = reinterpret_cast<double*>(at(ws, L.coeffs));
-  double* traces = reinterpret_cast<double*>(at(ws, L.traces));
-  double* w = reinterpret_cast<double*>(at(ws, L.w));
-  double* gx = reinterpret_cast<double*>(at(ws, L.gx));
-  double* partials = reinterpret_cast<double*>(at(ws, L.partials));
+  double* coeffs = dbl(L.coeffs);
+  double* traces = dbl(L.traces);
+  double* w = dbl(L.w);
+  double* gx = dbl(L.gx);
+  double* partials = dbl(L.partials);
   int* err = reinterpret_cast<int*>(at(ws, L.err));
-  double* Hs = reinterpret_cast<double*>(at(ws, L.Hs));
-  double* Ta = reinterpret_cast<double*>(at(ws, L.Ta));
-  double* Tb = reinterpret_cast<double*>(at(ws, L.Tb));
-  double* Y = reinterpret_cast<double*>(at(ws, L.Y));
-  int32_t* expsH = o.mode != DMP_FP64 ? reinterpret_cast<int32_t*>(at(ws, L.expsH)) : nullptr;
-  int32_t* expsT = o.mode != DMP_FP64 ? reinterpret_cast<int32_t*>(at(ws, L.expsT)) : nullptr;
-  void* planesH = o.mode != DMP_FP64 ? at(ws, L.planesH) : nullptr;
-  void* planesT = o.mode != DMP_FP64 ? at(ws, L.planesT) : nullptr;
-  double* scratch = L.scratch ? reinterpret_cast<double*>(at(ws, L.scratch)) : nullptr;
+  double* Hs = dbl(L.Hs);
+  double* Ta = dbl(L.Ta);
+  double* Tb = dbl(L.Tb);
+  double* Y = dbl(L.Y);
+  const bool oz = o.mode != DMP_FP64;
+  int32_t* expsH = oz ? reinterpret_cast<int32_t*>(at(ws, L.expsH)) : nullptr;
+  int32_t* expsT = oz ? reinterpret_cast<int32_t*>(at(ws, L.expsT)) : nullptr;
+  void* planesH = oz ? at(ws, L.planesH) : nullptr;
+  void* planesT = oz ? at(ws, L.planesT) : nullptr;
+  double* scratch = L.scratch ? dbl(L.scratch) : nullptr;
   DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
   PurifyState init;
@@ -947,53 +977,132 @@ int dm_foe(const double* H, int64_t n, int64_t ldh, const dmp_foe_params* params
   }
 
   int products = 0;
-  bool h_split = false;
-  // One pass of T_{k+1} = 2 H_s T_k - T_{k-1}: with `acc` it forms P from the
-  // coefficients, else it records tr T_k.
-  auto pass = [&](bool acc) -> int {
-    DMP_CUDA(launch_foe_init(H, ldh, n, sc, acc ? coeffs : nullptr, Hs, Ta, Tb, P, ldp, st));
-    if (!acc) {
-      DMP_CUDA(launch_foe_trace(Ta, n, n, traces, st));
-      DMP_CUDA(launch_foe_trace(Tb, n, n, traces + 1, st));
-    }
-    if (o.mode != DMP_FP64 && !h_split && M > 2) {
-      // H_s is the same in both passes: its digit planes serve every product
-      DMP_CUDA(launch_split_rows(Hs, n, n, n, o.s, o.beta, expsH, planesH, L.n_pad, L.k_pad, elem_kind(o), nullptr,
-                                 nullptr, st));
-      h_split = true;
-    }
+  // Symmetric product Y = A B of two polynomials in H_s: A's digit planes
+  // (pa, ea) are prepared by the caller, B is split here (FP64: A itself).
+  auto product = [&](const double* A, const void* pa, const int32_t* ea, const double* B) -> int {
     EpiArgs e{};
     e.kind = EPI_SYM_STORE;
     e.C = Y;
     e.ldc = n;
-    double* prev = Ta;
-    double* cur = Tb;
-    for (int k = 1; k <= M - 2; ++k) {
-      if (o.mode == DMP_FP64) {
-        DMP_CUDA(launch_gemm_f64(Hs, n, cur, n, n, n, n, 1, e, nullptr, st));
-      } else {
-        DMP_CUDA(launch_split_rows(cur, n, n, n, o.s, o.beta, expsT, planesT, L.n_pad, L.k_pad, elem_kind(o), nullptr,
-                                   nullptr, st));
-        DMP_CUDA(launch_product(o, planesH, planesT, expsH, expsT, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e, nullptr, err,
-                                scratch, st));
-      }
-      ++products;
-      DMP_CUDA(launch_foe_step(Y, prev, acc ? P : nullptr, ldp, coeffs + k + 1, n, st));
-      if (!acc) DMP_CUDA(launch_foe_trace(prev, n, n, traces + k + 1, st));
-      std::swap(prev, cur);
+    if (!oz) {
+      DMP_CUDA(launch_gemm_f64(A, n, B, n, n, n, n, 1, e, nullptr, st));
+    } else {
+      DMP_CUDA(launch_split_rows(B, n, n, n, o.s, o.beta, expsT, planesT, L.n_pad, L.k_pad, elem_kind(o), nullptr,
+                                 nullptr, st));
+      DMP_CUDA(launch_product(o, pa, planesT, ea, expsT, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e, nullptr, err,
+                              scratch, st));
     }
+    ++products;
+    return DMP_OK;
+  };
+  auto split_a = [&](const double* A, void* planes, int32_t* exps) -> int {
+    if (oz)
+      DMP_CUDA(launch_split_rows(A, n, n, n, o.s, o.beta, exps, planes, L.n_pad, L.k_pad, elem_kind(o), nullptr,
+                                 nullptr, st));
     return DMP_OK;
   };
 
-  if (canonical) {
-    rc = pass(false);
+  if (!ps) {
+    bool h_split = false;
+    // One pass of T_{k+1} = 2 H_s T_k - T_{k-1}: with `acc` it forms P from the
+    // coefficients, else it records tr T_k.
+    auto pass = [&](bool acc) -> int {
+      DMP_CUDA(launch_foe_init(H, ldh, n, sc, acc ? coeffs : nullptr, Hs, Ta, Tb, P, ldp, st));
+      if (!acc) {
+        DMP_CUDA(launch_foe_trace(Ta, n, n, traces, st));
+        DMP_CUDA(launch_foe_trace(Tb, n, n, traces + 1, st));
+      }
+      if (!h_split && M > 2) {
+        // H_s is the same in both passes: its digit planes serve every product
+        if (split_a(Hs, planesH, expsH) != DMP_OK) return DMP_ERR_CUDA;
+        h_split = true;
+      }
+      double* prev = Ta;
+      double* cur = Tb;
+      for (int k = 1; k <= M - 2; ++k) {
+        const int prc = product(Hs, planesH, expsH, cur);
+        if (prc != DMP_OK) return prc;
+        DMP_CUDA(launch_foe_step(Y, prev, acc ? P : nullptr, ldp, coeffs + k + 1, n, st));
+        if (!acc) DMP_CUDA(launch_foe_trace(prev, n, n, traces + k + 1, st));
+        std::swap(prev, cur);
+      }
+      return DMP_OK;
+    };
+    if (canonical) {
+      rc = pass(false);
+      if (rc != DMP_OK) return rc;
+      DMP_CUDA(launch_foe_coefficients(sc, fp.kT, 0.0, static_cast<double>(fp.n_occ), traces, M, w, gx, coeffs, st));
+    } else {
+      DMP_CUDA(launch_foe_coefficients(sc, fp.kT, fp.mu, 0.0, nullptr, M, w, gx, coeffs, st));
+    }
+    rc = pass(true);
     if (rc != DMP_OK) return rc;
-    DMP_CUDA(launch_foe_coefficients(sc, fp.kT, 0.0, static_cast<double>(fp.n_occ), traces, M, w, gx, coeffs, st));
   } else {
-    DMP_CUDA(launch_foe_coefficients(sc, fp.kT, fp.mu, 0.0, nullptr, M, w, gx, coeffs, st));
+    // ---- Paterson-Stockmeyer scheme: baby steps T_1 .. T_nb in slots (T_1 = H_s)
+    const int q = ps_q(M);
+    const int r = (M + q - 1) / q;
+    const int nb = r > 1 ? q : q - 1;
+    double* Tps = dbl(L.Tps);
+    auto slot = [&](int t) { return Tps + static_cast<size_t>(t - 1) * n * n; };
+    int32_t* expsY = oz ? reinterpret_cast<int32_t*>(at(ws, L.expsY)) : nullptr;
+    void* planesY = oz ? at(ws, L.planesY) : nullptr;
+    double* ip = dbl(L.ip);
+    double* dots = dbl(L.dots);
+    double* fold = dbl(L.fold);
+    double* psw = dbl(L.psw);
+    DMP_CUDA(launch_foe_init(H, ldh, n, sc, nullptr, slot(1), nullptr, nullptr, P, ldp, st));
+    if (nb >= 2 && split_a(slot(1), planesH, expsH) != DMP_OK) return DMP_ERR_CUDA;
+    for (int j = 1; j < nb; ++j) {
+      rc = product(slot(1), planesH, expsH, slot(j));
+      if (rc != DMP_OK) return rc;
+      DMP_CUDA(launch_foe_next(Y, j == 1 ? nullptr : slot(j - 1), slot(j + 1), n, st));
+    }
+    const double* yq = r > 1 ? slot(q) : nullptr;
+    if (r > 1 && split_a(yq, planesY, expsY) != DMP_OK) return DMP_ERR_CUDA;
+    if (canonical) {
+      // traces: T_1 .. T_{q-1} directly; T_{qm} = T_m(y) by the recurrence in y
+      // (T_q for m = 1), with <T_{qm}, T_j> for the rest
+      for (int k = 1; k < q && k < M; ++k) DMP_CUDA(launch_foe_trace(slot(k), n, n, traces + k, st));
+      const double* g_prev = nullptr;  // T_0 = I
+      const double* g_cur = yq;
+      for (int m = 1; q * m < M; ++m) {
+        if (m >= 2) {
+          rc = product(yq, planesY, expsY, g_cur);
+          if (rc != DMP_OK) return rc;
+          double* out = m == 2 ? Ta : (m == 3 ? Tb : const_cast<double*>(g_prev));
+          DMP_CUDA(launch_foe_next(Y, g_prev, out, n, st));
+          g_prev = g_cur;
+          g_cur = out;
+        }
+        DMP_CUDA(launch_foe_trace(g_cur, n, n, traces + q * m, st));
+        DMP_CUDA(launch_foe_dots(g_cur, Tps, q, n, dots, ip + static_cast<size_t>(m) * q + 1, st));
+      }
+      DMP_CUDA(launch_foe_ps_traces(traces, ip, q, M, n, st));
+      DMP_CUDA(launch_foe_coefficients(sc, fp.kT, 0.0, static_cast<double>(fp.n_occ), traces, M, w, gx, coeffs, st));
+    } else {
+      DMP_CUDA(launch_foe_coefficients(sc, fp.kT, fp.mu, 0.0, nullptr, M, w, gx, coeffs, st));
+    }
+    DMP_CUDA(launch_foe_fold(coeffs, M, q, r, fold, psw, st));
+    // Clenshaw in y: b_m = B_m + 2 y b_{m+1} - b_{m+2}, P = B_0 + y b_1 - b_2
+    if (r == 1) {
+      DMP_CUDA(launch_foe_combine(Tps, q, psw, nullptr, 0.0, nullptr, P, ldp, n, st));
+    } else {
+      double* b1 = Ta;
+      double* b2 = nullptr;  // zero
+      DMP_CUDA(launch_foe_combine(Tps, q, psw + static_cast<size_t>(r - 1) * q, nullptr, 0.0, nullptr, b1, n, n, st));
+      for (int m = r - 2; m >= 1; --m) {
+        rc = product(yq, planesY, expsY, b1);
+        if (rc != DMP_OK) return rc;
+        double* out = b2 ? b2 : Tb;
+        DMP_CUDA(launch_foe_combine(Tps, q, psw + static_cast<size_t>(m) * q, Y, 2.0, b2, out, n, n, st));
+        b2 = b1;
+        b1 = out;
+      }
+      rc = product(yq, planesY, expsY, b1);
+      if (rc != DMP_OK) return rc;
+      DMP_CUDA(launch_foe_combine(Tps, q, psw, Y, 1.0, b2, P, ldp, n, st));
+    }
   }
-  rc = pass(true);
-  if (rc != DMP_OK) return rc;
   DMP_CUDA(launch_energy(P, ldp, H, ldh, n, partials, state, st));
   DMP_CUDA(launch_foe_trace(P, ldp, n, &sc->trace, st));
 

@@ -184,6 +184,23 @@ cudaError_t launch_foe_step(const double* Y, double* Tprev, double* P, int64_t l
                             cudaStream_t st);
 // *out = tr A (fixed order).
 cudaError_t launch_foe_trace(const double* A, int64_t lda, int64_t n, double* out, cudaStream_t st);
+// Paterson-Stockmeyer scheme. Baby steps T_1 .. T_q are kept in consecutive
+// n x n slots (T_t at T + (t - 1) n^2; T_0 = I implicit).
+constexpr int kFoeDotBlocks = 304;  // 2 x 152 SMs; fixed so sums are reproducible
+// Tout = 2 Y - Tprev (Tprev = I when null; Tout may be Tprev).
+cudaError_t launch_foe_next(const double* Y, const double* Tprev, double* Tout, int64_t n, cudaStream_t st);
+// out = ((w_0 I + sum_{t=1}^{nt-1} w_t T_t) + alpha Y) - Bm2 (Y, Bm2 nullable; out
+// of leading dimension ldo may be Bm2).
+cudaError_t launch_foe_combine(const double* T, int nt, const double* w, const double* Y, double alpha,
+                               const double* Bm2, double* out, int64_t ldo, int64_t n, cudaStream_t st);
+// out[t - 1] = <G, T_t>_F for t = 1 .. nt - 1; partials holds kFoeDotBlocks (nt - 1) doubles.
+cudaError_t launch_foe_dots(const double* G, const double* T, int nt, int64_t n, double* partials, double* out,
+                            cudaStream_t st);
+// tr T_k, k < M, from the baby- and giant-step traces already in `traces` and the
+// Frobenius products ip[m q + j] = <T_{qm}, T_j>.
+cudaError_t launch_foe_ps_traces(double* traces, const double* ip, int q, int M, int64_t n, cudaStream_t st);
+// Block weights w[r][q] from the M coefficients (a: scratch of r q doubles).
+cudaError_t launch_foe_fold(const double* coeffs, int M, int q, int r, double* a, double* w, cudaStream_t st);
 
 }  // namespace dmp
 

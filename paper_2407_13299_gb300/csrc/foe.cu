@@ -134,9 +134,10 @@ __global__ void foe_coeff_kernel(const double* __restrict__ gx, int M, double* _
   coeffs[k] = (2.0 / static_cast<double>(N)) * acc;
 }
 
-// H_s = (H - a I) / b (upper triangle of H read, mirrored), T_0 = I, T_1 = H_s,
-// and, with coefficients, P = (c_0 / 2) I + c_1 H_s. Matrices of leading
-// dimension n except H (ldh) and P (ldp).
+// H_s = (H - a I) / b (upper triangle of H read, mirrored), T_0 = I, T_1 = H_s
+// (each when its pointer is non-null), and, with coefficients,
+// P = (c_0 / 2) I + c_1 H_s. Matrices of leading dimension n except H (ldh)
+// and P (ldp).
 __global__ void foe_init_kernel(const double* __restrict__ H, int64_t ldh, int64_t n, const FoeScalars* sc,
                                 const double* __restrict__ coeffs, double* __restrict__ Hs, double* __restrict__ T0,
                                 double* __restrict__ T1, double* __restrict__ P, int64_t ldp) {
@@ -150,8 +151,8 @@ __global__ void foe_init_kernel(const double* __restrict__ H, int64_t ldh, int64
     const double d = i == j ? 1.0 : 0.0;
     const double hs = (h - (i == j ? a : 0.0)) / b;
     Hs[i * n + j] = hs;
-    T0[i * n + j] = d;
-    T1[i * n + j] = hs;
+    if (T0) T0[i * n + j] = d;
+    if (T1) T1[i * n + j] = hs;
     if (coeffs) P[i * ldp + j] = c0h * d + c1 * hs;
   }
 }
@@ -178,6 +179,96 @@ foe_trace_kernel(const double* __restrict__ A, int64_t lda, int64_t n, double* _
   for (int64_t i = threadIdx.x; i < n; i += kReduceThreads) part += A[i * lda + i];
   const double total = block_sum(part, red);
   if (threadIdx.x == 0) *out = total;
+}
+
+// ---- Paterson-Stockmeyer evaluation (Liang et al., J. Chem. Phys. 119, 4117):
+// baby steps T_1 .. T_q kept in q slots of n x n (T_0 = I implicit), y = T_q.
+
+// Tout = 2 Y - Tprev, Tprev = I when null. Tout may be Tprev (in place).
+__global__ void foe_next_kernel(const double* __restrict__ Y, const double* Tprev, double* Tout, int64_t n) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
+    const double prev = Tprev ? Tprev[i * n + j] : (i == j ? 1.0 : 0.0);
+    Tout[i * n + j] = 2.0 * Y[i * n + j] - prev;
+  }
+}
+
+// out = ((w_0 I + w_1 T_1 + ... + w_{nt-1} T_{nt-1}) + alpha Y) - Bm2, the Y and
+// Bm2 terms only when their pointers are non-null. T_t lives at T + (t - 1) tstride.
+// out (leading dimension ldo) may be Bm2 (in place).
+__global__ void foe_combine_kernel(const double* __restrict__ T, int64_t tstride, int nt, const double* __restrict__ w,
+                                   const double* __restrict__ Y, double alpha, const double* Bm2, double* out,
+                                   int64_t ldo, int64_t n) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int64_t i = blockIdx.y; i < n; i += gridDim.y) {
+    double v = i == j ? w[0] : 0.0;
+    for (int t = 1; t < nt; ++t) v += w[t] * T[(t - 1) * tstride + i * n + j];
+    if (Y) v += alpha * Y[i * n + j];
+    if (Bm2) v -= Bm2[i * n + j];
+    out[i * ldo + j] = v;
+  }
+}
+
+// Frobenius products <G, T_t> for t = 1 .. nt - 1 (blockIdx.y = t - 1): per-block
+// partial sums over the rows blockIdx.x, blockIdx.x + gridDim.x, ...
+__global__ void __launch_bounds__(256)
+foe_dots_kernel(const double* __restrict__ G, const double* __restrict__ T, int64_t tstride, int64_t n,
+                double* __restrict__ partials) {
+  __shared__ double red[8];
+  const double* Tt = T + static_cast<int64_t>(blockIdx.y) * tstride;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) acc += G[i * n + j] * Tt[i * n + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    partials[static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// out[t] = sum of the partial sums of product t, in a fixed order (one CTA per t).
+__global__ void __launch_bounds__(kReduceThreads)
+foe_dots_final_kernel(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+  __shared__ double red[kReduceThreads];
+  double part = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += kReduceThreads)
+    part += partials[static_cast<int64_t>(blockIdx.x) * nblocks + b];
+  const double total = block_sum(part, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = total;
+}
+
+// tr T_k for every k < M from tr T_0 = n, the baby-step traces (k < q), the
+// giant-step traces tr T_{qm} and the Frobenius products ip[m q + j] =
+// <T_{qm}, T_j>: tr T_{qm+j} = 2 ip[m q + j] - tr T_{qm-j}. One thread.
+__global__ void foe_ps_traces_kernel(double* traces, const double* __restrict__ ip, int q, int M, int64_t n) {
+  traces[0] = static_cast<double>(n);
+  for (int m = 1; q * m < M; ++m)
+    for (int j = 1; j < q && q * m + j < M; ++j)
+      traces[q * m + j] = 2.0 * ip[m * q + j] - traces[q * m - j];
+}
+
+// The weights w[m][j] of B_m = sum_{j<q} w[m][j] T_j, P = sum_{m<r} T_m(y) B_m:
+// a_k = c_k (a_0 = c_0 / 2, zero past M), folded from the top block down
+// (T_{qm+j} = 2 T_m(y) T_j - T_{qm-j}). One thread; a holds r q doubles.
+__global__ void foe_fold_kernel(const double* __restrict__ coeffs, int M, int q, int r, double* __restrict__ a,
+                                double* __restrict__ w) {
+  for (int k = 0; k < r * q; ++k) a[k] = k < M ? coeffs[k] : 0.0;
+  a[0] = 0.5 * coeffs[0];
+  for (int m = r - 1; m > 0; --m) {
+    w[m * q] = a[q * m];
+    for (int j = 1; j < q; ++j) {
+      const double d = a[q * m + j];
+      w[m * q + j] = 2.0 * d;
+      a[q * m - j] -= d;
+    }
+  }
+  for (int j = 0; j < q; ++j) w[j] = a[j];
 }
 
 dim3 elem_grid(int64_t n) {
@@ -222,6 +313,46 @@ cudaError_t launch_foe_step(const double* Y, double* Tprev, double* P, int64_t l
                             cudaStream_t st) {
   ProfScope prof(DMP_PROF_OTHER, st);
   foe_step_kernel<<<elem_grid(n), kElemThreads, 0, st>>>(Y, Tprev, P, ldp, coeff, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_foe_next(const double* Y, const double* Tprev, double* Tout, int64_t n, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_OTHER, st);
+  foe_next_kernel<<<elem_grid(n), kElemThreads, 0, st>>>(Y, Tprev, Tout, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_foe_combine(const double* T, int nt, const double* w, const double* Y, double alpha,
+                               const double* Bm2, double* out, int64_t ldo, int64_t n, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_OTHER, st);
+  foe_combine_kernel<<<elem_grid(n), kElemThreads, 0, st>>>(T, n * n, nt, w, Y, alpha, Bm2, out, ldo, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_foe_dots(const double* G, const double* T, int nt, int64_t n, double* partials, double* out,
+                            cudaStream_t st) {
+  if (nt < 2) return cudaSuccess;
+  ProfScope prof(DMP_PROF_MEASURE, st);
+  const dim3 grid(kFoeDotBlocks, static_cast<unsigned>(nt - 1));
+  foe_dots_kernel<<<grid, 256, 0, st>>>(G, T, n * n, n, partials);
+  foe_dots_final_kernel<<<static_cast<unsigned>(nt - 1), kReduceThreads, 0, st>>>(partials, kFoeDotBlocks, out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_foe_ps_traces(double* traces, const double* ip, int q, int M, int64_t n, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_MEASURE, st);
+  foe_ps_traces_kernel<<<1, 1, 0, st>>>(traces, ip, q, M, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_foe_fold(const double* coeffs, int M, int q, int r, double* a, double* w, cudaStream_t st) {
+  ProfScope prof(DMP_PROF_INIT, st);
+  foe_fold_kernel<<<1, 1, 0, st>>>(coeffs, M, q, r, a, w);
   count_launch();
   return cudaGetLastError();
 }

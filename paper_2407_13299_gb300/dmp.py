@@ -53,7 +53,7 @@ class Info(ctypes.Structure):
 
 class FoeParams(ctypes.Structure):
     _fields_ = [("kT", ctypes.c_double), ("mu", ctypes.c_double), ("n_occ", ctypes.c_int64),
-                ("n_terms", ctypes.c_int32), ("reserved", ctypes.c_int32), ("e_min", ctypes.c_double),
+                ("n_terms", ctypes.c_int32), ("scheme", ctypes.c_int32), ("e_min", ctypes.c_double),
                 ("e_max", ctypes.c_double)]
 
 
@@ -68,6 +68,7 @@ class FoeInfo(ctypes.Structure):
 
 
 FOE_MAX_TERMS = 16384
+FOE_SCHEMES = {"recurrence": 0, "ps": 1}
 
 _lib = None
 
@@ -98,7 +99,7 @@ SIGNATURES = {
     "dmp_backward_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
     "dm_purify_backward": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(Opts), _vp, _sz, _vp, _vp, _vp,
                                           _sz, _vp]),
-    "dm_foe_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
+    "dm_foe_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(FoeParams), ctypes.POINTER(Opts), _szp]),
     "dm_foe": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(FoeParams), ctypes.POINTER(Opts), _vp, _i64,
                               ctypes.POINTER(FoeInfo), _vp, _sz, _vp]),
     "dmp_profile_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -263,31 +264,39 @@ def purify_host(H_host: torch.Tensor, n_occ: int, out: torch.Tensor | None = Non
     return out, info
 
 
-def foe_workspace_bytes(n: int, opts: Opts) -> int:
+def foe_params(kT: float, n_terms: int, mu: float | None = None, n_occ: int | None = None, bounds=None,
+               scheme="recurrence") -> FoeParams:
+    lo, hi = (0.0, 0.0) if bounds is None else (float(bounds[0]), float(bounds[1]))
+    return FoeParams(float(kT), 0.0 if mu is None else float(mu), 0 if n_occ is None else int(n_occ),
+                     int(n_terms), FOE_SCHEMES[scheme], lo, hi)
+
+
+def foe_workspace_bytes(n: int, params: FoeParams, opts: Opts) -> int:
     b = ctypes.c_size_t(0)
-    _check(lib().dm_foe_workspace_size(n, ctypes.byref(opts), ctypes.byref(b)), "dm_foe_workspace_size")
+    _check(lib().dm_foe_workspace_size(n, ctypes.byref(params), ctypes.byref(opts), ctypes.byref(b)),
+           "dm_foe_workspace_size")
     return b.value
 
 
 def foe(H: torch.Tensor, kT: float, n_terms: int, mu: float | None = None, n_occ: int | None = None,
-        bounds=None, mode="int8", slices=7, executor="auto", P=None, ws=None, stream=None):
+        bounds=None, mode="int8", slices=7, executor="auto", scheme="recurrence", P=None, ws=None, stream=None):
     """dm_foe: the Chebyshev Fermi-operator expansion P = f(H) at electronic
     temperature kT on a float64 CUDA tensor H. Give mu (grand-canonical) or
     n_occ (mu solved so that tr(P) = n_occ). `bounds` = (e_min, e_max) is a
-    spectral enclosure to scale H by (default: the Gershgorin bounds). Returns
+    spectral enclosure to scale H by (default: the Gershgorin bounds).
+    `scheme`: "recurrence" (M - 2 products per pass) or "ps" (the
+    Paterson-Stockmeyer evaluation, about 2 sqrt(M) products). Returns
     (P, info dict)."""
     _require_cuda(H)
     if (mu is None) == (n_occ is None):
         raise ValueError("give exactly one of mu and n_occ")
     n = H.shape[0]
     opts = make_opts(mode, slices, executor)
-    lo, hi = (0.0, 0.0) if bounds is None else (float(bounds[0]), float(bounds[1]))
-    params = FoeParams(float(kT), 0.0 if mu is None else float(mu), 0 if n_occ is None else int(n_occ),
-                       int(n_terms), 0, lo, hi)
+    params = foe_params(kT, n_terms, mu, n_occ, bounds, scheme)
     if P is None:
         P = torch.empty_like(H)
     if ws is None:
-        ws = workspace(foe_workspace_bytes(n, opts), H.device)
+        ws = workspace(foe_workspace_bytes(n, params, opts), H.device)
     info = FoeInfo()
     code = lib().dm_foe(H.data_ptr(), n, H.stride(0), ctypes.byref(params), ctypes.byref(opts), P.data_ptr(),
                         P.stride(0), ctypes.byref(info), ws.data_ptr(), ws.numel(), _stream_ptr(stream))

@@ -140,20 +140,30 @@ def test_foe_validation_needs_no_gpu(built):
 
     L = dmp.lib()
     b = ct.c_size_t(0)
+    fp = dmp.foe_params(0.05, 64, mu=0.0)
     for kw, want in ((dict(mode="int8", slices=5), dmp.OK), (dict(mode="fp64"), dmp.OK),
                      (dict(mode="e4m3", slices=8, executor="tc"), dmp.OK),
                      (dict(mode="int8", slices=5, refine=7), dmp.ERR_UNSUPPORTED),
                      (dict(mode="int8", slices=5, method="sp2"), dmp.ERR_UNSUPPORTED),
                      (dict(mode="int8", slices=5, fp32_storage=True), dmp.ERR_UNSUPPORTED),
                      (dict(mode="int8", slices=5, late_slices=4, late_idem=1e-3), dmp.ERR_UNSUPPORTED)):
-        assert L.dm_foe_workspace_size(512, ct.byref(dmp.make_opts(**kw)), ct.byref(b)) == want, kw
+        assert L.dm_foe_workspace_size(512, ct.byref(fp), ct.byref(dmp.make_opts(**kw)), ct.byref(b)) == want, kw
     o = dmp.make_opts("int8", 5)
-    assert L.dm_foe_workspace_size(1024, ct.byref(o), ct.byref(b)) == dmp.OK
+    assert L.dm_foe_workspace_size(1024, ct.byref(fp), ct.byref(o), ct.byref(b)) == dmp.OK
     assert b.value >= 4 * 1024 * 1024 * 8  # H_s, two recurrence terms and the product
     need = b.value
+    # the Paterson-Stockmeyer scheme keeps q = ceil(sqrt(M)) baby steps: 8 for M = 64
+    ps = dmp.foe_params(0.05, 64, mu=0.0, scheme="ps")
+    assert L.dm_foe_workspace_size(1024, ct.byref(ps), ct.byref(o), ct.byref(b)) == dmp.OK
+    assert b.value >= need + 7 * 1024 * 1024 * 8 - 1024 * 1024 * 8
+    bad = dmp.foe_params(0.05, 64, mu=0.0)
+    bad.scheme = 2
+    assert L.dm_foe_workspace_size(1024, ct.byref(bad), ct.byref(o), ct.byref(b)) == dmp.ERR_INVALID_ARG
+    bad = dmp.foe_params(0.05, dmp.FOE_MAX_TERMS + 1, mu=0.0)
+    assert L.dm_foe_workspace_size(1024, ct.byref(bad), ct.byref(o), ct.byref(b)) == dmp.ERR_INVALID_ARG
 
     def call(n=1024, ws_bytes=None, **kw):
-        p = dict(kT=0.05, mu=0.0, n_occ=0, n_terms=64, reserved=0, e_min=0.0, e_max=0.0)
+        p = dict(kT=0.05, mu=0.0, n_occ=0, n_terms=64, scheme=0, e_min=0.0, e_max=0.0)
         p.update(kw)
         params = dmp.FoeParams(**p)
         info = dmp.FoeInfo()
@@ -170,9 +180,10 @@ def test_foe_validation_needs_no_gpu(built):
     assert call(n_occ=1024) == dmp.ERR_INVALID_ARG
     assert call(n_occ=-1) == dmp.ERR_INVALID_ARG
     assert call(e_min=float("nan")) == dmp.ERR_INVALID_ARG
-    assert call(reserved=1) == dmp.ERR_INVALID_ARG
+    assert call(scheme=2) == dmp.ERR_INVALID_ARG
     assert call(n=1) == dmp.ERR_INVALID_ARG
     assert call(ws_bytes=need - 1) == dmp.ERR_WORKSPACE
+    assert call(scheme=1) == dmp.ERR_WORKSPACE  # the scheme needs its baby-step slots
     assert call(n=200000) == dmp.ERR_UNSUPPORTED  # level sums of k = n would overflow int32
 
 

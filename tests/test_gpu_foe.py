@@ -167,3 +167,85 @@ def test_full_size_sampled_rows(dmp):
     # the trace adds n such errors at most
     assert abs(info["trace"] - float(fe.sum())) <= 1e-5
     assert bool((P[rows][:, rows] == P[rows][:, rows].T).all())
+
+
+# ---- the Paterson-Stockmeyer scheme (scheme="ps")
+# Baby and giant steps carry no coefficients, so they are the same on both
+# sides as in the recurrence. The Clenshaw terms B_m are combinations whose
+# weights and roundings differ in the last bit, and a product of such a term
+# can then truncate one digit differently. With one-ulp noise on every weight
+# and element, the oracle moved by at most 1.3 % of its own Ozaki error on
+# these cases; the bound below is a quarter of that error (plus 1e-12).
+
+
+def _ps_tol(ref, ref64):
+    return 1e-12 + 0.25 * float(np.max(np.abs(ref - ref64)))
+
+
+@pytest.mark.parametrize("mode,s", [("int8", 5), ("int8", 7), ("bf16", 5), ("e4m3", 8)])
+@pytest.mark.parametrize("n", [256, 333])
+def test_ps_modes_match_oracle(dmp, mode, s, n):
+    h = _metallic(n, seed=n + s)
+    ref64, _ = fo.foe(h.H, 0.1, 80, mu=0.0, bounds=BOUNDS)
+    ref, rinfo = fo.foe(h.H, 0.1, 80, mu=0.0, bounds=BOUNDS, product=_oz(mode, s), scheme="ps")
+    P, info = dmp.foe(_dev(h.H), 0.1, 80, mu=0.0, bounds=BOUNDS, mode=mode, slices=s, scheme="ps")
+    P = P.cpu().numpy()
+    assert info["status"] == dmp.OK and info["products"] == rinfo["products"] == 8 + 8
+    assert np.max(np.abs(P - ref)) <= _ps_tol(ref, ref64)
+    assert np.array_equal(P, P.T)
+
+
+@pytest.mark.parametrize("M", [2, 3, 5, 17, 80])
+def test_ps_fp64_matches_oracle_and_recurrence(dmp, M):
+    h = _metallic(333, seed=M)
+    ref, rinfo = fo.foe(h.H, 0.1, M, mu=0.1, bounds=BOUNDS, scheme="ps")
+    P, info = dmp.foe(_dev(h.H), 0.1, M, mu=0.1, bounds=BOUNDS, mode="fp64", scheme="ps")
+    Pr, _ = dmp.foe(_dev(h.H), 0.1, M, mu=0.1, bounds=BOUNDS, mode="fp64")
+    P, Pr = P.cpu().numpy(), Pr.cpu().numpy()
+    assert info["products"] == rinfo["products"]
+    assert np.max(np.abs(P - ref)) <= 1e-12
+    assert np.max(np.abs(P - Pr)) <= 1e-12
+    assert np.array_equal(P, P.T)
+
+
+@pytest.mark.parametrize("mode,s", [("fp64", 0), ("int8", 7), ("int8", 5)])
+def test_ps_canonical(dmp, mode, s):
+    """mu from the traces of the giant steps: 39 products at M = 200 against
+    the recurrence's 396."""
+    h = make_hamiltonian(300, 75, occ=(-2.0, -0.3), virt=(0.3, 2.0), seed=301)
+    prod = None if mode == "fp64" else _oz(mode, s)
+    ref, rinfo = fo.foe(h.H, 0.05, 200, n_occ=75, bounds=BOUNDS, product=prod, scheme="ps")
+    ref64, _ = fo.foe(h.H, 0.05, 200, n_occ=75, bounds=BOUNDS, scheme="ps")
+    P, info = dmp.foe(_dev(h.H), 0.05, 200, n_occ=75, bounds=BOUNDS, mode=mode, slices=max(s, 1), scheme="ps")
+    P = P.cpu().numpy()
+    assert info["status"] == dmp.OK and info["products"] == rinfo["products"] == 39
+    # P comes from the Clenshaw sum, the trace mu was solved on from the giant
+    # steps: the two agree to the products' error (about 1e-9 at s = 5)
+    assert abs(info["trace"] - 75) <= 1e-7
+    assert abs(info["mu"] - rinfo["mu"]) <= 1e-9
+    assert np.max(np.abs(P - ref)) <= 1e-11 + 0.25 * float(np.max(np.abs(ref - ref64)))
+
+
+def test_ps_multiple_of_identity(dmp):
+    H = 0.3 * np.eye(64)
+    ref, _ = fo.foe(H, 0.2, 60, mu=0.1, scheme="ps")
+    P, info = dmp.foe(_dev(H), 0.2, 60, mu=0.1, mode="int8", slices=5, scheme="ps")
+    assert info["status"] == dmp.OK
+    assert np.max(np.abs(P.cpu().numpy() - ref)) <= 1e-13
+
+
+def test_ps_full_size_sampled_rows(dmp):
+    """The benchmark's expansion (n = 8192, kT = 0.05, M = 200, mu from n_occ,
+    Ozaki-INT8 s = 6) by the Paterson-Stockmeyer scheme: sampled rows against
+    the exact f(H) at the returned mu, the trace against n_occ, 39 products."""
+    h = config_hamiltonian(2, device="cuda")
+    kT, M = 0.05, 200
+    P, info = dmp.foe(h.H, kT, M, n_occ=h.n_occ, bounds=(-1.5, 1.5), mode="int8", slices=6, scheme="ps")
+    assert info["status"] == dmp.OK and info["products"] == 39
+    fe = torch.from_numpy(fo.fermi(h.e, info["mu"], kT)).cuda()
+    rows = torch.from_numpy(np.random.default_rng(6).choice(h.n, 64, replace=False)).cuda()
+    exact = (h.Q[rows] * fe[None, :]) @ h.Q.T
+    err = float((P[rows] - exact).abs().max())
+    assert err <= 1e-7, err
+    assert abs(info["trace"] - h.n_occ) <= 1e-6
+    assert abs(info["trace"] - float(fe.sum())) <= 1e-5
