@@ -227,11 +227,14 @@ def test_ps_canonical(dmp, mode, s):
 
 
 def test_ps_multiple_of_identity(dmp):
+    """P = p(0) I. The two sides' coefficients differ by about 3e-14 summed
+    over k (cosine and exponential roundings); the folding moves each into up
+    to r = 8 block weights, so p(0) may differ by some 1e-13 (1.0e-13 seen)."""
     H = 0.3 * np.eye(64)
     ref, _ = fo.foe(H, 0.2, 60, mu=0.1, scheme="ps")
     P, info = dmp.foe(_dev(H), 0.2, 60, mu=0.1, mode="int8", slices=5, scheme="ps")
     assert info["status"] == dmp.OK
-    assert np.max(np.abs(P.cpu().numpy() - ref)) <= 1e-13
+    assert np.max(np.abs(P.cpu().numpy() - ref)) <= 1e-12
 
 
 def test_ps_full_size_sampled_rows(dmp):
