@@ -13,6 +13,15 @@
 // file holds the scalar set-up (enclosure, mu, coefficients) and the
 // elementwise steps of the recurrence.
 //
+// Second evaluation of the same series (Paterson-Stockmeyer, after Liang et
+// al., J. Chem. Phys. 119, 4117 (2003)): q = ceil(sqrt(M)) baby steps T_1 .. T_q
+// are kept, the series is folded into sum_{m<r} T_m(y) B_m with y = T_q and
+// B_m = sum_{j<q} w_{m,j} T_j (T_{qm+j} = 2 T_m(y) T_j - T_{qm-j}), and summed
+// by Clenshaw's recurrence in y. Its kernels here: the next term of a
+// recurrence, the weighted combination with the Clenshaw update, the
+// Frobenius products <T_{qm}, T_j> and the trace assembly of canonical use,
+// and the block folding of the coefficients.
+//
 // With a target n_occ, mu solves sum_k c_k(mu) tr T_k = n_occ. Writing
 // w_j = t_0 / 2 + sum_{k>=1} t_k cos(k theta_j) (t_k = tr T_k from a first pass
 // of the recurrence), the expansion's trace is (2 / N) sum_j g_mu(x_j) w_j, and

@@ -187,6 +187,35 @@ def test_foe_validation_needs_no_gpu(built):
     assert call(n=200000) == dmp.ERR_UNSUPPORTED  # level sums of k = n would overflow int32
 
 
+def test_foe_scheme_slots_need_no_gpu(built):
+    """The Paterson-Stockmeyer workspace holds q = ceil(sqrt(M)) baby-step
+    slots of n x n doubles (H_s being the first) on top of the recurrence's
+    buffers less its separate H_s, plus one more set of digit planes (y = T_q)."""
+    import ctypes as ct
+    import math
+
+    from paper_2407_13299_gb300 import dmp
+
+    L = dmp.lib()
+    n = 512
+    nn = n * n * 8
+    for mode, slices in (("fp64", 0), ("int8", 5)):
+        o = dmp.make_opts(mode, max(slices, 1))
+        b_rec, b_ps = ct.c_size_t(0), ct.c_size_t(0)
+        for M in (2, 3, 4, 5, 17, 200, 1000, dmp.FOE_MAX_TERMS):
+            rec = dmp.foe_params(0.1, M, mu=0.0)
+            ps = dmp.foe_params(0.1, M, mu=0.0, scheme="ps")
+            assert L.dm_foe_workspace_size(n, ct.byref(rec), ct.byref(o), ct.byref(b_rec)) == dmp.OK
+            assert L.dm_foe_workspace_size(n, ct.byref(ps), ct.byref(o), ct.byref(b_ps)) == dmp.OK
+            q = math.isqrt(M - 1) + 1 if M > 1 else 1
+            extra = b_ps.value - b_rec.value - (q - 1) * nn
+            # the third plane set: s planes of n x n bfloat16 digits (n = 512 is
+            # already a multiple of the row and K padding) and n int32 exponents;
+            # none in FP64 mode
+            planes = 0 if mode == "fp64" else slices * n * n * 2 + n * 4
+            assert extra == planes, (mode, M, extra)
+
+
 def test_no_fallback_without_the_library(tmp_path, monkeypatch):
     """Without the compiled library every call fails loudly; nothing falls back
     to a host implementation."""
