@@ -59,7 +59,7 @@ mirrors it (the products H_s T_k are symmetric in exact arithmetic).
 
 Parity: pinned. The tests check the coefficients of polynomials (exact
 Chebyshev coefficients), the truncated series against the Fermi function on a
-grid, the matrix recurrence against a dense eigensolver with the same
+grid, the closed-form Fermi matrix of a 2 x 2 H, the matrix recurrence against a dense eigensolver with the same
 polynomial (numpy's Chebyshev evaluation on the eigenvalues) and with the
 Fermi function itself, the closed form for a multiple of the identity, the
 particle-hole identity P(2 mu I - H) = I - P(H), permutation equivariance,

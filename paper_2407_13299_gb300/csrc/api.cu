@@ -1057,19 +1057,20 @@ int dm_foe(const double* H, int64_t n, int64_t ldh, const dmp_foe_params* params
       if (rc != DMP_OK) return rc;
       DMP_CUDA(launch_foe_next(Y, j == 1 ? nullptr : slot(j - 1), slot(j + 1), n, st));
     }
-    const double* yq = r > 1 ? slot(q) : nullptr;
+    double* yq = r > 1 ? slot(q) : nullptr;
     if (r > 1 && split_a(yq, planesY, expsY) != DMP_OK) return DMP_ERR_CUDA;
     if (canonical) {
       // traces: T_1 .. T_{q-1} directly; T_{qm} = T_m(y) by the recurrence in y
       // (T_q for m = 1), with <T_{qm}, T_j> for the rest
       for (int k = 1; k < q && k < M; ++k) DMP_CUDA(launch_foe_trace(slot(k), n, n, traces + k, st));
-      const double* g_prev = nullptr;  // T_0 = I
-      const double* g_cur = yq;
+      double* g_prev = nullptr;  // T_0 = I
+      double* g_cur = yq;
       for (int m = 1; q * m < M; ++m) {
         if (m >= 2) {
           rc = product(yq, planesY, expsY, g_cur);
           if (rc != DMP_OK) return rc;
-          double* out = m == 2 ? Ta : (m == 3 ? Tb : const_cast<double*>(g_prev));
+          // G_2 and G_3 take the two free buffers; later terms overwrite G_{m-2} in place
+          double* out = m == 2 ? Ta : (m == 3 ? Tb : g_prev);
           DMP_CUDA(launch_foe_next(Y, g_prev, out, n, st));
           g_prev = g_cur;
           g_cur = out;

@@ -125,6 +125,23 @@ def test_multiple_of_identity():
     assert abs(p0 - fo.fermi(np.array([hval]), mu, kT)[0]) < 1e-12
 
 
+def test_two_by_two_closed_form():
+    """H = [[d, t], [t, d]] has eigenvalues d +- t on (1, +-1)/sqrt(2), so
+    f(H) = (f(d+t) + f(d-t))/2 I + (f(d+t) - f(d-t))/2 [[0, 1], [1, 0]];
+    at mu = d this is I/2 - tanh(t / 2kT)/2 [[0, 1], [1, 0]]."""
+    d, t, kT = 0.3, 0.7, 0.15
+    H = np.array([[d, t], [t, d]])
+    X = np.array([[0.0, 1.0], [1.0, 0.0]])
+    for mu in (d, -0.2, 1.1):
+        fp, fm = fo.fermi(np.array([d + t, d - t]), mu, kT)
+        closed = 0.5 * (fp + fm) * np.eye(2) + 0.5 * (fp - fm) * X
+        for scheme in ("recurrence", "ps"):
+            P, _ = fo.foe(H, kT, 120, mu=mu, scheme=scheme)  # Gershgorin bounds: exactly d -+ t
+            assert np.max(np.abs(P - closed)) < 1e-12, (mu, scheme)
+    P, _ = fo.foe(H, kT, 120, mu=d)
+    assert np.max(np.abs(P - (0.5 * np.eye(2) - 0.5 * np.tanh(t / (2 * kT)) * X))) < 1e-12
+
+
 def test_particle_hole_identity():
     """f(2 mu - e) = 1 - f(e): P(2 mu I - H) = I - P(H), with the Gershgorin
     enclosure mirrored as well."""
