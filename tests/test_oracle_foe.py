@@ -237,6 +237,16 @@ def test_ps_fold_reproduces_the_series_on_scalars():
         Tj = np.array([cheb.chebval(x, np.eye(q)[j]) for j in range(q)])
         val = sum(cheb.chebval(y, np.eye(r)[m]) * (w[m] @ Tj) for m in range(r))
         assert np.max(np.abs(val - cheb.chebval(x, _series(c)))) < 1e-12 * np.sum(np.abs(c))
+    # planted: the fold without the -c carried into block m - 1 misses the series
+    M, c = 50, rng.standard_normal(50)
+    q, r = fo.ps_blocks(M)
+    a = np.concatenate([[0.5 * c[0]], c[1:], np.zeros(r * q - M)])
+    w_bad = np.array([[a[q * m] if j == 0 or m == 0 else 2.0 * a[q * m + j] for j in range(q)] for m in range(r)])
+    w_bad[0] = a[:q]
+    y = cheb.chebval(x, np.eye(q + 1)[q])
+    Tj = np.array([cheb.chebval(x, np.eye(q)[j]) for j in range(q)])
+    bad = sum(cheb.chebval(y, np.eye(r)[m]) * (w_bad[m] @ Tj) for m in range(r))
+    assert np.max(np.abs(bad - cheb.chebval(x, _series(c)))) > 1e-3
 
 
 @pytest.mark.parametrize("M", [2, 3, 5, 17, 60, 200])
