@@ -102,6 +102,17 @@ def workload_name(w):
             f"spectrum {list(w['occ'])} u {list(w['virt'])} (gap 0.02), seed {w['seed']}")
 
 
+def fermi_occupations(e, mu, kT):
+    """Fermi-Dirac occupations 1 / (1 + exp((e - mu) / kT)) of the known
+    eigenvalues, evaluated without overflow (the exact f(H) the finite-temperature
+    expansion is checked against)."""
+    import numpy as np
+
+    z = (np.asarray(e, dtype=np.float64) - mu) / kT
+    ez = np.exp(-np.abs(z))
+    return np.where(z > 0, ez / (1.0 + ez), 1.0 / (1.0 + ez))
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -636,9 +647,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             dmp.profile_enable(False)
             f_prod_ms, f_prod_n = dmp.profile_read(dmp.PROF_PRODUCT)
-            z = (h.e - fi["mu"]) / f_kT
-            ez = np.exp(-np.abs(z))
-            occ_exact = np.where(z > 0, ez / (1.0 + ez), 1.0 / (1.0 + ez))
+            occ_exact = fermi_occupations(h.e, fi["mu"], f_kT)
             E_f = float(np.sum(occ_exact * h.e))
             exact_rows = (Q_d[rows] * torch.as_tensor(occ_exact, device=dev)[None, :]) @ Q_d.T
             f_flops = fi["products"] * pairs(f_slices) * unit_flops

@@ -30,3 +30,18 @@ def test_stale_summary_gives_no_traffic(tmp_path, monkeypatch):
     (root / "paper_2407_13299_gb300" / "csrc" / "gemm_tc.cu").write_text("// another source\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.kernel_traffic("gemm_tc.cu", "ozaki_tc_kernel_n8192.md", {5: 1}) is None
+
+
+def test_fermi_occupations_match_the_oracle():
+    """The benchmark's exact occupations (the reference its finite-temperature
+    errors are measured against) equal the oracle's Fermi function, without
+    overflow far from mu."""
+    import numpy as np
+
+    from oracle import foe as fo
+
+    e = np.concatenate([np.linspace(-1.5, 1.5, 1001), [-1e4, 1e4]])
+    for mu, kT in ((0.0, 0.05), (-0.0346, 0.05), (0.3, 0.001)):
+        got = bench.fermi_occupations(e, mu, kT)
+        assert np.all(np.isfinite(got)) and got[-2] == 1.0 and got[-1] == 0.0
+        assert np.max(np.abs(got - fo.fermi(e, mu, kT))) <= 1e-16
