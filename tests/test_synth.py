@@ -41,3 +41,36 @@ def test_batch_sizes():
 def test_symmetric_gaussian():
     W = symmetric_gaussian(20, 1)
     assert np.array_equal(W, W.T)
+
+
+def test_inputs_match_the_manifest():
+    """The seeded draws behind every benchmark workload hash to the digests in
+    tests/golden/inputs_manifest.json (written by make_inputs_manifest.py),
+    and those draws are the ones make_hamiltonian uses."""
+    import importlib.util
+    import json
+    import os
+
+    import numpy as np
+    import pytest
+
+    from synth import config_hamiltonian
+
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_inputs_manifest", os.path.join(here, "make_inputs_manifest.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    with open(mk.MANIFEST) as f:
+        stored = json.load(f)
+    now = mk.manifest()
+    if now["configs"] != stored["configs"] and now["numpy"] != stored["numpy"]:
+        pytest.skip(f"numpy {now['numpy']} draws differ from the manifest's numpy {stored['numpy']}")
+    assert now["configs"] == stored["configs"]
+    # the manifest's draw order is make_hamiltonian's
+    e, G = mk.draws(0)
+    h = config_hamiltonian(0)
+    assert np.array_equal(h.e, e)
+    Qg, R = np.linalg.qr(G)
+    sgn = np.sign(np.diag(R))
+    sgn[sgn == 0] = 1.0
+    assert np.array_equal(h.Q, Qg * sgn[None, :])
