@@ -58,17 +58,18 @@ Symmetric products: `symmetric_output` forms a product's upper triangle and
 mirrors it (the products H_s T_k are symmetric in exact arithmetic).
 
 Parity: pinned. The tests check the coefficients of polynomials (exact
-Chebyshev coefficients), the truncated series against the Fermi function on a
-grid, the closed-form Fermi matrix of a 2 x 2 H, the matrix recurrence against
-a dense eigensolver with the same polynomial (numpy's Chebyshev evaluation on
-the eigenvalues) and with the Fermi function itself, the closed form for a
-multiple of the identity, the particle-hole identity P(2 mu I - H) = I - P(H),
-permutation equivariance, tr(P) = n_occ in canonical use, and the approach to
-the zero-temperature projector as kT falls. For the Paterson-Stockmeyer
-scheme: the folded weights reproduce the series on scalars (numpy's Chebyshev
-evaluation, every block layout), P agrees with the recurrence and the
-eigensolver to rounding, the traces of the giant steps equal the recurrence's,
-and the product counts.
+Chebyshev coefficients) and of the Fermi function (the exact Chebyshev
+integrals, by mpmath at 30 digits), the truncated series against the Fermi
+function on a grid, the closed-form Fermi matrix of a 2 x 2 H, the matrix
+recurrence against a dense eigensolver with the same polynomial (numpy's
+Chebyshev evaluation on the eigenvalues) and with the Fermi function itself,
+the closed form for a multiple of the identity, the particle-hole identity P(2
+mu I - H) = I - P(H), permutation equivariance, tr(P) = n_occ in canonical
+use, and the approach to the zero-temperature projector as kT falls. For the
+Paterson-Stockmeyer scheme: the folded weights reproduce the series on scalars
+(numpy's Chebyshev evaluation, every block layout), P agrees with the
+recurrence and the eigensolver to rounding, the traces of the giant steps
+equal the recurrence's, and the product counts.
 """
 
 from __future__ import annotations
