@@ -254,13 +254,10 @@ cudaError_t launch_ozaki_imma(const int8_t* A, const int8_t* B, const int32_t* e
                               int s, int beta, int sym, const EpiArgs& epi, const int* done,
                               cudaStream_t st) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_imma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // set before every launch: the attribute belongs to the kernel as loaded in
+  // the current context (a context created anew starts from the default)
+  cudaError_t e = cudaFuncSetAttribute(ozaki_imma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
   Params p;
   p.A = A;
   p.B = B;

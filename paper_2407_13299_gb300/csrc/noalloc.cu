@@ -7,8 +7,6 @@
 
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "dmp_internal.cuh"
 
 namespace dmp {
@@ -16,27 +14,21 @@ namespace dmp {
 namespace {
 
 constexpr size_t kNoAllocBytes = size_t(128) << 20;  // 128 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of the array on the current device. The name is only a host
-// stand-in for the device symbol, so its address is looked up once per device
-// (with that device current) and cached.
+// Device address of the array in the current context. In host code the
+// array's name is only a stand-in for the device symbol, so the address is
+// looked up with cudaGetSymbolAddress -- on every call, not cached: a context
+// that is torn down and created again (cudaDeviceReset, or a caller's own
+// driver-API context on the same device) loads the library's device code at a
+// new address, and a pointer kept from the old context would point at memory
+// that no longer belongs to the array. The lookup is a host-side table query
+// of the runtime; it allocates nothing and enqueues no work.
 int noalloc_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return DMP_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return DMP_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return DMP_ERR_CUDA;
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return DMP_ERR_CUDA;
+  *out = p;
   return DMP_OK;
 }
 

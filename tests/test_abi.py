@@ -86,6 +86,26 @@ def test_workspace_sizes_are_host_side(built):
     assert dmp.tape_bytes(1024, dmp.make_opts("fp64", max_iter=100, checkpoint_every=8)) >= 13 * 1024 * 1024 * 8
 
 
+# Largest square size ozaki_gemm_noalloc accepts at s = 7, as include/dmp.h states
+# it: (mode, executor) -> size (a multiple of 32).
+NOALLOC_LIMITS_S7 = {("int8", "tc"): 1056, ("bf16", "tc"): 1056, ("e4m3", "tc"): 1440, ("int8", "imma"): 2432}
+
+
+@pytest.mark.parametrize("mode,executor", sorted(NOALLOC_LIMITS_S7))
+def test_noalloc_limits_in_the_header_hold(built, mode, executor):
+    """The sizes the header promises for ozaki_gemm_noalloc fit its 128 MiB array
+    and the next multiple of 32 does not, so the documented limit cannot drift
+    away from the workspace the product really needs."""
+    from paper_2407_13299_gb300 import dmp
+
+    text = open(HEADER).read()
+    limit = NOALLOC_LIMITS_S7[(mode, executor)]
+    assert str(limit) in text
+    cap = 128 << 20
+    assert dmp.gemm_workspace_bytes(limit, limit, limit, mode, 7, executor) <= cap
+    assert dmp.gemm_workspace_bytes(limit + 32, limit + 32, limit + 32, mode, 7, executor) > cap
+
+
 def test_argument_errors_without_gpu(built):
     from paper_2407_13299_gb300 import dmp
 

@@ -42,6 +42,25 @@ def test_noalloc_matches_workspace_entry_point_twice(dmp, executor):
         assert torch.equal(got, want), (m, n, k, s)
 
 
+@pytest.mark.parametrize("mode,limit", [("int8", 1056), ("e4m3", 1440)])
+def test_noalloc_at_its_size_limit(dmp, mode, limit):
+    """The largest square problem the header promises (s = 7, tcgen05) gives the
+    bits of ozaki_gemm; one step of 32 larger is refused before any launch."""
+    rng = np.random.default_rng(limit)
+    A = torch.from_numpy(rng.standard_normal((limit, limit))).cuda()
+    B = torch.from_numpy(rng.standard_normal((limit, limit))).cuda()
+    want = dmp.ozaki_gemm(A, B, mode, 7, "tc")
+    got = torch.full_like(want, float("nan"))
+    assert _noalloc(dmp, A, B, got, mode, 7, "tc") == dmp.OK
+    assert torch.equal(got, want)
+    big = limit + 32
+    Z = torch.zeros((big, big), dtype=torch.float64, device="cuda")
+    C = torch.zeros_like(Z)
+    before = dmp.launch_count()
+    assert _noalloc(dmp, Z, Z, C, mode, 7, "tc") == dmp.ERR_WORKSPACE
+    assert dmp.launch_count() == before
+
+
 def test_noalloc_rejects_problems_beyond_its_array(dmp):
     A = torch.zeros((4096, 4096), dtype=torch.float64, device="cuda")
     C = torch.zeros_like(A)
