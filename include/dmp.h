@@ -207,6 +207,32 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
               double* P, int64_t ldp, dmp_info* info, void* ws, size_t ws_bytes,
               void* tape, size_t tape_bytes, void* stream);
 
+/* Bytes of device workspace dm_purify_host needs for this n and these
+ * options: room for device copies of H and P (2 n^2 doubles) followed by
+ * dm_purify's workspace. */
+int dmp_host_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
+
+/*
+ * dm_purify_host: dm_purify with H and P in HOST memory -- the problem as Sec.
+ * "Density Matrix Purification" states it, Hamiltonian in and density matrix
+ * out, with both transfers inside the library's boundary.
+ *   H_host  n x n row-major float64 in host memory, leading dimension ldh
+ *           (upper triangle read, as for dm_purify).
+ *   P_host  n x n host output, leading dimension ldp (may not alias H_host).
+ *   ws      DEVICE workspace of dmp_host_workspace_size bytes: H is copied to
+ *           its front with one cudaMemcpy2DAsync on `stream`, dm_purify runs
+ *           on that copy with the rest of the workspace, and P is copied back
+ *           with one cudaMemcpy2DAsync on `stream`.
+ * The call synchronises `stream` before it returns, so P_host holds the result
+ * (and H_host may be reused) on return. Page-locked host buffers make both
+ * copies DMA transfers at full link speed; pageable ones work but the driver
+ * stages them. P_host is written only when the status is >= 0. Options,
+ * statuses and errors are those of dm_purify; there is no tape (the adjoint
+ * needs the device-resident dm_purify).
+ */
+int dm_purify_host(const double* H_host, int64_t n, int64_t ldh, int64_t n_occ, const dmp_opts* opts,
+                   double* P_host, int64_t ldp, dmp_info* info, void* ws, size_t ws_bytes, void* stream);
+
 /* Bytes of workspace ozaki_gemm needs. */
 int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int32_t slices,
                               int32_t executor, size_t* bytes);
@@ -246,16 +272,20 @@ int ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, co
  * allocation of its own (no cudaMalloc/cudaFree, no allocating library call).
  *   - The array belongs to the library: every GPU that loads it keeps the
  *     128 MiB until the process exits.
- *   - Its first call on a device looks up the array's device address (one
- *     cudaGetSymbolAddress with that device current) and caches it; make that
- *     first call before any stream capture.
+ *   - Every call looks up the array's device address in the current context
+ *     (cudaGetSymbolAddress with the caller's device current) instead of
+ *     keeping it, so a context created anew after cudaDeviceReset gets the
+ *     array's new address. The first call on a device may load the library's
+ *     device code; make it before any stream capture.
  *   - All calls share the one array, so calls that overlap on the GPU (on
  *     different streams, or from several threads) race and give undefined
  *     results. Serialise them.
  *   - Problems whose scratch (as ozaki_gemm_workspace_size reports it) exceeds
- *     128 MiB are rejected with DMP_ERR_WORKSPACE before any work is enqueued;
- *     at s = 7 square problems fit up to m = n = k = 1536 on the tcgen05
- *     executor and 2432 on the int8 mma executor. DMP_FP64 needs no scratch.
+ *     128 MiB are rejected with DMP_ERR_WORKSPACE before any work is enqueued.
+ *     At s = 7 square problems fit up to m = n = k = 1056 in the INT8 and BF16
+ *     modes on the tcgen05 executor (two-byte digits and an 80 MiB partial-sum
+ *     area), 1440 in the E4M3 mode and 2432 on the int8 mma executor.
+ *     DMP_FP64 needs no scratch.
  * Arguments and the other return codes are those of ozaki_gemm.
  */
 int ozaki_gemm_noalloc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
@@ -295,7 +325,11 @@ int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* 
 
 /*
  * dm_purify_batched: purify `batch` independent Hamiltonians of possibly
- * different sizes with the same options. H, P, n and n_occ are HOST arrays of
+ * different sizes with the same options. Each member is the canonical
+ * purification of Sec. "Density Matrix Purification" (the method of dm_purify,
+ * with the Ozaki products of Sec. "Ozaki Scheme"); the paper purifies one
+ * system at a time, and grouping many small ones into shared launches is this
+ * library's scheduling, which changes no member's arithmetic. H, P, n and n_occ are HOST arrays of
  * length `batch`; H[b] and P[b] are device pointers (n[b] x n[b], leading
  * dimension n[b]). infos (host, length batch, nullable) receives one report per
  * matrix. Each matrix stops on its own rule; the call returns DMP_OK when all
@@ -312,7 +346,10 @@ int dmp_backward_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes);
 /*
  * dm_purify_backward: reverse mode through the purification that dm_purify
  * ran with `tape` and the same options, giving dL/dH for a loss L(P) from
- * G = dL/dP (n x n, leading dimension n). Each step k is differentiated with
+ * G = dL/dP (n x n, leading dimension n). The forward is the canonical
+ * purification of Sec. "Density Matrix Purification" (the update of the cited
+ * Palser-Manolopoulos method, products by the Ozaki scheme); the paper does
+ * not differentiate it, and this is the exact adjoint of that iteration. Each step k is differentiated with
  * its branch and the iteration count frozen and with the dependence of the
  * coefficient c_k on P_k kept:
  *   dL/dP_k = alpha G + b2 (G P + P G) + b3 (G P^2 + P G P + P^2 G)
@@ -454,6 +491,36 @@ const char* dmp_version(void);
  * launch; returns the previous setting. A performance knob with no
  * counterpart in the paper. */
 int dmp_set_tc_pairing(int enable);
+
+/* Whether single-matrix DMP_EXEC_TC products split their output tiles when
+ * they fill at most half a wave of the persistent kernel (one CTA, or CTA
+ * pair, per SM): the tiles are then cut into units of one exact fp32 chunk and
+ * shared out evenly over every CTA, so the idle part of the GPU works too
+ * (n <= 2048 in the purification on GB300: 25-40 % less product time). The
+ * partial level sums are
+ * integers added at L2, so any split gives the same exact sums and the result
+ * is bit-for-bit that of whole tiles. Used by dm_purify, dm_purify_backward and
+ * dm_foe (their workspaces include the room it needs), with at most two level
+ * groups (s <= 8 for beta 7 and 5, s <= 6 for beta 8); ozaki_gemm runs whole
+ * tiles. On by default. Process-wide, read at each launch; returns the
+ * previous setting. A performance knob with no counterpart in the paper. */
+int dmp_set_tc_split_tiles(int enable);
+
+/* Test hook for the bounded device waits (no counterpart in the paper). The
+ * next tcgen05 product launch of the process (from any single-matrix entry
+ * point, on any stream) is started with every wait bounded by wait_limit_us
+ * microseconds instead of the
+ * normal 5 s, and each of its CTAs withholds the operand copies of its first
+ * pipeline stage: that stage's barrier never completes, so the MMA issuer's
+ * wait on it runs out. The kernel then takes its abort path -- it raises the
+ * call's error flag, waits (bounded) for the copies it did issue, frees its
+ * tensor memory and returns -- and the call reports DMP_ERR_TIMEOUT. Nothing
+ * faults and nothing is left running; the next call is unaffected. One-shot:
+ * the setting is consumed by that launch. 0 cancels a pending request; a
+ * negative limit is DMP_ERR_INVALID_ARG. Launches being captured into a CUDA
+ * graph, the grouped launches of dm_purify_batched, the int8 mma executor and
+ * the FP64 products do not take it. */
+int dmp_test_stall_next_product(int32_t wait_limit_us);
 
 #ifdef __cplusplus
 }

@@ -111,7 +111,7 @@ int64_t row_pad(int executor) { return executor == DMP_EXEC_TC ? 256 : kTileM; }
 
 // ---------------------------------------------------------------- dm_purify layout
 struct PurifyLayout {
-  size_t state, partials, rowbuf, expsP, expsX, err, Palt, X2, planesP, planesX, scratch, total;
+  size_t state, partials, rowbuf, expsP, expsX, err, Palt, X2, planesP, planesX, scratch, split, total;
   int64_t n_pad, k_pad;
 };
 
@@ -138,17 +138,20 @@ PurifyLayout purify_layout(int64_t n, const Opts& o) {
     L.planesP = L.planesX = 0;
   }
   L.scratch = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_scratch_bytes()) : 0;
+  L.split = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_split_bytes()) : 0;
   L.total = c.cur;
   return L;
 }
 
 // One Ozaki product from prepared digit planes on the chosen executor.
+// `split_ws` (nullable) is the tcgen05 executor's workspace for split launches (tc_split_bytes).
 cudaError_t launch_product(const Opts& o, const void* pa, const void* pb, const int32_t* ea, const int32_t* eb,
                            int64_t m, int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int sym,
-                           const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st) {
+                           const EpiArgs& epi, const int* done, int* err, double* scratch, void* split_ws,
+                           cudaStream_t st) {
   if (o.executor == DMP_EXEC_TC)
     return launch_ozaki_tc(pa, pb, ea, eb, m, n, rows_a, rows_b, k_pad, o.s, o.beta, sym, epi, done, err, scratch,
-                           st);
+                           split_ws, st);
   return launch_ozaki_imma(static_cast<const int8_t*>(pa), static_cast<const int8_t*>(pb), ea, eb, m, n, rows_a,
                            rows_b, k_pad, o.s, o.beta, sym, epi, done, st);
 }
@@ -184,7 +187,7 @@ inline char* at(void* base, size_t off) { return static_cast<char*>(base) + off;
 // buffers of one product.
 struct BackwardLayout {
   size_t state, scalars, p0, partials, err, expsP, expsA, G, Gn, Y, Z, YP, ZP, segP, segX, planesP, planesA,
-      scratch, total;
+      scratch, split, total;
   int64_t n_pad, k_pad;
 };
 
@@ -217,6 +220,7 @@ BackwardLayout backward_layout(int64_t n, const Opts& o) {
     B.planesP = B.planesA = 0;
   }
   B.scratch = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_scratch_bytes()) : 0;
+  B.split = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_split_bytes()) : 0;
   B.total = c.cur;
   return B;
 }
@@ -237,7 +241,7 @@ constexpr int kFoeMaxQ = 128;  // ps_q(DMP_FOE_MAX_TERMS)
 // (split once), of the current right operand, and of y = T_q (scheme 1).
 struct FoeLayout {
   size_t state, rowbuf, scal, coeffs, traces, w, gx, fold, psw, ip, dots, partials, err, Hs, Ta, Tb, Y, Tps, expsH,
-      expsT, expsY, planesH, planesT, planesY, scratch, total;
+      expsT, expsY, planesH, planesT, planesY, scratch, split, total;
   int64_t n_pad, k_pad;
 };
 
@@ -282,6 +286,7 @@ FoeLayout foe_layout(int64_t n, const Opts& o, int scheme, int M) {
     }
   }
   F.scratch = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_scratch_bytes()) : 0;
+  F.split = (o.mode != DMP_FP64 && o.executor == DMP_EXEC_TC) ? c.take(tc_split_bytes()) : 0;
   F.total = c.cur;
   return F;
 }
@@ -306,6 +311,10 @@ const char* dmp_version(void) { return "dmp 0.1 (sm_103a)"; }
 long long dmp_launch_count(void) { return g_launches.load(); }
 
 int dmp_set_tc_pairing(int enable) { return set_tc_pairing(enable); }
+
+int dmp_test_stall_next_product(int32_t wait_limit_us) { return set_stall_test(wait_limit_us); }
+
+int dmp_set_tc_split_tiles(int enable) { return set_tc_split_tiles(enable); }
 
 const char* dmp_status_str(int code) {
   switch (code) {
@@ -377,6 +386,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
   void* planesX = o.mode != DMP_FP64 ? at(ws, L.planesX) : nullptr;
   int* err = reinterpret_cast<int*>(at(ws, L.err));
   double* scratch = L.scratch ? reinterpret_cast<double*>(at(ws, L.scratch)) : nullptr;
+  void* split_ws = L.split ? at(ws, L.split) : nullptr;
   DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
   PurifyState init;
@@ -422,7 +432,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
       DMP_CUDA(launch_split_rows(cur, n, n, ldcur, oi.s, oi.beta, expsP, planesP, L.n_pad, L.k_pad,
                                  elem_kind(o), nullptr, done, st));
       DMP_CUDA(launch_product(oi, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e2, done,
-                              err, scratch, st));
+                              err, scratch, split_ws, st));
     }
     if (o.method == DMP_METHOD_PM) {
       DMP_CUDA(launch_measure(cur, ldcur, X2, n, H, ldh, n, partials, state, st));
@@ -460,7 +470,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
           DMP_CUDA(launch_split_rows(alt, n, n, ldalt, oi.s, oi.beta, expsP, planesP, L.n_pad, L.k_pad,
                                      elem_kind(o), nullptr, done, st));
           DMP_CUDA(launch_product(oi, planesX, planesP, expsX, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, ez, done,
-                                  err, scratch, st));
+                                  err, scratch, split_ws, st));
         }
       }
       continue;
@@ -484,7 +494,7 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
       DMP_CUDA(launch_split_rows(X2, n, n, n, oi.s, oi.beta, expsX, planesX, L.n_pad, L.k_pad,
                                  elem_kind(o), nullptr, done, st));
       DMP_CUDA(launch_product(oi, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e3, done,
-                              err, scratch, st));
+                              err, scratch, split_ws, st));
     }
     std::swap(cur, alt);
     std::swap(ldcur, ldalt);
@@ -522,11 +532,11 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
         DMP_CUDA(launch_split_rows(cur, n, n, ldcur, orr.s, orr.beta, expsP, planesP, L.n_pad, L.k_pad,
                                    elem_kind(o), nullptr, nullptr, st));
         DMP_CUDA(launch_product(orr, planesP, planesP, expsP, expsP, n, n, L.n_pad, L.n_pad, L.k_pad, 1, r2, nullptr,
-                                err, scratch, st));
+                                err, scratch, split_ws, st));
         DMP_CUDA(launch_split_rows(X2, n, n, n, orr.s, orr.beta, expsX, planesX, L.n_pad, L.k_pad,
                                    elem_kind(o), nullptr, nullptr, st));
         DMP_CUDA(launch_product(orr, planesP, planesX, expsP, expsX, n, n, L.n_pad, L.n_pad, L.k_pad, 1, r3, nullptr,
-                                err, scratch, st));
+                                err, scratch, split_ws, st));
       }
       std::swap(cur, alt);
       std::swap(ldcur, ldalt);
@@ -583,6 +593,50 @@ int dm_purify(const double* H, int64_t n, int64_t ldh, int64_t n_occ, const dmp_
     info->h_max = fin.h_max;
   }
   return fin.status;
+}
+
+// dm_purify_host: device copies of H and P at the front of the workspace,
+// dm_purify's own workspace after them.
+static size_t host_front_bytes(int64_t n) {
+  const size_t nn = static_cast<size_t>(n) * static_cast<size_t>(n) * sizeof(double);
+  return 2 * ((nn + 255) / 256 * 256);
+}
+
+int dmp_host_workspace_size(int64_t n, const dmp_opts* opts, size_t* bytes) {
+  size_t inner = 0;
+  const int rc = dmp_workspace_size(n, opts, &inner);
+  if (rc != DMP_OK) return rc;
+  *bytes = host_front_bytes(n) + inner;
+  return DMP_OK;
+}
+
+int dm_purify_host(const double* H_host, int64_t n, int64_t ldh, int64_t n_occ, const dmp_opts* opts,
+                   double* P_host, int64_t ldp, dmp_info* info, void* ws, size_t ws_bytes, void* stream) {
+  if (H_host == nullptr || P_host == nullptr || ws == nullptr || opts == nullptr) return DMP_ERR_INVALID_ARG;
+  if (n < 2 || ldh < n || ldp < n) return DMP_ERR_INVALID_ARG;
+  size_t need = 0;
+  const int rc = dmp_host_workspace_size(n, opts, &need);
+  if (rc != DMP_OK) return rc;
+  if (ws_bytes < need) return DMP_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t front = host_front_bytes(n);
+  double* Hd = reinterpret_cast<double*>(ws);
+  double* Pd = reinterpret_cast<double*>(static_cast<char*>(ws) + front / 2);
+  const size_t row = static_cast<size_t>(n) * sizeof(double);
+  // H in: one strided copy on the caller's stream (asynchronous DMA from pinned memory)
+  DMP_CUDA(cudaMemcpy2DAsync(Hd, row, H_host, static_cast<size_t>(ldh) * sizeof(double), row, n,
+                             cudaMemcpyHostToDevice, st));
+  const int status = dm_purify(Hd, n, n, n_occ, opts, Pd, n, info, static_cast<char*>(ws) + front, ws_bytes - front,
+                               nullptr, 0, stream);
+  if (status < 0) {
+    cudaStreamSynchronize(st);  // the copy of H may still read the caller's buffer
+    return status;
+  }
+  // P out, then wait: the caller's host buffer holds P when the call returns
+  DMP_CUDA(cudaMemcpy2DAsync(P_host, static_cast<size_t>(ldp) * sizeof(double), Pd, row, row, n,
+                             cudaMemcpyDeviceToHost, st));
+  DMP_CUDA(cudaStreamSynchronize(st));
+  return status;
 }
 
 int ozaki_gemm_workspace_size(int64_t m, int64_t n, int64_t k, int32_t mode, int32_t slices,
@@ -655,7 +709,7 @@ static int ozaki_common(int64_t m, int64_t n, int64_t k, const double* A, int64_
   DMP_CUDA(launch_split_rows(Bt, n, k, k, o.s, o.beta, eb, pb, n_pad, k_pad, elem_kind(o), nullptr,
                              nullptr, st));
   if (o.executor == DMP_EXEC_TC) DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  DMP_CUDA(launch_product(o, pa, pb, ea, eb, m, n, m_pad, n_pad, k_pad, 0, epi, nullptr, err, scratch, st));
+  DMP_CUDA(launch_product(o, pa, pb, ea, eb, m, n, m_pad, n_pad, k_pad, 0, epi, nullptr, err, scratch, nullptr, st));
   if (o.executor == DMP_EXEC_TC) {
     // report an expired device wait; skipped while the stream is being captured
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -784,6 +838,7 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
   void* planesP = o.mode != DMP_FP64 ? at(ws, B.planesP) : nullptr;
   void* planesA = o.mode != DMP_FP64 ? at(ws, B.planesA) : nullptr;
   double* scratch = B.scratch ? reinterpret_cast<double*>(at(ws, B.scratch)) : nullptr;
+  void* split_ws = B.split ? at(ws, B.split) : nullptr;
   DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   const int64_t npad = B.n_pad, kpad = B.k_pad;
 
@@ -797,7 +852,8 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
     cudaError_t r = launch_split_rows(A, n, n, n, o.s, o.beta, expsA, planesA, npad, kpad, elem_kind(o),
                                       nullptr, nullptr, st);
     if (r != cudaSuccess) return r;
-    return launch_product(o, planesA, planesP, expsA, expsP, n, n, npad, npad, kpad, 0, e, nullptr, err, scratch, st);
+    return launch_product(o, planesA, planesP, expsA, expsP, n, n, npad, npad, kpad, 0, e, nullptr,
+                          err, scratch, split_ws, st);
   };
   auto split_P = [&](const double* Pk) -> cudaError_t {
     if (o.mode == DMP_FP64) return cudaSuccess;
@@ -840,8 +896,8 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
         DMP_CUDA(launch_gemm_f64(Pk, n, Pk, n, n, n, n, 1, e2, nullptr, st));
       } else {
         DMP_CUDA(split_P(Pk));
-        DMP_CUDA(launch_product(o, planesP, planesP, expsP, expsP, n, n, npad, npad, kpad, 1, e2, nullptr, err,
-                                scratch, st));
+        DMP_CUDA(launch_product(o, planesP, planesP, expsP, expsP, n, n, npad, npad, kpad, 1, e2, nullptr,
+                                err, scratch, split_ws, st));
       }
       if (k + 1 < k1) {
         DMP_CUDA(cudaMemcpyAsync(&state->alpha, &wts[k].alpha, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -859,8 +915,8 @@ int dm_purify_backward(const double* H, int64_t n, int64_t n_occ, const dmp_opts
         } else {
           DMP_CUDA(launch_split_rows(Xk, n, n, n, o.s, o.beta, expsA, planesA, npad, kpad, elem_kind(o),
                                      nullptr, nullptr, st));
-          DMP_CUDA(launch_product(o, planesP, planesA, expsP, expsA, n, n, npad, npad, kpad, 1, e3, nullptr, err,
-                                  scratch, st));
+          DMP_CUDA(launch_product(o, planesP, planesA, expsP, expsA, n, n, npad, npad, kpad, 1, e3, nullptr,
+                                  err, scratch, split_ws, st));
         }
       }
     }
@@ -956,6 +1012,7 @@ int dm_foe(const double* H, int64_t n, int64_t ldh, const dmp_foe_params* params
   void* planesH = oz ? at(ws, L.planesH) : nullptr;
   void* planesT = oz ? at(ws, L.planesT) : nullptr;
   double* scratch = L.scratch ? dbl(L.scratch) : nullptr;
+  void* split_ws = L.split ? at(ws, L.split) : nullptr;
   DMP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
 
   PurifyState init;
@@ -979,6 +1036,11 @@ int dm_foe(const double* H, int64_t n, int64_t ldh, const dmp_foe_params* params
   int products = 0;
   // Symmetric product Y = A B of two polynomials in H_s: A's digit planes
   // (pa, ea) are prepared by the caller, B is split here (FP64: A itself).
+  // After a product whose bounded device wait ran out, the error flag makes
+  // every later split and product kernel return at once (it is their `done`
+  // word), and every kFoeCheckEvery products the host reads the flag and
+  // stops enqueueing with DMP_ERR_TIMEOUT.
+  constexpr int kFoeCheckEvery = 8;
   auto product = [&](const double* A, const void* pa, const int32_t* ea, const double* B) -> int {
     EpiArgs e{};
     e.kind = EPI_SYM_STORE;
@@ -988,17 +1050,23 @@ int dm_foe(const double* H, int64_t n, int64_t ldh, const dmp_foe_params* params
       DMP_CUDA(launch_gemm_f64(A, n, B, n, n, n, n, 1, e, nullptr, st));
     } else {
       DMP_CUDA(launch_split_rows(B, n, n, n, o.s, o.beta, expsT, planesT, L.n_pad, L.k_pad, elem_kind(o), nullptr,
-                                 nullptr, st));
-      DMP_CUDA(launch_product(o, pa, planesT, ea, expsT, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e, nullptr, err,
-                              scratch, st));
+                                 err, st));
+      DMP_CUDA(launch_product(o, pa, planesT, ea, expsT, n, n, L.n_pad, L.n_pad, L.k_pad, 1, e, err,
+                              err, scratch, split_ws, st));
     }
     ++products;
+    if (oz && o.executor == DMP_EXEC_TC && products % kFoeCheckEvery == 0) {
+      int32_t flag = 0;
+      DMP_CUDA(cudaMemcpyAsync(&flag, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      DMP_CUDA(cudaStreamSynchronize(st));
+      if (flag) return DMP_ERR_TIMEOUT;
+    }
     return DMP_OK;
   };
   auto split_a = [&](const double* A, void* planes, int32_t* exps) -> int {
     if (oz)
       DMP_CUDA(launch_split_rows(A, n, n, n, o.s, o.beta, exps, planes, L.n_pad, L.k_pad, elem_kind(o), nullptr,
-                                 nullptr, st));
+                                 err, st));
     return DMP_OK;
   };
 

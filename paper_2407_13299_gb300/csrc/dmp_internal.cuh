@@ -123,11 +123,21 @@ cudaError_t launch_ozaki_imma(const int8_t* A, const int8_t* B, const int32_t* e
 // at most kTcMaxCtas CTAs, one per SM).
 constexpr int kTcMaxCtas = 160;
 size_t tc_scratch_bytes();
+// workspace of the tcgen05 executor's split launches (the tiles' shared group sums and
+// counters); a launch given none runs whole tiles only
+size_t tc_split_bytes();
+// whether single-matrix tcgen05 products that fill at most half a wave of CTAs
+// are split into chunk units shared by every CTA; returns the previous setting
+int set_tc_split_tiles(int enable);
 // beta = 7 single-matrix products on CTA pairs (2-SM MMA); returns the previous setting
 int set_tc_pairing(int enable);
+// The next tcgen05 product launch withholds each CTA's first operand stage and
+// bounds its waits by wait_limit_us (the bounded-wait test); one-shot.
+int set_stall_test(int wait_limit_us);
 cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, const int32_t* eb, int64_t m,
                             int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int s, int beta, int sym,
-                            const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st);
+                            const EpiArgs& epi, const int* done, int* err, double* scratch, void* split_ws,
+                            cudaStream_t st);
 
 // FP64 executor: C = A B (A m x k, B k x n row-major) with the same epilogues.
 cudaError_t launch_gemm_f64(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t m,

@@ -36,6 +36,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -91,6 +92,13 @@ struct TcParams {
   const int* done;
   int* err;
   unsigned long long timeout_ns;
+  int stall_test;  // withhold each CTA's first stage (the bounded-wait test; see dmp_test_stall_next_product)
+  // split launches (fewer tiles than CTAs or CTA pairs): every tile is cut
+  // into split_unit_count units of one fp32 chunk, shared out in contiguous
+  // ranges over all CTAs (CTA pairs)
+  int split_unit_count;
+  long long* split_area;  // per (tile, CTA rank in the pair): two TC_BM x BN int64 group sums
+  int* split_cnt;         // per (tile, rank, epilogue warp): contributors counted in
   // grouped mode (batched purification): tiles of many matrices in one launch
   const BatchMat* mats;  // nullptr: the single matrix above
   const int4* tiles;     // {matrix, bi, bj, 0}
@@ -257,13 +265,26 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
-__device__ __forceinline__ long long ld_keep(const void* p, uint64_t pol) {
-  long long v;
-  asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
-  return v;
-}
 __device__ __forceinline__ void st_keep(void* p, long long v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
+}
+// 64-bit load from L2 (.cg: not through this SM's L1, which may hold a line
+// from before a reduction at L2)
+__device__ __forceinline__ long long ld_l2(const void* p, uint64_t pol) {
+  long long v;
+  asm volatile("ld.global.cg.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol) : "memory");
+  return v;
+}
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+// 64-bit integer add performed at L2 (no value returned, so no round trip):
+// two's complement, so it adds signed values exactly
+__device__ __forceinline__ void red_add_keep(void* p, long long v, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
 }
 
 // x 2^e for a finite double: exponent arithmetic when the result stays normal,
@@ -453,7 +474,14 @@ __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA,
 // leader's (rank 0) full barrier; the leader alone issues the cta_group::2
 // MMAs and its commits arrive on the stage and accumulator barriers of both
 // CTAs; both epilogues release a TMEM buffer on the leader's barrier.
-template <int BN, bool PAIR, bool F8 = false>
+//
+// SPLIT: the launch's tiles fill at most half a wave of CTAs (CTA pairs), so
+// they are all cut into units of one exact fp32 chunk and shared out evenly in
+// contiguous ranges over every CTA; each range's partial level sums are added
+// at L2 into the tiles' shared group sums, and the last contributor to a tile
+// writes its output. Integer sums do not depend on the split: the result is
+// bit-for-bit that of whole tiles.
+template <int BN, bool PAIR, bool F8 = false, bool SPLIT = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const TcParams p) {
@@ -514,53 +542,97 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
   const int CH = p.CH;
 
+  // SPLIT: this CTA's contiguous range [u_begin, u_end) of the launch's chunk
+  // units (p.split_unit_count per tile, all tiles split)
+  const int KTS_ = p.KT / Cfg::KSUB;  // stages per slice pair (single-matrix launches)
+  const int CHS_ = CH / Cfg::KSUB;    // stages per fp32 chunk
+  const int64_t split_units = SPLIT ? static_cast<int64_t>(p.ntiles) * p.split_unit_count : 0;
+  const int64_t u_begin = split_units * cta_id / cta_stride;
+  const int64_t u_end = split_units * (cta_id + 1) / cta_stride;
+  // unit u: its tile tt, level L and stage range [kb0, kb1)
+  auto split_unit = [&](int64_t u, int& tt, int& L, int& kb0, int& kb1) __attribute__((always_inline)) {
+    tt = static_cast<int>(u / p.split_unit_count);
+    int w = static_cast<int>(u % p.split_unit_count);
+    for (L = p.s + 1; L > 2; --L) {
+      const int nkb = npairs_of(L, p.s) * KTS_;
+      const int nch = (nkb + CHS_ - 1) / CHS_;
+      if (w < nch) break;
+      w -= nch;
+    }
+    const int nkb = npairs_of(L, p.s) * KTS_;
+    kb0 = w * CHS_;
+    kb1 = min(kb0 + CHS_, nkb);
+  };
+
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      uint32_t armed = 0;  // stages armed in the current ring pass (for the abort drain)
+      // for the abort drain: stages ever armed, and the parity of the phase each
+      // was last armed in (that phase completes when its copies have landed)
+      uint32_t armed = 0, armed_par = 0;
+      bool withheld = false;  // stall test: the first stage has been withheld
       // PAIR: both CTAs' copies complete on the leader's full barrier, which expects both
       const uint32_t full_target0 = PAIR ? map_to_cta(full_bar(0), 0) : full_bar(0);
       const uint32_t expect_bytes = PAIR ? 2u * Cfg::STAGE_BYTES : static_cast<uint32_t>(Cfg::STAGE_BYTES);
       const int b_off = PAIR ? static_cast<int>(rank) * (BN / 2) : 0;  // this CTA's half of the B rows
-      for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
-        const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
-        if (jb.skip) continue;
-        const int s = jb.s;
-        for (int L = s + 1; L >= 2 && ok; --L) {
-          const int i_lo = max(1, L - s), i_hi = min(s, L - 1);
-          for (int i = i_lo; i <= i_hi && ok; ++i) {
-            const int j = L - i;
-            const int ya = static_cast<int>((i - 1) * jb.rows_a + jb.m0);
-            const int yb = static_cast<int>((j - 1) * jb.rows_b + jb.n0) + b_off;
-            for (int kt = 0; kt < jb.KT; kt += Cfg::KSUB) {
-              if (!wait_bar<PAIR>(empty_bar(stage), phase ^ 1u, abort_flag, p)) {
-                ok = false;
-                break;
-              }
-              const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
-              if (PAIR) {
-                const uint32_t fb = full_target0 + 8u * stage;
-                if (leader) mbar_arrive_expect_tx(full_bar(stage), expect_bytes);
+      // one stage: slice pair (i, j), K atoms kt .. kt + KSUB - 1
+      auto put_stage = [&](const Job& jb, int i, int j, int kt) __attribute__((always_inline)) -> bool {
+        if (!wait_bar<PAIR>(empty_bar(stage), phase ^ 1u, abort_flag, p)) return false;
+        const int ya = static_cast<int>((i - 1) * jb.rows_a + jb.m0);
+        const int yb = static_cast<int>((j - 1) * jb.rows_b + jb.n0) + b_off;
+        const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
+        if (p.stall_test && !withheld) {
+          // stall test: neither the expected bytes nor the copies of this CTA's
+          // first stage are issued, so its full barrier never completes and
+          // the MMA issuer's bounded wait on it runs out (nothing is in
+          // flight for this stage; the later stages drain as in any abort)
+          withheld = true;
+        } else {
+          if (PAIR) {
+            const uint32_t fb = full_target0 + 8u * stage;
+            if (leader) mbar_arrive_expect_tx(full_bar(stage), expect_bytes);
 #pragma unroll
-                for (int u = 0; u < Cfg::KSUB; ++u) {
-                  tma_load_2d_pair(sa + u * Cfg::A_ATOM, jb.ta, fb, (kt + u) * Cfg::ATOM_K, ya);
-                  tma_load_2d_pair(sa + Cfg::A_BYTES + u * Cfg::B_ATOM, jb.tb, fb, (kt + u) * Cfg::ATOM_K, yb);
-                }
-              } else {
-                mbar_arrive_expect_tx(full_bar(stage), expect_bytes);
-                tma_load_2d(sa, jb.ta, full_bar(stage), kt * Cfg::ATOM_K, ya);
-                tma_load_2d(sa + Cfg::A_BYTES, jb.tb, full_bar(stage), kt * Cfg::ATOM_K, yb);
-              }
-              armed |= 1u << stage;
-              if (++stage == Cfg::STAGES) {
-                stage = 0;
-                phase ^= 1u;
-                armed = 0;
-              }
+            for (int u = 0; u < Cfg::KSUB; ++u) {
+              tma_load_2d_pair(sa + u * Cfg::A_ATOM, jb.ta, fb, (kt + u) * Cfg::ATOM_K, ya);
+              tma_load_2d_pair(sa + Cfg::A_BYTES + u * Cfg::B_ATOM, jb.tb, fb, (kt + u) * Cfg::ATOM_K, yb);
             }
+          } else {
+            mbar_arrive_expect_tx(full_bar(stage), expect_bytes);
+            tma_load_2d(sa, jb.ta, full_bar(stage), kt * Cfg::ATOM_K, ya);
+            tma_load_2d(sa + Cfg::A_BYTES, jb.tb, full_bar(stage), kt * Cfg::ATOM_K, yb);
+          }
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+        }
+        if (++stage == Cfg::STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+        return true;
+      };
+      if constexpr (!SPLIT) {
+        for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
+          const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
+          if (jb.skip) continue;
+          const int s = jb.s;
+          for (int L = s + 1; L >= 2 && ok; --L) {
+            const int i_lo = max(1, L - s), i_hi = min(s, L - 1);
+            for (int i = i_lo; i <= i_hi && ok; ++i)
+              for (int kt = 0; kt < jb.KT && ok; kt += Cfg::KSUB) ok = put_stage(jb, i, L - i, kt);
+          }
+        }
+      } else {
+        for (int64_t u = u_begin; u < u_end && ok; ++u) {
+          int tt, L, kb0, kb1;
+          split_unit(u, tt, L, kb0, kb1);
+          const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tt, rank);
+          const int i_lo = max(1, L - p.s);
+          for (int kb = kb0; kb < kb1 && ok; ++kb) {
+            const int i = i_lo + kb / KTS_;
+            ok = put_stage(jb, i, L - i, (kb % KTS_) * Cfg::KSUB);
           }
         }
       }
@@ -569,8 +641,9 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         // leader's full barriers count both CTAs' copies)
         for (int st = 0; st < Cfg::STAGES; ++st) {
           if (armed & (1u << st)) {
+            const uint32_t par = (armed_par >> st) & 1u;
             const uint64_t dl = globaltimer() + 100000000ull;
-            while (!mbar_try_wait(full_bar(st), phase) && globaltimer() < dl) {
+            while (!mbar_try_wait(full_bar(st), par) && globaltimer() < dl) {
             }
           }
         }
@@ -590,80 +663,87 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0 && leader) {
-      constexpr uint32_t idesc = F8 ? idesc_e4m3(PAIR ? 2 * TC_BM : TC_BM, BN) : idesc_bf16(PAIR ? 2 * TC_BM : TC_BM, BN);
+      constexpr uint32_t idesc =
+          F8 ? idesc_e4m3(PAIR ? 2 * TC_BM : TC_BM, BN) : idesc_bf16(PAIR ? 2 * TC_BM : TC_BM, BN);
       int stage = 0;
       uint32_t phase = 0;
       int buf = 0;
       uint32_t aph[2] = {0u, 0u};
       bool ok = true;
       bool issued = false;
-      for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
-        const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
-        if (jb.skip) continue;
-        const int s = jb.s;
-        // stages per level and per fp32 chunk (KT and CH are multiples of KSUB)
-        const int CHS = CH / Cfg::KSUB;
-        for (int L = s + 1; L >= 2 && ok; --L) {
-          const int nkb = npairs_of(L, s) * (jb.KT / Cfg::KSUB);
-          for (int kb = 0; kb < nkb; ++kb) {
-            const int kc = kb % CHS;
-            const bool first = kc == 0;
-            const bool last = (kc == CHS - 1) || (kb == nkb - 1);
-            if (first) {
-              if (!wait_bar<PAIR>(accempty_bar(buf), aph[buf] ^ 1u, abort_flag, p)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-            }
-            if (!wait_bar<PAIR>(full_bar(stage), phase, abort_flag, p)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
-            const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
+      // one stage of MMAs; `first` starts a chunk (waits for a free TMEM buffer
+      // and overwrites it), `last` ends it (publishes the buffer)
+      auto mma_stage = [&](bool first, bool last) __attribute__((always_inline)) -> bool {
+        if (first) {
+          if (!wait_bar<PAIR>(accempty_bar(buf), aph[buf] ^ 1u, abort_flag, p)) return false;
+          tc_fence_after();
+        }
+        if (!wait_bar<PAIR>(full_bar(stage), phase, abort_flag, p)) return false;
+        tc_fence_after();
+        const uint32_t sa = sbase + stage * Cfg::STAGE_BYTES;
+        const uint32_t d = tmem + static_cast<uint32_t>(buf * BN);
 #pragma unroll
-            for (int u = 0; u < Cfg::KSUB; ++u) {
-              const uint64_t ad = sdesc_sw128(sa + u * Cfg::A_ATOM);
-              const uint64_t bd = sdesc_sw128(sa + Cfg::A_BYTES + u * Cfg::B_ATOM);
+        for (int u = 0; u < Cfg::KSUB; ++u) {
+          const uint64_t ad = sdesc_sw128(sa + u * Cfg::A_ATOM);
+          const uint64_t bd = sdesc_sw128(sa + Cfg::A_BYTES + u * Cfg::B_ATOM);
 #pragma unroll
-              for (int ks = 0; ks < TC_MMA_PER_ATOM; ++ks) {
-                // advance 32 bytes (16 bf16 or 32 e4m3) along K inside the swizzled row
-                const uint32_t acc = (first && u == 0 && ks == 0) ? 0u : 1u;
-                if (F8) {
-                  if (PAIR) {
-                    umma_e4m3_pair(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
-                  } else {
-                    umma_e4m3(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
-                  }
-                } else if (PAIR) {
-                  umma_bf16_pair(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
-                } else {
-                  umma_bf16(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
-                }
-              }
-            }
-            issued = true;
-            if (PAIR) {
-              umma_commit_pair_both(empty_bar(stage));
-            } else {
-              umma_commit(empty_bar(stage));
-            }
-            if (last) {
+          for (int ks = 0; ks < TC_MMA_PER_ATOM; ++ks) {
+            // advance 32 bytes (16 bf16 or 32 e4m3) along K inside the swizzled row
+            const uint32_t acc = (first && u == 0 && ks == 0) ? 0u : 1u;
+            if (F8) {
               if (PAIR) {
-                umma_commit_pair_both(accfull_bar(buf));
+                umma_e4m3_pair(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
               } else {
-                umma_commit(accfull_bar(buf));
+                umma_e4m3(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
               }
-              aph[buf] ^= 1u;
-              buf ^= 1;
-            }
-            if (++stage == Cfg::STAGES) {
-              stage = 0;
-              phase ^= 1u;
+            } else if (PAIR) {
+              umma_bf16_pair(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
+            } else {
+              umma_bf16(d, ad + 2ull * ks, bd + 2ull * ks, idesc, acc);
             }
           }
+        }
+        issued = true;
+        if (PAIR) {
+          umma_commit_pair_both(empty_bar(stage));
+        } else {
+          umma_commit(empty_bar(stage));
+        }
+        if (last) {
+          if (PAIR) {
+            umma_commit_pair_both(accfull_bar(buf));
+          } else {
+            umma_commit(accfull_bar(buf));
+          }
+          aph[buf] ^= 1u;
+          buf ^= 1;
+        }
+        if (++stage == Cfg::STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+        return true;
+      };
+      if constexpr (!SPLIT) {
+        for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
+          const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
+          if (jb.skip) continue;
+          const int s = jb.s;
+          // stages per level and per fp32 chunk (KT and CH are multiples of KSUB)
+          const int CHS = CH / Cfg::KSUB;
+          for (int L = s + 1; L >= 2 && ok; --L) {
+            const int nkb = npairs_of(L, s) * (jb.KT / Cfg::KSUB);
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+              const int kc = kb % CHS;
+              ok = mma_stage(kc == 0, (kc == CHS - 1) || (kb == nkb - 1));
+            }
+          }
+        }
+      } else {
+        for (int64_t u = u_begin; u < u_end && ok; ++u) {
+          int tt, L, kb0, kb1;
+          split_unit(u, tt, L, kb0, kb1);
+          for (int kb = kb0; kb < kb1 && ok; ++kb) ok = mma_stage(kb == kb0, kb == kb1 - 1);
         }
       }
       if (!ok && issued) {
@@ -692,13 +772,18 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const int row = 32 * q + lane;
     const int cbase = h * COLS;
     const uint32_t taddr_row = tmem + (static_cast<uint32_t>(32 * q) << 16);
-    // this thread's float64 partial sums: element c at scr[32 c] (a warp touches
+    // fold buffers of this thread (whole tiles): the int64 group sums, or the
+    // running group and the float64 sum D; element c at [32 c] (a warp touches
     // 256 contiguous bytes per column), private to this CTA and L2-resident
-    // fold buffers of this thread: the int64 group sum and the float64 sum,
-    // element c at [32 c] (a warp touches 256 contiguous bytes per column)
     long long* scr_i = reinterpret_cast<long long*>(p.scratch) +
                        static_cast<int64_t>(blockIdx.x) * (2 * TC_BM * BN) + e * (COLS * 32) + lane;
     long long* scr_d = scr_i + TC_BM * BN;
+    // SPLIT: the group sums of (tile tt, this CTA's row half), shared by the
+    // CTAs that contribute to the tile; same element layout
+    auto split_area_of = [&](int tt, int gidx) __attribute__((always_inline)) -> long long* {
+      return p.split_area + ((static_cast<int64_t>(tt) * (PAIR ? 2 : 1) + rank) * 2 + gidx) * (TC_BM * BN) +
+             e * (COLS * 32) + lane;
+    };
 
     int32_t S[COLS];
     int buf = 0;
@@ -706,149 +791,276 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     bool ok = true;
     // PAIR: TMEM buffers are released on the leader's barrier
     const uint32_t accempty_target0 = PAIR ? map_to_cta(accempty_bar(0), 0) : accempty_bar(0);
-    for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
-      int64_t m0, n0;
-      int s, KT;
-      bool skip;
-      {
-        const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
-        m0 = jb.m0;
-        n0 = jb.n0;
-        s = jb.s;
-        KT = jb.KT;
-        skip = jb.skip;
+
+    // one finished chunk from TMEM added into the level sum S (one call site
+    // per kernel: a second, specialised copy costs the register allocator far
+    // more than zeroing S)
+    auto drain_chunk = [&]() __attribute__((always_inline)) -> bool {
+      // one lane polls the barrier (32 pollers per warp would crowd the
+      // barrier word the MMA issuer and the copies also use); the warp then
+      // synchronises and orders its TMEM loads after that wait (tcgen05.ld
+      // below is warp-collective, so the whole warp takes the same branch)
+      int got = 0;
+      if (lane == 0) got = wait_bar<PAIR>(accfull_bar(buf), aph[buf], abort_flag, p) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (!got) return false;
+      tc_fence_after();
+#pragma unroll
+      for (int g = 0; g < COLS / 16; ++g) {
+        uint32_t v[16];
+        tmem_ld16(taddr_row + static_cast<uint32_t>(buf * BN + cbase + 16 * g), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) S[16 * g + t] += __float2int_rn(__uint_as_float(v[t]));
       }
-      if (skip) continue;
-      for (int L = s + 1; L >= 2 && ok; --L) {
-#pragma unroll
-        for (int c = 0; c < COLS; ++c) S[c] = 0;
-        const int nkb = npairs_of(L, s) * KT;
-        const int nch = (nkb + CH - 1) / CH;
-        for (int ch = 0; ch < nch; ++ch) {
-          // the whole warp takes the same branch: tcgen05.ld below is warp-collective
-          const bool got = wait_bar<PAIR>(accfull_bar(buf), aph[buf], abort_flag, p);
-          if (!__all_sync(0xffffffffu, got)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-#pragma unroll
-          for (int g = 0; g < COLS / 16; ++g) {
-            uint32_t v[16];
-            tmem_ld16(taddr_row + static_cast<uint32_t>(buf * BN + cbase + 16 * g), v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int t = 0; t < 16; ++t) S[16 * g + t] += __float2int_rn(__uint_as_float(v[t]));
-          }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            if (PAIR) {
-              mbar_arrive_cluster(accempty_target0 + 8u * buf);
-            } else {
-              mbar_arrive(accempty_bar(buf));
-            }
-          }
-          aph[buf] ^= 1u;
-          buf ^= 1;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (PAIR) {
+          mbar_arrive_cluster(accempty_target0 + 8u * buf);
+        } else {
+          mbar_arrive(accempty_bar(buf));
         }
-        if (!ok) break;
-        if (p.epi.kind == EPI_LEVELS && p.mats == nullptr) {
-          // test hook: write the exact level sum itself
-          const int64_t r = m0 + row;
-          if (r < p.m) {
+      }
+      aph[buf] ^= 1u;
+      buf ^= 1;
+      return true;
+    };
+
+    // the output step of a finished tile: unscale the group sums in a0 (group 0)
+    // and a1 (group 1, or D with three or more groups) and write C (or the
+    // update). The group sums are read from L2 (.cg): reductions at L2, and for
+    // the split those of other CTAs, never pass through this SM's L1.
+    auto output_tile = [&](const Job& jb, int64_t m0, int64_t n0, int s, const long long* a0,
+                           const long long* a1) __attribute__((always_inline)) {
+      const int64_t r = m0 + row;
+      if (r >= jb.m) return;
+      const int32_t er = jb.ea[r];
+      const bool upd = jb.epi.kind == EPI_PM_UPDATE;
+      const double wa = upd ? jb.epi.state->alpha : 0.0;
+      const double w2 = upd ? jb.epi.state->b2 : 0.0;
+      const double w3 = upd ? jb.epi.state->b3 : 0.0;
+      // last group (levels 2 .. L_a, L_a = 2 + (s - 1) mod G) in a0, or in a1
+      // for two groups (then a0 holds group 0, weight 2^(-beta (s+1))); with
+      // three or more groups the earlier ones are summed in D (a1)
+      const double lscale = ldexp(1.0, -p.beta * (2 + (s - 1) % p.group));
+      const bool has_d = s > p.group;
+      const bool two_groups = has_d && s <= 2 * p.group;
+      const double g0scale = ldexp(1.0, -p.beta * (s + 1));
+      const uint64_t pol = policy_evict_last();
+      double* Cout = jb.epi.C;
+      const int64_t ldc = jb.epi.ldc;
+      // batches of 8 columns: issue every load of the batch, then compute and
+      // store; the next batch's P and P^2 lines are requested into L1 meanwhile
+      auto prefetch_batch = [&](int gb) __attribute__((always_inline)) {
+        const int64_t c0 = n0 + cbase + 8 * gb;
+        if (!upd || gb >= COLS / 8 || c0 >= jb.n) return;
 #pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (c0 + t < jb.n) {
+            prefetch_l1(jb.epi.P + (c0 + t) * jb.epi.ldp + r);
+            prefetch_l1(jb.epi.X2 + (c0 + t) * jb.epi.ldx + r);
+          }
+        }
+      };
+      for (int g = 0; g < COLS / 8; ++g) {
+        const int64_t col0 = n0 + cbase + 8 * g;
+        if (col0 >= jb.n) break;
+        long long ti[8], td[8];
+        double pv[8], xv[8];
+        int32_t ecv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int c = 8 * g + t;
+          const int64_t col = col0 + t;
+          const bool ok = col < jb.n;
+          ti[t] = ld_l2(a0 + 32 * c, pol);
+          td[t] = has_d ? ld_l2(a1 + 32 * c, pol) : 0ll;
+          ecv[t] = ok ? jb.eb[col] : 0;
+          // P and P^2 are exactly symmetric: read them at (col, r), coalesced across the warp
+          pv[t] = (upd && ok) ? jb.epi.P[col * jb.epi.ldp + r] : 0.0;
+          xv[t] = (upd && ok) ? jb.epi.X2[col * jb.epi.ldx + r] : 0.0;
+        }
+        prefetch_batch(g + 1);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int64_t col = col0 + t;
+          if (col >= jb.n) break;
+          if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
+          const double acc =
+              two_groups ? static_cast<double>(ti[t]) * g0scale + static_cast<double>(td[t]) * lscale
+                         : (has_d ? __longlong_as_double(td[t]) + static_cast<double>(ti[t]) * lscale
+                                  : static_cast<double>(ti[t]) * lscale);
+          double v = (er == kBadExp || ecv[t] == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                          : scale_pow2(acc, er + ecv[t]);
+          if (upd) v = wa * pv[t] + w2 * xv[t] + w3 * v;
+          v = stored_value(v, jb.epi.round32 != 0);
+          Cout[r * ldc + col] = v;
+          if (jb.sym && r < col) Cout[col * ldc + r] = v;
+        }
+      }
+    };
+
+    if constexpr (!SPLIT) {
+      // ---- whole tiles
+      for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
+        int64_t m0, n0;
+        int s, KT;
+        bool skip;
+        {
+          const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
+          m0 = jb.m0;
+          n0 = jb.n0;
+          s = jb.s;
+          KT = jb.KT;
+          skip = jb.skip;
+        }
+        if (skip) continue;
+        for (int L = s + 1; L >= 2 && ok; --L) {
+#pragma unroll
+          for (int c = 0; c < COLS; ++c) S[c] = 0;
+          if (L == 2 && p.epi.kind == EPI_PM_UPDATE && p.mats == nullptr && m0 + row < p.m) {
+            // the update reads P and P^2 in the output pass: ask L2 for this
+            // thread's elements while the last level's chunks are still running
             for (int c = 0; c < COLS; ++c) {
               const int64_t col = n0 + cbase + c;
-              if (col < p.n) p.epi.levels[static_cast<int64_t>(L - 2) * p.m * p.n + r * p.n + col] = S[c];
+              if (col >= p.n) break;
+              prefetch_l2(p.epi.P + col * p.epi.ldp + m0 + row);
+              prefetch_l2(p.epi.X2 + col * p.epi.ldx + m0 + row);
             }
           }
-          continue;
-        }
-        // ---- fold the exact level sum (groups of levels, smallest first; see the header)
-        {
-          const uint64_t pol = policy_evict_last();
-          // up to G consecutive levels (G = 4 for beta 7 and 5, 3 for beta 8)
-          // combine exactly in int64, T = sum S_L 2^(beta (L_a - L)) < 2^53. At
-          // the end of a group (other than the last) its exact value
-          // T 2^(-beta L_a) is added to D in float64; the last group is
-          // finished by the output pass below.
-          const int G = p.group;
-          const int gpos = (s + 1 - L) % G;
-          const int La = L + gpos;
-          const bool gend = (gpos == G - 1) && (L != 2);
-          const bool first_group = (s + 1 - L) < G;
-          const double gscale = ldexp(1.0, -p.beta * La);
+          const int nkb = npairs_of(L, s) * KT;
+          const int nch = (nkb + CH - 1) / CH;
+          for (int ch = 0; ch < nch && ok; ++ch) ok = drain_chunk();
+          if (!ok) break;
+          if (p.epi.kind == EPI_LEVELS && p.mats == nullptr) {
+            // test hook: write the exact level sum itself
+            const int64_t r = m0 + row;
+            if (r < p.m) {
 #pragma unroll
-          for (int g = 0; g < COLS / 8; ++g) {
-            long long told[8];
-            if (gpos > 0) {
-#pragma unroll
-              for (int t = 0; t < 8; ++t) told[t] = ld_keep(scr_i + 32 * (8 * g + t), pol);
+              for (int c = 0; c < COLS; ++c) {
+                const int64_t col = n0 + cbase + c;
+                if (col < p.n) p.epi.levels[static_cast<int64_t>(L - 2) * p.m * p.n + r * p.n + col] = S[c];
+              }
             }
+            continue;
+          }
+          // ---- fold the exact level sum (groups of levels, smallest first; see the header)
+          {
+            const uint64_t pol = policy_evict_last();
+            // up to G consecutive levels (G = 4 for beta 7 and 5, 3 for beta 8)
+            // combine exactly in int64, T = sum S_L 2^(beta (L_a - L)) < 2^53; the
+            // first level of a group stores its sum, the others add theirs at L2
+            // (red: nothing comes back, so the fold costs no round trip). With at
+            // most two groups each has its own area (group 0 in scr_i, group 1 in
+            // scr_d) and both are finished by the output pass. With three or more,
+            // scr_i holds the running group: at the end of a group (other than the
+            // last) its exact value T 2^(-beta L_a) is read back and added to D
+            // (scr_d) in float64.
+            const int G = p.group;
+            const int gpos = (s + 1 - L) % G;
+            const int gidx = (s + 1 - L) / G;
+            const bool two_areas = s <= 2 * G;
+            long long* area = (two_areas && gidx == 1) ? scr_d : scr_i;
+            const bool gend = !two_areas && (gpos == G - 1) && (L != 2);
+            const int La = L + gpos;
+            const bool first_group = gidx == 0;
+            const double gscale = ldexp(1.0, -p.beta * La);
+            const long long wgt = 1ll << (p.beta * gpos);
+            if (!gend) {
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              const int c = 8 * g + t;
-              const long long T = (gpos > 0 ? told[t] : 0ll) + static_cast<long long>(S[c]) * (1ll << (p.beta * gpos));
-              if (!gend) {
-                st_keep(scr_i + 32 * c, T, pol);
-              } else {
-                const double gv = static_cast<double>(T) * gscale;
-                const double d = first_group ? gv : __longlong_as_double(ld_keep(scr_d + 32 * c, pol)) + gv;
-                st_keep(scr_d + 32 * c, __double_as_longlong(d), pol);
+              for (int c = 0; c < COLS; ++c) {
+                const long long v = static_cast<long long>(S[c]) * wgt;
+                if (gpos == 0) {
+                  st_keep(area + 32 * c, v, pol);
+                } else {
+                  red_add_keep(area + 32 * c, v, pol);
+                }
+              }
+            } else {
+#pragma unroll
+              for (int g = 0; g < COLS / 8; ++g) {
+                long long told[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) told[t] = ld_l2(scr_i + 32 * (8 * g + t), pol);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                  const int c = 8 * g + t;
+                  const long long T = told[t] + static_cast<long long>(S[c]) * wgt;
+                  const double gv = static_cast<double>(T) * gscale;
+                  const double d = first_group ? gv : __longlong_as_double(ld_l2(scr_d + 32 * c, pol)) + gv;
+                  st_keep(scr_d + 32 * c, __double_as_longlong(d), pol);
+                }
               }
             }
           }
+          if (L != 2) continue;
+          // ---- last level: unscale and apply the output step
+          const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
+          output_tile(jb, m0, n0, s, scr_i, scr_d);
         }
-        if (L != 2) continue;
-        // ---- last level: unscale and apply the output step
-        const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
-        const int64_t r = m0 + row;
-        if (r >= jb.m) continue;
-        const int32_t er = jb.ea[r];
-        const bool upd = jb.epi.kind == EPI_PM_UPDATE;
-        const double wa = upd ? jb.epi.state->alpha : 0.0;
-        const double w2 = upd ? jb.epi.state->b2 : 0.0;
-        const double w3 = upd ? jb.epi.state->b3 : 0.0;
-        // last group (levels 2 .. L_a, L_a = 2 + (s - 1) mod G); earlier groups are in D
-        const double lscale = ldexp(1.0, -p.beta * (2 + (s - 1) % p.group));
-        const bool has_d = s > p.group;
-        const uint64_t pol = policy_evict_last();
-        double* Cout = jb.epi.C;
-        const int64_t ldc = jb.epi.ldc;
-        // batches of 8 columns: issue every load of the batch, then compute and store
-        for (int g = 0; g < COLS / 8; ++g) {
-          const int64_t col0 = n0 + cbase + 8 * g;
-          if (col0 >= jb.n) break;
-          long long ti[8], td[8];
-          double pv[8], xv[8];
-          int32_t ecv[8];
+      }
+    } else if (u_begin < u_end) {
+      // ---- the split: (tile, level) runs of this CTA's range, each drained
+      // into S and added at L2 to the tile's group sums (at most two groups,
+      // areas zeroed before the launch); leaving a tile counts this warp in
+      // for it, and the last of the tile's contributors writes this warp's
+      // part of the output
+      const uint64_t pol = policy_evict_last();
+      const int s = p.s;
+      const int G = p.group;
+      const int64_t units_per_tile = p.split_unit_count;
+      // CTA (pair) that owns unit u
+      auto owner = [&](int64_t u) __attribute__((always_inline)) -> int64_t {
+        return ((u + 1) * cta_stride + split_units - 1) / split_units - 1;
+      };
+      // tiles whose output this warp writes, after its whole range (a range
+      // shorter than a tile meets at most two tiles)
+      int out_tiles[2] = {-1, -1};
+      int n_out = 0;
+      // the tiles this range meets, level by level as whole tiles are walked;
+      // level L of tile tt holds units [base, base + nch_L) of the launch
+      const int tt_lo = static_cast<int>(u_begin / units_per_tile);
+      const int tt_hi = static_cast<int>((u_end - 1) / units_per_tile);
+      for (int tt = tt_lo; tt <= tt_hi && ok; ++tt) {
+        int base = static_cast<int>(static_cast<int64_t>(tt) * units_per_tile);
+        for (int L = s + 1; L >= 2 && ok; --L) {
+          const int nch_l = (npairs_of(L, s) * KTS_ + CHS_ - 1) / CHS_;
+          const int lo = max(base, static_cast<int>(u_begin));
+          const int hi = min(base + nch_l, static_cast<int>(u_end));
+          base += nch_l;
+          if (lo >= hi) continue;
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int c = 8 * g + t;
-            const int64_t col = col0 + t;
-            const bool ok = col < jb.n;
-            ti[t] = ld_keep(scr_i + 32 * c, pol);
-            td[t] = has_d ? ld_keep(scr_d + 32 * c, pol) : 0ll;
-            ecv[t] = ok ? jb.eb[col] : 0;
-            // P and P^2 are exactly symmetric: read them at (col, r), coalesced across the warp
-            pv[t] = (upd && ok) ? jb.epi.P[col * jb.epi.ldp + r] : 0.0;
-            xv[t] = (upd && ok) ? jb.epi.X2[col * jb.epi.ldx + r] : 0.0;
-          }
+          for (int c = 0; c < COLS; ++c) S[c] = 0;
+          for (int ch = lo; ch < hi && ok; ++ch) ok = drain_chunk();
+          if (!ok) break;
+          const int gpos = (s + 1 - L) % G;
+          long long* area = split_area_of(tt, (s + 1 - L) / G);
+          const long long wgt = 1ll << (p.beta * gpos);
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int64_t col = col0 + t;
-            if (col >= jb.n) break;
-            if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
-            const double acc = has_d ? __longlong_as_double(td[t]) + static_cast<double>(ti[t]) * lscale
-                                     : static_cast<double>(ti[t]) * lscale;
-            double v = (er == kBadExp || ecv[t] == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                            : scale_pow2(acc, er + ecv[t]);
-            if (upd) v = wa * pv[t] + w2 * xv[t] + w3 * v;
-            v = stored_value(v, jb.epi.round32 != 0);
-            Cout[r * ldc + col] = v;
-            if (jb.sym && r < col) Cout[col * ldc + r] = v;
-          }
+          for (int c = 0; c < COLS; ++c) red_add_keep(area + 32 * c, static_cast<long long>(S[c]) * wgt, pol);
+        }
+        if (!ok) break;
+        __threadfence();  // this lane's reductions before the count
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+          // the CTAs (pairs) whose non-empty ranges meet this tile (with fewer
+          // units than CTAs some ranges are empty)
+          const int64_t u0 = static_cast<int64_t>(tt) * units_per_tile;
+          int contributors = 0;
+          for (int64_t c = owner(u0); c <= owner(u0 + units_per_tile - 1); ++c)
+            contributors += (split_units * (c + 1) / cta_stride > split_units * c / cta_stride) ? 1 : 0;
+          int* cnt = p.split_cnt + (static_cast<int64_t>(tt) * (PAIR ? 2 : 1) + rank) * TC_EPI_WARPS + e;
+          last = atomicAdd(cnt, 1) == contributors - 1 ? 1 : 0;
+        }
+        if (__shfl_sync(0xffffffffu, last, 0) != 0 && n_out < 2) out_tiles[n_out++] = tt;
+      }
+      if (ok && n_out > 0) {
+        __threadfence();  // every contributor's reductions before the reads
+        for (int k = 0; k < n_out; ++k) {
+          const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, out_tiles[k], rank);
+          output_tile(jb, jb.m0, jb.n0, s, split_area_of(out_tiles[k], 0), split_area_of(out_tiles[k], 1));
         }
       }
     }
@@ -908,23 +1120,21 @@ bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int6
 
 namespace {
 
-template <int BN, bool PAIR, bool F8 = false>
+// Set before every launch rather than once per process: the attribute belongs
+// to the kernel as loaded in the current context, and a context created anew
+// (after cudaDeviceReset) starts from the default limit. The call is host-side
+// only and costs about a microsecond against milliseconds of kernel.
+template <int BN, bool PAIR, bool F8 = false, bool SPLIT = false>
 cudaError_t set_smem_attr() {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(ozaki_tc_kernel<BN, PAIR, F8>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, PAIR, F8>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  return cudaSuccess;
+  return cudaFuncSetAttribute(ozaki_tc_kernel<BN, PAIR, F8, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              TcCfg<BN, PAIR, F8>::SMEM);
 }
 
-template <int BN, bool PAIR = false, bool F8 = false>
+template <int BN, bool PAIR = false, bool F8 = false, bool SPLIT = false>
 cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& p, int grid,
                            cudaStream_t st) {
   using Cfg = TcCfg<BN, PAIR, F8>;
-  cudaError_t e = set_smem_attr<BN, PAIR, F8>();
+  cudaError_t e = set_smem_attr<BN, PAIR, F8, SPLIT>();
   if (e != cudaSuccess) return e;
   if (PAIR) {
     cudaLaunchConfig_t cfg;
@@ -940,16 +1150,20 @@ cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const T
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, PAIR, F8>, ta, tb, p);
+    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, PAIR, F8, SPLIT>, ta, tb, p);
     if (e != cudaSuccess) return e;
   } else {
-    ozaki_tc_kernel<BN, PAIR, F8><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
+    ozaki_tc_kernel<BN, PAIR, F8, SPLIT><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
   }
   count_launch();
   return cudaGetLastError();
 }
 
 bool g_pairing = true;
+
+// One-shot stall test (dmp_test_stall_next_product): wait limit in microseconds
+// for the next tcgen05 product launch, 0 = off.
+std::atomic<int> g_stall_us{0};
 
 // CTA pairs of the PAIR kernel that can be resident at once (0: none)
 int tc_max_pairs() {
@@ -980,6 +1194,12 @@ int tc_max_pairs() {
 
 }  // namespace
 
+int set_stall_test(int wait_limit_us) {
+  if (wait_limit_us < 0) return DMP_ERR_INVALID_ARG;
+  g_stall_us.store(wait_limit_us);
+  return DMP_OK;
+}
+
 int set_tc_pairing(int enable) {
   const int prev = g_pairing ? 1 : 0;
   g_pairing = enable != 0;
@@ -999,9 +1219,28 @@ int tc_max_ctas() {
 
 size_t tc_scratch_bytes() { return static_cast<size_t>(kTcMaxCtas) * 2 * TC_BM * 256 * sizeof(double); }
 
+// Split launches: fewer than kTcMaxCtas / 2 tiles of one CTA (or kTcMaxCtas / 4
+// of a CTA pair, two row halves each), each with two TC_BM x 256 int64 group
+// sums per CTA, then one counter per (tile, CTA, epilogue warp).
+static size_t tc_split_area_bytes() {
+  return static_cast<size_t>(kTcMaxCtas / 2) * 2 * TC_BM * 256 * sizeof(long long);
+}
+size_t tc_split_bytes() {
+  return tc_split_area_bytes() + static_cast<size_t>(kTcMaxCtas / 2) * TC_EPI_WARPS * sizeof(int);
+}
+
+bool g_split_tiles = true;
+
+int set_tc_split_tiles(int enable) {
+  const int prev = g_split_tiles ? 1 : 0;
+  g_split_tiles = enable != 0;
+  return prev;
+}
+
 cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, const int32_t* eb, int64_t m,
                             int64_t n, int64_t rows_a, int64_t rows_b, int64_t k_pad, int s, int beta, int sym,
-                            const EpiArgs& epi, const int* done, int* err, double* scratch, cudaStream_t st) {
+                            const EpiArgs& epi, const int* done, int* err, double* scratch, void* split_ws,
+                            cudaStream_t st) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   const bool f8 = beta == 5;  // E4M3 nearest digits
   const int BN = 256;
@@ -1047,6 +1286,16 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   p.done = done;
   p.err = err;
   p.timeout_ns = 5000000000ull;
+  p.stall_test = 0;
+  // the stall test is taken by a launch that runs now, never by one being
+  // captured into a graph (every replay would stall)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+    if (const int us = g_stall_us.exchange(0); us > 0) {
+      p.stall_test = 1;
+      p.timeout_ns = 1000ull * static_cast<unsigned long long>(us);
+    }
+  }
   int ntiles = 0;
   if (sym) {
     for (int bj = 0; bj < p.tiles_n; ++bj) ntiles += std::min(p.tiles_m, (BN * (bj + 1)) / BM);
@@ -1055,12 +1304,53 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   }
   p.ntiles = ntiles;
   p.scratch = scratch;
+  // split: when the tiles fill at most half a wave of CTAs (CTA pairs), they
+  // are all cut into fp32-chunk units shared out evenly over every CTA, so the
+  // idle part of the wave works too. Needs at most two level groups (their
+  // sums are then finished in the output pass) and the caller's split
+  // workspace. Measured on GB300 (INT8, s = 5 with an 8-slice refinement):
+  // 10 pair tiles (n = 1024) 0.197 -> 0.117 ms per product, 36 (n = 2048) 0.273
+  // -> 0.204 ms, but 66 of 74 pairs (n = 2816) 0.339 -> 0.443 ms: the units'
+  // L2 reductions then cost more than the few idle pairs; sharing out only the
+  // last partial wave of a larger launch measured slower as well (n >= 4096).
+  const int units = pair ? tc_max_pairs() : tc_max_ctas();
+  p.split_unit_count = 0;
+  p.split_area = nullptr;
+  p.split_cnt = nullptr;
+  const bool split =
+      g_split_tiles && split_ws != nullptr && 2 * ntiles <= units && s <= 2 * p.group && epi.kind != EPI_LEVELS;
+  if (split) {
+    const int ranks = pair ? 2 : 1;
+    const int KSUB = pair ? 2 : 1;
+    const int kts = p.KT / KSUB, chs = p.CH / KSUB;
+    int cnt = 0;
+    for (int L = s + 1; L >= 2; --L) {
+      const int np = std::min(s, L - 1) - std::max(1, L - s) + 1;
+      cnt += (np * kts + chs - 1) / chs;
+    }
+    p.split_unit_count = cnt;
+    p.split_area = static_cast<long long*>(split_ws);
+    p.split_cnt = reinterpret_cast<int*>(static_cast<char*>(split_ws) + tc_split_area_bytes());
+    // the tiles' group sums and counters start from zero
+    const size_t area = static_cast<size_t>(ntiles) * ranks * 2 * TC_BM * 256 * sizeof(long long);
+    cudaError_t e = cudaMemsetAsync(split_ws, 0, area, st);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(p.split_cnt, 0, static_cast<size_t>(ntiles) * ranks * TC_EPI_WARPS * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
   ProfScope prof(DMP_PROF_PRODUCT, st);
+  const int grid_units = split ? units : std::min(ntiles, units);
   if (pair) {
-    const int grid = 2 * std::min(ntiles, tc_max_pairs());
+    const int grid = 2 * grid_units;
+    if (split)
+      return f8 ? launch_tc_impl<256, true, true, true>(ta, tb, p, grid, st)
+                : launch_tc_impl<256, true, false, true>(ta, tb, p, grid, st);
     return f8 ? launch_tc_impl<256, true, true>(ta, tb, p, grid, st) : launch_tc_impl<256, true>(ta, tb, p, grid, st);
   }
-  const int grid = std::min(ntiles, tc_max_ctas());
+  const int grid = grid_units;
+  if (split)
+    return f8 ? launch_tc_impl<256, false, true, true>(ta, tb, p, grid, st)
+              : launch_tc_impl<256, false, false, true>(ta, tb, p, grid, st);
   return f8 ? launch_tc_impl<256, false, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
 }
 

@@ -9,7 +9,6 @@ library is missing or no GPU is present, the calls raise.
 from __future__ import annotations
 
 import ctypes
-import time
 import os
 
 import torch
@@ -84,6 +83,9 @@ SIGNATURES = {
     "dmp_tape_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
     "dm_purify": (ctypes.c_int, [_vp, _i64, _i64, _i64, ctypes.POINTER(Opts), _vp, _i64,
                                  ctypes.POINTER(Info), _vp, _sz, _vp, _sz, _vp]),
+    "dmp_host_workspace_size": (ctypes.c_int, [_i64, ctypes.POINTER(Opts), _szp]),
+    "dm_purify_host": (ctypes.c_int, [_vp, _i64, _i64, _i64, ctypes.POINTER(Opts), _vp, _i64,
+                                      ctypes.POINTER(Info), _vp, _sz, _vp]),
     "ozaki_gemm_workspace_size": (ctypes.c_int, [_i64, _i64, _i64, _i32, _i32, _i32, _szp]),
     "ozaki_gemm": (ctypes.c_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _i32, _i32,
                                   _vp, _sz, _vp]),
@@ -109,6 +111,8 @@ SIGNATURES = {
     "dmp_launch_count": (ctypes.c_longlong, []),
     "dmp_version": (ctypes.c_char_p, []),
     "dmp_set_tc_pairing": (ctypes.c_int, [ctypes.c_int]),
+    "dmp_test_stall_next_product": (ctypes.c_int, [_i32]),
+    "dmp_set_tc_split_tiles": (ctypes.c_int, [ctypes.c_int]),
 }
 
 
@@ -143,6 +147,20 @@ def set_tc_pairing(enable: bool) -> bool:
     """Run tcgen05 beta = 7 products on CTA pairs (2-SM MMA, the default) or on
     single CTAs (dmp_set_tc_pairing). Returns the previous setting."""
     return bool(lib().dmp_set_tc_pairing(1 if enable else 0))
+
+
+def set_tc_split_tiles(enable: bool) -> bool:
+    """Split the last partial wave of tcgen05 product tiles into chunk units
+    shared by every CTA (dmp_set_tc_split_tiles; on by default). Returns the
+    previous setting."""
+    return bool(lib().dmp_set_tc_split_tiles(1 if enable else 0))
+
+
+def test_stall_next_product(wait_limit_us: int) -> None:
+    """Test hook (dmp_test_stall_next_product): the next tcgen05 product launch
+    withholds its first operand stage and bounds its waits by wait_limit_us, so
+    its call returns DMP_ERR_TIMEOUT through the kernel's abort path."""
+    _check(lib().dmp_test_stall_next_product(int(wait_limit_us)), "dmp_test_stall_next_product")
 
 
 PROF_PRODUCT, PROF_SPLIT, PROF_MEASURE, PROF_INIT, PROF_OTHER = 0, 1, 2, 3, 4
@@ -244,24 +262,40 @@ def purify(H: torch.Tensor, n_occ: int, mode="int8", slices=7, executor="auto", 
     return P, info.as_dict()
 
 
-def purify_host(H_host: torch.Tensor, n_occ: int, out: torch.Tensor | None = None, timings: dict | None = None,
-                **kw):
-    """End-to-end call from host memory: copies H to the device, purifies, and
-    copies P back into `out` (a host tensor; pinned memory keeps the copies at
-    full PCIe/C2C speed). Returns (P on the host, info). `timings`, if given,
-    receives the host-clock seconds of the copy in plus the purification (which
-    synchronises) and of the copy out."""
-    t0 = time.perf_counter()
-    H = H_host.to("cuda", non_blocking=True)
-    P, info = purify(H, n_occ, **kw)
-    t1 = time.perf_counter()
+def host_workspace_bytes(n: int, opts: Opts) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().dmp_host_workspace_size(n, ctypes.byref(opts), ctypes.byref(b)), "dmp_host_workspace_size")
+    return b.value
+
+
+def purify_host(H_host: torch.Tensor, n_occ: int, out: torch.Tensor | None = None, ws=None, stream=None,
+                mode="int8", slices=7, executor="auto", tol=1e-10, energy_tol=0.0, max_iter=100, refine=0,
+                method="pm", fp32_storage=False, late_slices=0, late_idem=0.0):
+    """dm_purify_host: H and P in host memory, both copies made by the library
+    on its stream (one cudaMemcpy2DAsync each way). `H_host` is a float64 CPU
+    tensor (pinned memory keeps the copies at full link speed); `out`, a host
+    tensor of the same shape, receives P (allocated, pinned like H_host, when
+    not given). `ws` is a device workspace of host_workspace_bytes bytes.
+    Returns (P on the host, info dict)."""
+    if not (isinstance(H_host, torch.Tensor) and not H_host.is_cuda and H_host.dtype == torch.float64):
+        raise TypeError("expected a float64 host tensor")
+    if H_host.dim() != 2 or H_host.stride(1) != 1:
+        raise ValueError("H_host must be a row-major matrix")
+    n = H_host.shape[0]
+    opts = make_opts(mode, slices, executor, tol, energy_tol, max_iter, 8, refine, method, fp32_storage,
+                     late_slices, late_idem)
     if out is None:
-        out = torch.empty(P.shape, dtype=P.dtype, pin_memory=H_host.is_pinned())
-    out.copy_(P, non_blocking=False)
-    if timings is not None:
-        timings["in_and_purify"] = t1 - t0
-        timings["out"] = time.perf_counter() - t1
-    return out, info
+        out = torch.empty((n, n), dtype=torch.float64, pin_memory=H_host.is_pinned())
+    if out.is_cuda or out.dtype != torch.float64 or out.stride(1) != 1 or tuple(out.shape) != (n, n):
+        raise ValueError("out must be an n x n row-major float64 host tensor")
+    if ws is None:
+        ws = workspace(host_workspace_bytes(n, opts))
+    info = Info()
+    code = lib().dm_purify_host(H_host.data_ptr(), n, H_host.stride(0), int(n_occ), ctypes.byref(opts),
+                                out.data_ptr(), out.stride(0), ctypes.byref(info), ws.data_ptr(), ws.numel(),
+                                _stream_ptr(stream))
+    _check(code, "dm_purify_host", allow_status=True)
+    return out, info.as_dict()
 
 
 def foe_params(kT: float, n_terms: int, mu: float | None = None, n_occ: int | None = None, bounds=None,
