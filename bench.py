@@ -67,8 +67,17 @@ def parse_args():
                     help="purify: the n=8192 benchmark; batch64: the 64-matrix batched workload")
     ap.add_argument("--batch-mode", default="int8", choices=["int8", "bf16", "e4m3"],
                     help="slice mode of the batch64 workload")
+    ap.add_argument("--batched", choices=("on", "off"), default="on",
+                    help="also time the 64-matrix batched workload (dm_purify_batched) and report it as `batched`")
     ap.add_argument("--foe", choices=("on", "off"), default="on",
                     help="also time the finite-temperature expansion (dm_foe) on the same H, once")
+    ap.add_argument("--oracle-full", choices=("on", "off"), default="on",
+                    help="run the FP64 oracle purification whole on the host cores once (rank 0, N = 1): its "
+                         "wall time is reported as cpu_baseline.fp64_oracle and its P is the reference of "
+                         "config.parity_vs_oracle")
+    ap.add_argument("--oracle-budget", type=float, default=600.0,
+                    help="skip the whole-oracle run when its projected time (from one timed host product) "
+                         "exceeds this many seconds")
     ap.add_argument("--gen", default="device", choices=["device", "host"],
                     help="where the QR of the input generator runs (host: numpy, for profiler runs)")
     return ap.parse_args()
@@ -388,31 +397,30 @@ def run_ours(args):
         _, info = step()
     torch.cuda.synchronize()
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the C ABI with host buffers: dm_purify_host copies H
+    # in and P out on the library's stream, both inside the timed call
     H_host = H.to("cpu").pin_memory()
     P_host = torch.empty_like(H_host).pin_memory()
+    ws_host = dmp.workspace(dmp.host_workspace_bytes(n, dmp.make_opts(mode, s, args.executor, refine=refine)), dev)
     e2e_times = []
     # (measured after the warm-up steps and before the timed region, so that both
-    # run in the same warm state of the GPU; the first call through the host path,
-    # whose device copy of H comes from torch's caching allocator, is untimed)
-    dmp.purify_host(H_host, n_occ, out=P_host, mode=mode, slices=s, executor=args.executor, ws=ws, P=P,
+    # run in the same warm state of the GPU; the first host call is untimed)
+    dmp.purify_host(H_host, n_occ, out=P_host, ws=ws_host, mode=mode, slices=s, executor=args.executor,
                     refine=refine)
     torch.cuda.synchronize()
-    e2e_parts = []
     for _ in range(max(args.e2e_steps, 1)):
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        parts = {}
-        dmp.purify_host(H_host, n_occ, out=P_host, mode=mode, slices=s, executor=args.executor, ws=ws, P=P,
-                        refine=refine, timings=parts)
-        torch.cuda.synchronize()
+        _, e2e_info = dmp.purify_host(H_host, n_occ, out=P_host, ws=ws_host, mode=mode, slices=s,
+                                      executor=args.executor, refine=refine)
         e2e_times.append(time.perf_counter() - t0)
-        e2e_parts.append(parts)
-    med = sorted(range(len(e2e_times)), key=lambda i: e2e_times[i])[len(e2e_times) // 2]
     e2e = {"value": max_over_ranks(statistics.median(e2e_times), dev), "unit": UNIT,
-           "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8,
-           "runs_s": e2e_times, "median_run_parts_s": e2e_parts[med]}
+           "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8, "runs_s": e2e_times,
+           "call": "dm_purify_host (C ABI): pinned host H in, pinned host P out, one cudaMemcpy2DAsync each way "
+                   "on the library's stream, synchronised before return; host clock around the call",
+           "matches_device_call": bool(torch.equal(P_host, P.cpu()))}
+    del ws_host
 
     # ---- timed region: K full purifications, H resident in HBM (512 MiB > L2)
     dmp.profile_enable(True)
@@ -433,6 +441,7 @@ def run_ours(args):
         infos.append(info)
     ev1.record(stream)
     torch.cuda.synchronize()
+    P_head = P.clone()  # the returned P of the headline setting (later sections reuse P)
     barrier()
     launches = dmp.launch_count() - launches0
     clk = clocks.stop() if clocks else None
@@ -668,6 +677,12 @@ def run_ours(args):
                                  "128th row)"})
         del ws_f, P_f, Q_d
 
+    # ---- the batched workload (64 Hamiltonians of n = 128..1536 in one graph
+    # launch): reported beside the headline, not the metric
+    batched = None
+    if args.batched == "on" and not args.slices:
+        batched = batched_leg(dmp, "int8")
+
     # ---- FP64 purification on the same GPU (once)
     fp64 = None
     if args.fp64 == "full":
@@ -714,11 +729,53 @@ def run_ours(args):
                             "sample": f"one {n}x{n} by {n}x{blk} FP64 product on the host, scaled to "
                                       f"{products} full products (the purification's product count)"}
 
+    # ---- the FP64 oracle run whole on the host cores (rank 0, N = 1): a measured
+    # CPU baseline of the purification, and the reference the headline's returned
+    # P is compared with element by element (Sec. "Error Evaluation Criteria",
+    # K = 2P). Skipped when one timed host product projects past the budget.
+    parity = None
+    if rank == 0 and world == 1 and args.oracle_full == "on":
+        import numpy as np
+
+        from oracle import purify as pu
+
+        H_np = H.cpu().numpy()
+        t0 = time.perf_counter()
+        np.dot(H_np, H_np)
+        t_prod = time.perf_counter() - t0
+        o_iters = oracle_iterations(H_np, n_occ, h.e, 1e-10)
+        projected = (2 * o_iters + 1) * t_prod * 1.15
+        if projected > args.oracle_budget:
+            parity = {"skipped": f"projected {projected:.0f} s (from one {n}x{n} host product of {t_prod:.2f} s) "
+                                 f"exceeds the budget of {args.oracle_budget:.0f} s"}
+        else:
+            t0 = time.perf_counter()
+            ref = pu.purify(H_np, n_occ, tol=1e-10)
+            t_oracle = time.perf_counter() - t0
+            m = pu.error_metrics(P_head.cpu().numpy(), H_np, P_ref=ref["P"], E_ref=ref["energy"])
+            parity = {"setting": f"ozaki-{mode} s={s}" + (f" + refinement ({refine} slices)" if refine else ""),
+                      "max_abs": m["max_abs"], "rmsd": m["rmsd"], "commutator": m["commutator"],
+                      "idempotency_returned": m["idempotency"], "rel_energy_vs_oracle": m["rel_energy"],
+                      "rel_energy_vs_exact": rel_energy, "oracle_iters": ref["iters"],
+                      "oracle_status": ref["status_name"],
+                      "oracle_rel_energy_vs_exact": abs(ref["energy"] - E_star) / abs(E_star),
+                      "note": "returned P of the timed setting vs the FP64 oracle's P on the same H, every "
+                              "element; RMSD = ||K - K_oracle||_F / n and commutator ||HK - KH||_F with K = 2P"}
+            if cpu is not None:
+                cpu["fp64_oracle"] = {"value": t_oracle, "unit": UNIT, "cores": os.cpu_count(),
+                                      "kind": "oracle, FP64 products, run whole (measured, not extrapolated)",
+                                      "iters": ref["iters"]}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "e4m3" if mode == "e4m3" else "bf16", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": ("ozaki-e4m3 (5-bit digits carried in e4m3, exact fp32 chunk sums, int32/int64 level sums, "
+                      "fp64 recombination)" if mode == "e4m3" else
+                      "ozaki-int8 (7-bit digits carried in bf16, exact fp32 chunk sums, int32/int64 level sums, "
+                      "fp64 recombination)"),
+            "data": "synthetic",
             "config": {"workload": workload_name(w), "mode": f"ozaki-{mode}", "slices": s, "executor": args.executor,
                        "refinement": ("one McWeeny step after the loop (Sec. Precision Requirements Sweep) with "
                                       f"Ozaki products of {refine} slices" if refine > 0 else
@@ -732,6 +789,7 @@ def run_ours(args):
                        "l2": (f"inputs larger than L2 (H {n * n * 8 / 2**20:.0f} MiB, digit planes "
                               f"{2 * s * n * n * (1 if mode == 'e4m3' else 2) / 2**30:.2f} GiB)"),
                        "slice_tuning": tune,
+                       "parity_vs_oracle": parity,
                        "replicas": world},
             "roofline": roofline,
             "fp64_equivalent": fp64_equivalent,
@@ -740,6 +798,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk,
             "fp64_reference": fp64,
+            "batched": batched,
             "phases_ms_per_step": {"products": prod_ms / args.steps, "splits": split_ms / args.steps,
                                    "measures": meas_ms / args.steps, "init": init_ms / args.steps},
         }
@@ -749,56 +808,76 @@ def run_ours(args):
     return 0
 
 
-def run_batch64(args):
-    """64 Hamiltonians, n = 32 U{4..48}, n_occ = n/4, gap 0.2: dm_purify_batched
-    (one graph launch, autotuned s and tile width) against 64 sequential
-    dm_purify calls at the same s. One JSON line; not the benchmark metric."""
+def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True):
+    """The batched workload: 64 Hamiltonians, n = 32 U{4..48}, n_occ = n/4, gap
+    0.2, through dm_purify_batched (one graph launch, slice count and tile width
+    from the library's autotuner), against 64 sequential dm_purify calls at the
+    same s. Returns a dict with both times, the slice-pair work and its rate
+    against the measured sustained bf16 peak (E4M3: twice that)."""
     import numpy as np
     import torch
 
-    from paper_2407_13299_gb300 import build as _build
-    from paper_2407_13299_gb300 import dmp
     from synth import batch_sizes, make_hamiltonian
 
-    _build.build()
     sizes = batch_sizes()
     hs = [make_hamiltonian(n, o, occ=(-2.0, -0.1), virt=(0.1, 2.0), seed=sd) for n, o, sd in sizes]
     Hs = [torch.from_numpy(h.H).cuda() for h in hs]
     occ = [o for _, o, _ in sizes]
-    mode = args.batch_mode
     opts = dmp.make_opts(mode, 7, "tc")
     opts.slices = 0
     ws = dmp.workspace(dmp.batched_workspace_bytes([h.n for h in hs], opts))
     Ps = [torch.empty_like(H) for H in Hs]
     _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)  # tunes and builds the graph
     s = infos[0]["slices_used"]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)
     b.record()
     torch.cuda.synchronize()
-    t_batch = a.elapsed_time(b) / 1e3 / args.steps
-    wss = dmp.workspace(dmp.purify_workspace_bytes(max(h.n for h in hs), dmp.make_opts(mode, s, "tc")))
-    for H, o, P in zip(Hs, occ, Ps):
-        dmp.purify(H, o, mode=mode, slices=s, executor="tc", P=P, ws=wss)
-    torch.cuda.synchronize()
-    a.record()
-    for H, o, P in zip(Hs, occ, Ps):
-        dmp.purify(H, o, mode=mode, slices=s, executor="tc", P=P, ws=wss)
-    b.record()
-    torch.cuda.synchronize()
-    t_seq = a.elapsed_time(b) / 1e3
-    errs = [abs(i["energy"] - float(np.sum(h.e[:h.n_occ]))) / abs(float(np.sum(h.e[:h.n_occ])))
-            for i, h in zip(infos, hs)]
-    print(json.dumps({"workload": "batch64: 64 H, n = 32 U{4..48}, n_occ = n/4, gap 0.2",
-                      "mode": f"ozaki-{mode}",
-                      "slices": s, "batched_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
-                      "max_rel_energy_error": max(errs), "iters_max": max(i["iters"] for i in infos),
-                      "steps": args.steps, "warmup": args.warmup}), flush=True)
+    t_batch = a.elapsed_time(b) / 1e3 / steps
+    out = {"workload": "batch64: 64 H, n = 32 U{4..48}, n_occ = n/4, gap 0.2", "mode": f"ozaki-{mode}",
+           "slices": s, "value": t_batch, "unit": UNIT}
+    # slice-pair work: per matrix 2 iters + 1 symmetric products of p n^2 (n + 1)
+    p_s = s * (s + 1) // 2
+    flops = sum((2 * i["iters"] + 1) * p_s * h.n * h.n * (h.n + 1) for i, h in zip(infos, hs))
+    peaks, _ = load_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])) * \
+        (2.0 if mode == "e4m3" else 1.0)
+    out.update({"slice_pair_flops": flops, "achieved_tflops": flops / t_batch / 1e12, "peak_tflops": peak,
+                "frac": flops / t_batch / 1e12 / peak,
+                "frac_note": "whole batched call (splits, measures and padding included) against the measured "
+                             "sustained bf16 peak" + (" x 2 (fp8)" if mode == "e4m3" else ""),
+                "iters_max": max(i["iters"] for i in infos),
+                "max_rel_energy_error": max(abs(i["energy"] - float(np.sum(h.e[:h.n_occ]))) /
+                                            abs(float(np.sum(h.e[:h.n_occ]))) for i, h in zip(infos, hs))})
+    if sequential:
+        wss = dmp.workspace(dmp.purify_workspace_bytes(max(h.n for h in hs), dmp.make_opts(mode, s, "tc")))
+        for H, o, P in zip(Hs, occ, Ps):
+            dmp.purify(H, o, mode=mode, slices=s, executor="tc", P=P, ws=wss)
+        torch.cuda.synchronize()
+        a.record()
+        for H, o, P in zip(Hs, occ, Ps):
+            dmp.purify(H, o, mode=mode, slices=s, executor="tc", P=P, ws=wss)
+        b.record()
+        torch.cuda.synchronize()
+        out["sequential_s"] = a.elapsed_time(b) / 1e3
+        out["speedup_over_sequential"] = out["sequential_s"] / t_batch
+    return out
+
+
+def run_batch64(args):
+    """The batched workload alone, one JSON line (not the benchmark metric)."""
+    from paper_2407_13299_gb300 import build as _build
+    from paper_2407_13299_gb300 import dmp
+
+    _build.build()
+    out = batched_leg(dmp, args.batch_mode, steps=args.steps, warmup=args.warmup)
+    out.update({"steps": args.steps, "warmup": args.warmup})
+    print(json.dumps(out), flush=True)
     return 0
 
 
