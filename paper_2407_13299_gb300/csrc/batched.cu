@@ -131,7 +131,7 @@ __global__ void finish_grouped_kernel(const BatchMat* __restrict__ mats) {
 
 // ---------------------------------------------------------------- host side
 struct BatchLayout {
-  size_t mats, tiles, row_start, partials, err, scratch, tune_ws, total;
+  size_t mats, tiles, row_start, partials, err, counter, scratch, tune_ws, total;
   std::vector<size_t> state, rowbuf, expsP, expsX, buf1, X2, planesP, planesX;
   std::vector<int64_t> n_pad, k_pad;
   int ntiles;
@@ -167,6 +167,7 @@ BatchLayout batch_layout(int batch, const int64_t* n, int s_max, int beta) {
   L.row_start = c.take(sizeof(int64_t) * (batch + 1));
   L.partials = c.take(sizeof(double) * 8 * kMeasBlk * batch);
   L.err = c.take(sizeof(int));
+  L.counter = c.take(sizeof(int));
   L.scratch = c.take(tc_scratch_bytes());
   int64_t nmax = 2;
   for (int b = 0; b < batch; ++b) {
@@ -284,6 +285,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   int64_t* drow = reinterpret_cast<int64_t*>(at(ws, L.row_start));
   double* dpart = reinterpret_cast<double*>(at(ws, L.partials));
   int* derr = reinterpret_cast<int*>(at(ws, L.err));
+  int* dcounter = reinterpret_cast<int*>(at(ws, L.counter));
   double* scratch = reinterpret_cast<double*>(at(ws, L.scratch));
   const int64_t nmax_idx = std::max_element(n, n + batch) - n;
 
@@ -370,11 +372,16 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     }
     return true;
   };
+  // matrices by decreasing size: their tiles are listed largest first, so the
+  // CTAs that take tiles from the counter finish at about the same time
+  std::vector<int> by_size(batch);
+  for (int b = 0; b < batch; ++b) by_size[b] = b;
+  std::stable_sort(by_size.begin(), by_size.end(), [&](int x, int y) { return n[x] > n[y]; });
   auto build_tiles = [&](int tile_n, std::vector<int4>& out) {
     out.clear();
-    // column blocks outermost across all matrices (largest first), so CTAs
-    // running together work on the same matrix and share its B blocks
-    for (int b = 0; b < batch; ++b) {
+    // column blocks outermost within each matrix, so CTAs running together
+    // work on the same matrix and share its B blocks
+    for (int b : by_size) {
       const int tm = static_cast<int>(hm[b].n_pad / 128), tn = static_cast<int>(hm[b].n_pad / tile_n);
       for (int bj = 0; bj < tn; ++bj)
         for (int bi = 0; bi < std::min(tm, tile_n * (bj + 1) / 128); ++bi) out.push_back(make_int4(b, bi, bj, 0));
@@ -417,7 +424,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       DMP_CUDA(cudaEventCreate(&e1));
       DMP_CUDA(cudaEventRecord(e0, st));
       DMP_CUDA(launch_ozaki_tc_grouped(dmats, dtiles, static_cast<int>(htiles.size()), cand, tbeta, 0, 0, derr,
-                                       scratch, st));
+                                       scratch, dcounter, st));
       DMP_CUDA(cudaEventRecord(e1, st));
       DMP_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -479,10 +486,10 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     DMP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     for (int cur = 0; cur < 2; ++cur) {
       launch_split_grouped(dmats, drow, batch, hrow[batch], cur, tbeta, cs);
-      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, bn, tbeta, 0, cur, derr, scratch, cs);
+      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, bn, tbeta, 0, cur, derr, scratch, dcounter, cs);
       launch_measure_grouped(dmats, batch, cur, dpart, cond, 1, cs);
       launch_split_grouped(dmats, drow, batch, hrow[batch], 2, tbeta, cs);
-      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, bn, tbeta, 1, cur, derr, scratch, cs);
+      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, bn, tbeta, 1, cur, derr, scratch, dcounter, cs);
     }
     cudaGraph_t captured = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &captured);

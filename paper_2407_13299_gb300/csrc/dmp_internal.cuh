@@ -321,8 +321,10 @@ cudaError_t launch_measure_grouped(const BatchMat* mats, int nmats, int cur, dou
                                    cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st);
 cudaError_t launch_finish_grouped(const BatchMat* mats, int nmats, cudaStream_t st);
 // phase 0: X2 = P P from buf[cur]; phase 1: update buf[cur] -> buf[1 - cur].
+// `counter` (one int of device memory) is zeroed on the stream before the
+// launch; the CTAs take tiles from it in list order.
 cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, int beta,
-                                    int phase, int cur, int* err, double* scratch, cudaStream_t st);
+                                    int phase, int cur, int* err, double* scratch, int* counter, cudaStream_t st);
 
 }  // namespace dmp
 

@@ -52,6 +52,7 @@ constexpr int TC_ROW_BYTES = 128;  // bytes of one K block row (the swizzle atom
 constexpr int TC_MMA_PER_ATOM = 4;  // MMAs per K block: 32 bytes of K each (16 bf16 or 32 e4m3)
 constexpr int TC_THREADS = 320;
 constexpr int TC_EPI_WARPS = 8;
+constexpr int kTileRing = 4;  // WALK 2: tile indices the producer may announce ahead
 
 // PAIR: a cluster of two CTAs computes a 256 x BN tile with tcgen05.mma.cta_group::2;
 // each CTA stages its own 128 rows of A and half of the BN rows of B, and its
@@ -97,6 +98,7 @@ struct TcParams {
   // into split_unit_count units of one fp32 chunk, shared out in contiguous
   // ranges over all CTAs (CTA pairs)
   int split_unit_count;
+  int* tile_counter;  // WALK 2: next tile to take (zeroed before the launch)
   long long* split_area;  // per (tile, CTA rank in the pair): two TC_BM x BN int64 group sums
   int* split_cnt;         // per (tile, rank, epilogue warp): contributors counted in
   // grouped mode (batched purification): tiles of many matrices in one launch
@@ -475,13 +477,20 @@ __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA,
 // MMAs and its commits arrive on the stage and accumulator barriers of both
 // CTAs; both epilogues release a TMEM buffer on the leader's barrier.
 //
-// SPLIT: the launch's tiles fill at most half a wave of CTAs (CTA pairs), so
+// WALK: how the CTAs share the launch's tiles.
+//   0  each CTA (pair) takes tiles cta, cta + #CTAs, ... (the single-matrix products)
+//   2  each CTA takes the next tile from a counter in global memory (the
+//      grouped launches of the batched purification, whose tiles differ in
+//      work: listed largest first, taken as CTAs free up); the producer takes
+//      the tile and passes its index to the MMA and epilogue warps through a
+//      small ring in shared memory
+//   1  (split) the launch's tiles fill at most half a wave of CTAs (CTA pairs), so
 // they are all cut into units of one exact fp32 chunk and shared out evenly in
 // contiguous ranges over every CTA; each range's partial level sums are added
 // at L2 into the tiles' shared group sums, and the last contributor to a tile
 // writes its output. Integer sums do not depend on the split: the result is
 // bit-for-bit that of whole tiles.
-template <int BN, bool PAIR, bool F8 = false, bool SPLIT = false>
+template <int BN, bool PAIR, bool F8 = false, int WALK = 0>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const TcParams p) {
@@ -497,8 +506,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   auto accfull_bar = [&](int b) { return bar0 + 8u * (2 * Cfg::STAGES + b); };
   auto accempty_bar = [&](int b) { return bar0 + 8u * (2 * Cfg::STAGES + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * Cfg::STAGES + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 8 * (2 * Cfg::STAGES + 5));
+  // WALK 2: ring of tile indices from the producer to the MMA and epilogue warps
+  auto ring_full = [&](int r) { return bar0 + 8u * (2 * Cfg::STAGES + 5 + r); };
+  auto ring_empty = [&](int r) { return bar0 + 8u * (2 * Cfg::STAGES + 5 + kTileRing + r); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 8 * (2 * Cfg::STAGES + 5 + 2 * kTileRing));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* ring_tile = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -518,6 +531,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       mbar_init(accempty_bar(b), PAIR ? 2 * TC_EPI_WARPS : TC_EPI_WARPS);
     }
     mbar_init(drain_bar, 1);
+    if (WALK == 2) {
+      for (int r = 0; r < kTileRing; ++r) {
+        mbar_init(ring_full(r), 1);
+        mbar_init(ring_empty(r), 1 + TC_EPI_WARPS);  // the MMA issuer and every epilogue warp
+      }
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -542,11 +561,11 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
   const int CH = p.CH;
 
-  // SPLIT: this CTA's contiguous range [u_begin, u_end) of the launch's chunk
+  // WALK 1: this CTA's contiguous range [u_begin, u_end) of the launch's chunk
   // units (p.split_unit_count per tile, all tiles split)
   const int KTS_ = p.KT / Cfg::KSUB;  // stages per slice pair (single-matrix launches)
   const int CHS_ = CH / Cfg::KSUB;    // stages per fp32 chunk
-  const int64_t split_units = SPLIT ? static_cast<int64_t>(p.ntiles) * p.split_unit_count : 0;
+  const int64_t split_units = WALK == 1 ? static_cast<int64_t>(p.ntiles) * p.split_unit_count : 0;
   const int64_t u_begin = split_units * cta_id / cta_stride;
   const int64_t u_end = split_units * (cta_id + 1) / cta_stride;
   // unit u: its tile tt, level L and stage range [kb0, kb1)
@@ -613,16 +632,42 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         }
         return true;
       };
-      if constexpr (!SPLIT) {
+      // every stage of one whole tile
+      auto put_tile = [&](const Job& jb) __attribute__((always_inline)) {
+        const int s = jb.s;
+        for (int L = s + 1; L >= 2 && ok; --L) {
+          const int i_lo = max(1, L - s), i_hi = min(s, L - 1);
+          for (int i = i_lo; i <= i_hi && ok; ++i)
+            for (int kt = 0; kt < jb.KT && ok; kt += Cfg::KSUB) ok = put_stage(jb, i, L - i, kt);
+        }
+      };
+      if constexpr (WALK == 0) {
         for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
           const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
           if (jb.skip) continue;
-          const int s = jb.s;
-          for (int L = s + 1; L >= 2 && ok; --L) {
-            const int i_lo = max(1, L - s), i_hi = min(s, L - 1);
-            for (int i = i_lo; i <= i_hi && ok; ++i)
-              for (int kt = 0; kt < jb.KT && ok; kt += Cfg::KSUB) ok = put_stage(jb, i, L - i, kt);
+          put_tile(jb);
+        }
+      } else if constexpr (WALK == 2) {
+        // take tiles from the global counter (skipping finished matrices) and
+        // announce each, then -1, to the other warps through the ring
+        int rslot = 0;
+        uint32_t rph = 0;
+        while (ok) {
+          int tile = atomicAdd(p.tile_counter, 1);
+          while (tile < p.ntiles && job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank).skip) tile = atomicAdd(p.tile_counter, 1);
+          if (tile >= p.ntiles) tile = -1;
+          if (!wait_bar<false>(ring_empty(rslot), rph ^ 1u, abort_flag, p)) {
+            ok = false;
+            break;
           }
+          ring_tile[rslot] = tile;
+          mbar_arrive(ring_full(rslot));  // release: the index is visible to the waiting warps
+          if (++rslot == kTileRing) {
+            rslot = 0;
+            rph ^= 1u;
+          }
+          if (tile < 0) break;
+          put_tile(job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank));
         }
       } else {
         for (int64_t u = u_begin; u < u_end && ok; ++u) {
@@ -724,20 +769,41 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         }
         return true;
       };
-      if constexpr (!SPLIT) {
+      // every stage of one whole tile
+      auto mma_tile = [&](const Job& jb) __attribute__((always_inline)) {
+        const int s = jb.s;
+        // stages per level and per fp32 chunk (KT and CH are multiples of KSUB)
+        const int CHS = CH / Cfg::KSUB;
+        for (int L = s + 1; L >= 2 && ok; --L) {
+          const int nkb = npairs_of(L, s) * (jb.KT / Cfg::KSUB);
+          for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int kc = kb % CHS;
+            ok = mma_stage(kc == 0, (kc == CHS - 1) || (kb == nkb - 1));
+          }
+        }
+      };
+      if constexpr (WALK == 0) {
         for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
           const Job jb = job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank);
           if (jb.skip) continue;
-          const int s = jb.s;
-          // stages per level and per fp32 chunk (KT and CH are multiples of KSUB)
-          const int CHS = CH / Cfg::KSUB;
-          for (int L = s + 1; L >= 2 && ok; --L) {
-            const int nkb = npairs_of(L, s) * (jb.KT / Cfg::KSUB);
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-              const int kc = kb % CHS;
-              ok = mma_stage(kc == 0, (kc == CHS - 1) || (kb == nkb - 1));
-            }
+          mma_tile(jb);
+        }
+      } else if constexpr (WALK == 2) {
+        int rslot = 0;
+        uint32_t rph = 0;
+        while (ok) {
+          if (!wait_bar<false>(ring_full(rslot), rph, abort_flag, p)) {
+            ok = false;
+            break;
           }
+          const int tile = ring_tile[rslot];
+          mbar_arrive(ring_empty(rslot));
+          if (++rslot == kTileRing) {
+            rslot = 0;
+            rph ^= 1u;
+          }
+          if (tile < 0) break;
+          mma_tile(job_of<BN, PAIR>(p, &tmA, &tmB, tile, rank));
         }
       } else {
         for (int64_t u = u_begin; u < u_end && ok; ++u) {
@@ -778,7 +844,7 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     long long* scr_i = reinterpret_cast<long long*>(p.scratch) +
                        static_cast<int64_t>(blockIdx.x) * (2 * TC_BM * BN) + e * (COLS * 32) + lane;
     long long* scr_d = scr_i + TC_BM * BN;
-    // SPLIT: the group sums of (tile tt, this CTA's row half), shared by the
+    // WALK 1: the group sums of (tile tt, this CTA's row half), shared by the
     // CTAs that contribute to the tile; same element layout
     auto split_area_of = [&](int tt, int gidx) __attribute__((always_inline)) -> long long* {
       return p.split_area + ((static_cast<int64_t>(tt) * (PAIR ? 2 : 1) + rank) * 2 + gidx) * (TC_BM * BN) +
@@ -901,9 +967,37 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       }
     };
 
-    if constexpr (!SPLIT) {
-      // ---- whole tiles
-      for (int tile = cta_id; tile < p.ntiles && ok; tile += cta_stride) {
+    if constexpr (WALK != 1) {
+      // ---- whole tiles: cta, cta + #CTAs, ... (WALK 0) or as the producer
+      // announces them through the ring (WALK 2)
+      int rslot = 0;
+      uint32_t rph = 0;
+      for (int tile = cta_id - cta_stride; ok;) {
+        if constexpr (WALK == 0) {
+          tile += cta_stride;
+          if (tile >= p.ntiles) break;
+        } else {
+          int got = 0, t = 0;
+          if (lane == 0) {
+            got = wait_bar<false>(ring_full(rslot), rph, abort_flag, p) ? 1 : 0;
+            if (got) {
+              t = ring_tile[rslot];
+              mbar_arrive(ring_empty(rslot));
+            }
+          }
+          got = __shfl_sync(0xffffffffu, got, 0);
+          t = __shfl_sync(0xffffffffu, t, 0);
+          if (++rslot == kTileRing) {
+            rslot = 0;
+            rph ^= 1u;
+          }
+          if (!got) {
+            ok = false;
+            break;
+          }
+          if (t < 0) break;
+          tile = t;
+        }
         int64_t m0, n0;
         int s, KT;
         bool skip;
@@ -1124,17 +1218,17 @@ namespace {
 // to the kernel as loaded in the current context, and a context created anew
 // (after cudaDeviceReset) starts from the default limit. The call is host-side
 // only and costs about a microsecond against milliseconds of kernel.
-template <int BN, bool PAIR, bool F8 = false, bool SPLIT = false>
+template <int BN, bool PAIR, bool F8 = false, int WALK = 0>
 cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(ozaki_tc_kernel<BN, PAIR, F8, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(ozaki_tc_kernel<BN, PAIR, F8, WALK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               TcCfg<BN, PAIR, F8>::SMEM);
 }
 
-template <int BN, bool PAIR = false, bool F8 = false, bool SPLIT = false>
+template <int BN, bool PAIR = false, bool F8 = false, int WALK = 0>
 cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const TcParams& p, int grid,
                            cudaStream_t st) {
   using Cfg = TcCfg<BN, PAIR, F8>;
-  cudaError_t e = set_smem_attr<BN, PAIR, F8, SPLIT>();
+  cudaError_t e = set_smem_attr<BN, PAIR, F8, WALK>();
   if (e != cudaSuccess) return e;
   if (PAIR) {
     cudaLaunchConfig_t cfg;
@@ -1150,10 +1244,10 @@ cudaError_t launch_tc_impl(const CUtensorMap& ta, const CUtensorMap& tb, const T
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, PAIR, F8, SPLIT>, ta, tb, p);
+    e = cudaLaunchKernelEx(&cfg, ozaki_tc_kernel<BN, PAIR, F8, WALK>, ta, tb, p);
     if (e != cudaSuccess) return e;
   } else {
-    ozaki_tc_kernel<BN, PAIR, F8, SPLIT><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
+    ozaki_tc_kernel<BN, PAIR, F8, WALK><<<grid, TC_THREADS, Cfg::SMEM, st>>>(ta, tb, p);
   }
   count_launch();
   return cudaGetLastError();
@@ -1317,6 +1411,7 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   p.split_unit_count = 0;
   p.split_area = nullptr;
   p.split_cnt = nullptr;
+  p.tile_counter = nullptr;
   const bool split =
       g_split_tiles && split_ws != nullptr && 2 * ntiles <= units && s <= 2 * p.group && epi.kind != EPI_LEVELS;
   if (split) {
@@ -1343,19 +1438,19 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   if (pair) {
     const int grid = 2 * grid_units;
     if (split)
-      return f8 ? launch_tc_impl<256, true, true, true>(ta, tb, p, grid, st)
-                : launch_tc_impl<256, true, false, true>(ta, tb, p, grid, st);
+      return f8 ? launch_tc_impl<256, true, true, 1>(ta, tb, p, grid, st)
+                : launch_tc_impl<256, true, false, 1>(ta, tb, p, grid, st);
     return f8 ? launch_tc_impl<256, true, true>(ta, tb, p, grid, st) : launch_tc_impl<256, true>(ta, tb, p, grid, st);
   }
   const int grid = grid_units;
   if (split)
-    return f8 ? launch_tc_impl<256, false, true, true>(ta, tb, p, grid, st)
-              : launch_tc_impl<256, false, false, true>(ta, tb, p, grid, st);
+    return f8 ? launch_tc_impl<256, false, true, 1>(ta, tb, p, grid, st)
+              : launch_tc_impl<256, false, false, 1>(ta, tb, p, grid, st);
   return f8 ? launch_tc_impl<256, false, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
 }
 
 cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, int beta,
-                                    int phase, int cur, int* err, double* scratch, cudaStream_t st) {
+                                    int phase, int cur, int* err, double* scratch, int* counter, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   TcParams p;
   std::memset(&p, 0, sizeof(p));
@@ -1372,14 +1467,19 @@ cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int
   p.err = err;
   p.done = nullptr;
   p.timeout_ns = 5000000000ull;
+  // tiles are taken from a counter as CTAs free up (they differ in work: the
+  // list holds the largest matrices' tiles first)
+  p.tile_counter = counter;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   CUtensorMap unused;
   std::memset(&unused, 0, sizeof(unused));
   const int grid = std::min(ntiles, tc_max_ctas());
   ProfScope prof(DMP_PROF_PRODUCT, st);
-  if (beta == 5) return bn == 256 ? launch_tc_impl<256, false, true>(unused, unused, p, grid, st)
+  if (beta == 5) return bn == 256 ? launch_tc_impl<256, false, true, 2>(unused, unused, p, grid, st)
                                   : cudaErrorInvalidValue;  // E4M3 digits: 256-column tiles
-  if (bn == 128) return launch_tc_impl<128, false>(unused, unused, p, grid, st);
-  return launch_tc_impl<256, false>(unused, unused, p, grid, st);
+  if (bn == 128) return launch_tc_impl<128, false, false, 2>(unused, unused, p, grid, st);
+  return launch_tc_impl<256, false, false, 2>(unused, unused, p, grid, st);
 }
 
 }  // namespace dmp
