@@ -35,8 +35,8 @@ namespace dmp {
 
 namespace {
 
-constexpr int kSplitThreads = 256;
-constexpr int kPairs = 16;                                          // entry pairs a thread holds
+constexpr int kSplitThreads = 512;
+constexpr int kPairs = 8;                                           // entry pairs a thread holds
 constexpr int kSweep = 2 * kPairs * kSplitThreads;  // 8192 entries
 constexpr int64_t kMaxRow = (int64_t{1} << 31) - 1 - kSweep;     // in-row offsets stay below 2^31
 
@@ -260,12 +260,15 @@ __device__ __forceinline__ void max_bits(double a, uint32_t& mxh, uint32_t& mxl,
 // Offsets within a row are 32-bit (k_pad < 2^31, checked by the launcher).
 // KIND 1: int8 digits, 3: bfloat16 holding the same integers, 4: E4M3 bytes.
 // BETA 7: truncated digits; BETA 5 and 8: nearest digits (four entries per thread).
-template <int KIND, int BETA>
+// S > 0: the slice count is the compile-time constant S (s is ignored), so the
+// per-digit slice test folds away.
+template <int KIND, int BETA, int S = 0>
 __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int64_t r, int64_t m, int k,
-                                              int64_t lda, int s, int32_t* __restrict__ exps,
+                                              int64_t lda, int s_arg, int32_t* __restrict__ exps,
                                               void* __restrict__ planes, int k_pad, int64_t plane_stride,
                                               int* flag) {
   constexpr bool kNearest = BETA != 7;
+  const int s = S > 0 ? S : s_arg;
   const int tid = threadIdx.x;
   __shared__ uint32_t red_h[kSplitThreads / 32], red_l[kSplitThreads / 32];
   __shared__ int red_bad[kSplitThreads / 32];
@@ -346,14 +349,38 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
   }
 }
 
-template <int KIND, int BETA>
+template <int KIND, int BETA, int S = 0>
 __global__ void __launch_bounds__(kSplitThreads, 2)
 split_rows_kernel(const double* __restrict__ A, int64_t m, int64_t k, int64_t lda, int s,
                   int32_t* __restrict__ exps, void* __restrict__ planes, int64_t k_pad,
                   int64_t plane_stride, int* flag, const int* done) {
   if (done != nullptr && *done) return;
-  split_one_row<KIND, BETA>(A, blockIdx.x, m, static_cast<int>(k), lda, s, exps, planes, static_cast<int>(k_pad),
-                            plane_stride, flag);
+  split_one_row<KIND, BETA, S>(A, blockIdx.x, m, static_cast<int>(k), lda, s, exps, planes,
+                               static_cast<int>(k_pad), plane_stride, flag);
+}
+
+// The split with a compile-time slice count for the counts the purification
+// uses most (INT8 digits in bf16, BF16 nearest digits, E4M3 digits), else the
+// runtime count.
+template <int KIND, int BETA, int S>
+void launch_split_s(dim3 grid, cudaStream_t st, const double* A, int64_t m, int64_t k, int64_t lda, int s,
+                    int32_t* exps, void* planes, int64_t k_pad, int64_t plane_stride, int* flag, const int* done) {
+  split_rows_kernel<KIND, BETA, S><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad,
+                                                                   plane_stride, flag, done);
+}
+template <int KIND, int BETA, int S_LO, int S_HI>
+void launch_split_any(dim3 grid, cudaStream_t st, const double* A, int64_t m, int64_t k, int64_t lda, int s,
+                      int32_t* exps, void* planes, int64_t k_pad, int64_t plane_stride, int* flag, const int* done) {
+  if constexpr (S_LO <= S_HI) {
+    if (s == S_LO) {
+      launch_split_s<KIND, BETA, S_LO>(grid, st, A, m, k, lda, s, exps, planes, k_pad, plane_stride, flag, done);
+      return;
+    }
+    launch_split_any<KIND, BETA, S_LO + 1, S_HI>(grid, st, A, m, k, lda, s, exps, planes, k_pad, plane_stride, flag,
+                                                 done);
+  } else {
+    launch_split_s<KIND, BETA, 0>(grid, st, A, m, k, lda, s, exps, planes, k_pad, plane_stride, flag, done);
+  }
 }
 
 // Grouped: CTA x covers row x - row_start[b] of matrix b (row_start ascending,
@@ -409,14 +436,11 @@ cudaError_t launch_split_rows(const double* A, int64_t m, int64_t k, int64_t lda
     split_rows_kernel<1, 7><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
                                                             flag, done);
   } else if (elem_kind == 3 && beta == 7) {
-    split_rows_kernel<3, 7><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
-                                                            flag, done);
+    launch_split_any<3, 7, 4, 9>(grid, st, A, m, k, lda, s, exps, planes, k_pad, plane_stride, flag, done);
   } else if (elem_kind == 3 && beta == 8) {
-    split_rows_kernel<3, 8><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
-                                                            flag, done);
+    launch_split_any<3, 8, 3, 7>(grid, st, A, m, k, lda, s, exps, planes, k_pad, plane_stride, flag, done);
   } else if (elem_kind == 4 && beta == 5) {
-    split_rows_kernel<4, 5><<<grid, kSplitThreads, 0, st>>>(A, m, k, lda, s, exps, planes, k_pad, plane_stride,
-                                                            flag, done);
+    launch_split_any<4, 5, 5, 11>(grid, st, A, m, k, lda, s, exps, planes, k_pad, plane_stride, flag, done);
   } else {
     return cudaErrorInvalidValue;
   }
