@@ -203,7 +203,7 @@ struct TuneKey {
   bool operator<(const TuneKey& o) const { return std::tie(mode, n) < std::tie(o.mode, o.n); }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tuned;  // -> (slices, bn)
+std::map<TuneKey, std::pair<int, int>> g_tuned;  // -> (slices, tile shape cfg)
 
 struct GraphEntry {
   cudaGraph_t graph = nullptr;
@@ -290,15 +290,15 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   const int64_t nmax_idx = std::max_element(n, n + batch) - n;
 
   // ---- autotune: slice count (accuracy) and tile width (speed), cached per shape
-  TuneKey key{std::vector<int64_t>(n, n + batch), opts->mode * 16 + opts->slices};
-  int s = opts->slices, bn = 256;
+  TuneKey key{std::vector<int64_t>(n, n + batch), opts->mode * 16 + opts->slices + (tc_pairs_available() ? 1024 : 0)};
+  int s = opts->slices, cfg = 256;
   bool tuned = false;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
       s = it->second.first;
-      bn = it->second.second;
+      cfg = it->second.second;
       tuned = true;
     }
   }
@@ -362,13 +362,19 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     M.state = reinterpret_cast<PurifyState*>(at(ws, L.state[b]));
     hrow[b + 1] = hrow[b] + M.n_pad;
   }
-  auto build_maps = [&](int tile_n) -> bool {
+  // tile shapes of the grouped product: cfg 128 and 256 are single CTAs on
+  // 128 x cfg tiles, cfg 512 is CTA pairs on 256 x 256 tiles (each CTA stages
+  // 128 rows of A and 128 of the 256 B rows)
+  auto cfg_bn = [](int cfg) { return cfg == 128 ? 128 : 256; };
+  auto cfg_pair = [](int cfg) { return cfg == 512; };
+  auto build_maps = [&](int cfg) -> bool {
+    const int box_b = cfg_pair(cfg) ? cfg_bn(cfg) / 2 : cfg_bn(cfg);
     for (int b = 0; b < batch; ++b) {
       BatchMat& M = hm[b];
       const int64_t rows = static_cast<int64_t>(s) * M.n_pad;
       if (!make_map(&M.tmPa, M.planesP, M.k_pad, rows, 128, f8)) return false;
-      if (!make_map(&M.tmPb, M.planesP, M.k_pad, rows, tile_n, f8)) return false;
-      if (!make_map(&M.tmXb, M.planesX, M.k_pad, rows, tile_n, f8)) return false;
+      if (!make_map(&M.tmPb, M.planesP, M.k_pad, rows, box_b, f8)) return false;
+      if (!make_map(&M.tmXb, M.planesX, M.k_pad, rows, box_b, f8)) return false;
     }
     return true;
   };
@@ -377,14 +383,16 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   std::vector<int> by_size(batch);
   for (int b = 0; b < batch; ++b) by_size[b] = b;
   std::stable_sort(by_size.begin(), by_size.end(), [&](int x, int y) { return n[x] > n[y]; });
-  auto build_tiles = [&](int tile_n, std::vector<int4>& out) {
+  auto build_tiles = [&](int cfg, std::vector<int4>& out) {
     out.clear();
+    const int tile_n = cfg_bn(cfg), bm = cfg_pair(cfg) ? 256 : 128;
     // column blocks outermost within each matrix, so CTAs running together
-    // work on the same matrix and share its B blocks
+    // work on the same matrix and share its B blocks; only tiles holding some
+    // element with row <= column
     for (int b : by_size) {
-      const int tm = static_cast<int>(hm[b].n_pad / 128), tn = static_cast<int>(hm[b].n_pad / tile_n);
+      const int tm = static_cast<int>(hm[b].n_pad / bm), tn = static_cast<int>(hm[b].n_pad / tile_n);
       for (int bj = 0; bj < tn; ++bj)
-        for (int bi = 0; bi < std::min(tm, tile_n * (bj + 1) / 128); ++bi) out.push_back(make_int4(b, bi, bj, 0));
+        for (int bi = 0; bi < std::min(tm, tile_n * (bj + 1) / bm); ++bi) out.push_back(make_int4(b, bi, bj, 0));
     }
   };
   auto init_states = [&]() -> int {
@@ -406,14 +414,17 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   std::vector<int4> htiles;
   DMP_CUDA(cudaMemcpyAsync(drow, hrow.data(), sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, st));
 
-  if (!tuned && !f8) {
-    // tile width: time the P^2 product of the batch's initial guesses with both
-    // (the E4M3 digits run on 256-column tiles only)
+  if (!tuned) {
+    // tile shape: time the P^2 product of the batch's initial guesses with each
+    // (128 x 128 and 128 x 256 single CTAs, 256 x 256 CTA pairs; E4M3 digits run
+    // on 256-column tiles only)
     float best = 1e30f;
-    int best_bn = 256;
+    int best_cfg = 256;
     int rc = init_states();
     if (rc != DMP_OK) return rc;
-    for (int cand : {128, 256}) {
+    std::vector<int> cands = f8 ? std::vector<int>{256} : std::vector<int>{128, 256};
+    if (tc_pairs_available()) cands.push_back(512);
+    for (int cand : cands) {
       if (!build_maps(cand)) return DMP_ERR_CUDA;
       build_tiles(cand, htiles);
       DMP_CUDA(cudaMemcpyAsync(dmats, hm.data(), sizeof(BatchMat) * batch, cudaMemcpyHostToDevice, st));
@@ -423,8 +434,8 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       DMP_CUDA(cudaEventCreate(&e0));
       DMP_CUDA(cudaEventCreate(&e1));
       DMP_CUDA(cudaEventRecord(e0, st));
-      DMP_CUDA(launch_ozaki_tc_grouped(dmats, dtiles, static_cast<int>(htiles.size()), cand, tbeta, 0, 0, derr,
-                                       scratch, dcounter, st));
+      DMP_CUDA(launch_ozaki_tc_grouped(dmats, dtiles, static_cast<int>(htiles.size()), cfg_bn(cand), cfg_pair(cand),
+                                       tbeta, 0, 0, derr, scratch, dcounter, st));
       DMP_CUDA(cudaEventRecord(e1, st));
       DMP_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -433,19 +444,19 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       cudaEventDestroy(e1);
       if (ms < best) {
         best = ms;
-        best_bn = cand;
+        best_cfg = cand;
       }
     }
-    bn = best_bn;
+    cfg = best_cfg;
   }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = std::make_pair(s, bn);
+    g_tuned[key] = std::make_pair(s, cfg);
   }
 
   // ---- the real run
-  if (!build_maps(bn)) return DMP_ERR_CUDA;
-  build_tiles(bn, htiles);
+  if (!build_maps(cfg)) return DMP_ERR_CUDA;
+  build_tiles(cfg, htiles);
   DMP_CUDA(cudaMemcpyAsync(dmats, hm.data(), sizeof(BatchMat) * batch, cudaMemcpyHostToDevice, st));
   DMP_CUDA(cudaMemcpyAsync(dtiles, htiles.data(), sizeof(int4) * htiles.size(), cudaMemcpyHostToDevice, st));
   DMP_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
@@ -458,7 +469,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   // graph: WHILE(any matrix running) { two iterations }, cached per argument set
   std::string gkey(reinterpret_cast<const char*>(hm.data()), sizeof(BatchMat) * batch);
   gkey.append(reinterpret_cast<const char*>(&ws), sizeof(ws));
-  gkey.append(reinterpret_cast<const char*>(&bn), sizeof(bn));
+  gkey.append(reinterpret_cast<const char*>(&cfg), sizeof(cfg));
   gkey.append(reinterpret_cast<const char*>(&tbeta), sizeof(tbeta));  // the digit rule picks the kernels
   cudaGraphExec_t exec = nullptr;
   {
@@ -486,10 +497,12 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     DMP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     for (int cur = 0; cur < 2; ++cur) {
       launch_split_grouped(dmats, drow, batch, hrow[batch], cur, tbeta, cs);
-      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, bn, tbeta, 0, cur, derr, scratch, dcounter, cs);
+      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, cfg_bn(cfg), cfg_pair(cfg), tbeta, 0, cur, derr, scratch,
+                              dcounter, cs);
       launch_measure_grouped(dmats, batch, cur, dpart, cond, 1, cs);
       launch_split_grouped(dmats, drow, batch, hrow[batch], 2, tbeta, cs);
-      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, bn, tbeta, 1, cur, derr, scratch, dcounter, cs);
+      launch_ozaki_tc_grouped(dmats, dtiles, ntiles, cfg_bn(cfg), cfg_pair(cfg), tbeta, 1, cur, derr, scratch,
+                              dcounter, cs);
     }
     cudaGraph_t captured = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &captured);

@@ -131,6 +131,9 @@ size_t tc_split_bytes();
 int set_tc_split_tiles(int enable);
 // beta = 7 single-matrix products on CTA pairs (2-SM MMA); returns the previous setting
 int set_tc_pairing(int enable);
+// whether products may run on CTA pairs (the pairing switch is on and clusters of
+// two CTAs of the paired kernel can be resident)
+bool tc_pairs_available();
 // The next tcgen05 product launch withholds each CTA's first operand stage and
 // bounds its waits by wait_limit_us (the bounded-wait test); one-shot.
 int set_stall_test(int wait_limit_us);
@@ -321,9 +324,11 @@ cudaError_t launch_measure_grouped(const BatchMat* mats, int nmats, int cur, dou
                                    cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st);
 cudaError_t launch_finish_grouped(const BatchMat* mats, int nmats, cudaStream_t st);
 // phase 0: X2 = P P from buf[cur]; phase 1: update buf[cur] -> buf[1 - cur].
-// `counter` (one int of device memory) is zeroed on the stream before the
-// launch; the CTAs take tiles from it in list order.
-cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, int beta,
+// `counter` (one int of device memory) is zeroed on the stream before a
+// single-CTA launch; its CTAs take tiles from it in list order.
+// `pair`: CTA pairs on 256-row tiles (bn 256; the tiles' row blocks are 256
+// rows and the B maps have bn / 2-row boxes), else single CTAs on 128-row tiles.
+cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, bool pair, int beta,
                                     int phase, int cur, int* err, double* scratch, int* counter, cudaStream_t st);
 
 }  // namespace dmp

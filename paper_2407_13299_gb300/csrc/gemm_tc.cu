@@ -406,7 +406,7 @@ template <int BN, bool PAIR = false>
 __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB, int tile,
                                       uint32_t rank = 0) {
   Job j;
-  if (PAIR || p.mats == nullptr) {
+  if (p.mats == nullptr) {
     int bi, bj;
     tile_of<BN, PAIR ? 2 * TC_BM : TC_BM>(p, tile, bi, bj);
     j.ta = tmA;
@@ -428,7 +428,8 @@ __device__ __forceinline__ Job job_of(const TcParams& p, const CUtensorMap* tmA,
   }
   const int4 t = p.tiles[tile];
   const BatchMat& M = p.mats[t.x];
-  j.m0 = static_cast<int64_t>(t.y) * TC_BM;
+  // row block t.y of 128 rows, or of 256 for a CTA pair (this CTA: half `rank`)
+  j.m0 = static_cast<int64_t>(t.y) * (PAIR ? 2 * TC_BM : TC_BM) + TC_BM * static_cast<int64_t>(rank);
   j.n0 = static_cast<int64_t>(t.z) * BN;
   j.rows_a = M.n_pad;
   j.rows_b = M.n_pad;
@@ -1288,6 +1289,8 @@ int tc_max_pairs() {
 
 }  // namespace
 
+bool tc_pairs_available() { return g_pairing && tc_max_pairs() > 0; }
+
 int set_stall_test(int wait_limit_us) {
   if (wait_limit_us < 0) return DMP_ERR_INVALID_ARG;
   g_stall_us.store(wait_limit_us);
@@ -1449,7 +1452,7 @@ cudaError_t launch_ozaki_tc(const void* A, const void* B, const int32_t* ea, con
   return f8 ? launch_tc_impl<256, false, true>(ta, tb, p, grid, st) : launch_tc_impl<256, false>(ta, tb, p, grid, st);
 }
 
-cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, int beta,
+cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int ntiles, int bn, bool pair, int beta,
                                     int phase, int cur, int* err, double* scratch, int* counter, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   TcParams p;
@@ -1467,13 +1470,22 @@ cudaError_t launch_ozaki_tc_grouped(const BatchMat* mats, const int4* tiles, int
   p.err = err;
   p.done = nullptr;
   p.timeout_ns = 5000000000ull;
-  // tiles are taken from a counter as CTAs free up (they differ in work: the
-  // list holds the largest matrices' tiles first)
+  CUtensorMap unused;
+  std::memset(&unused, 0, sizeof(unused));
+  if (pair) {
+    // CTA pairs (256-row tiles, 256 columns): the pairs walk the list (largest
+    // matrices first) round robin
+    if (bn != 256 || tc_max_pairs() <= 0) return cudaErrorInvalidValue;
+    const int grid = 2 * std::min(ntiles, tc_max_pairs());
+    ProfScope prof(DMP_PROF_PRODUCT, st);
+    return beta == 5 ? launch_tc_impl<256, true, true>(unused, unused, p, grid, st)
+                     : launch_tc_impl<256, true, false>(unused, unused, p, grid, st);
+  }
+  // single CTAs take tiles from a counter as they free up (the tiles differ in
+  // work: the list holds the largest matrices' tiles first)
   p.tile_counter = counter;
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  CUtensorMap unused;
-  std::memset(&unused, 0, sizeof(unused));
   const int grid = std::min(ntiles, tc_max_ctas());
   ProfScope prof(DMP_PROF_PRODUCT, st);
   if (beta == 5) return bn == 256 ? launch_tc_impl<256, false, true, 2>(unused, unused, p, grid, st)

@@ -202,12 +202,12 @@ __device__ __forceinline__ void store_nearest4(int s, const uint32_t (&w)[4][3],
 // adjacent pairs across the threads (bf16 and int8 digits), or two adjacent
 // pairs per thread (E4M3 digits, so that each thread owns four consecutive
 // entries and stores 4-byte words).
-template <bool QUAD>
+template <bool QUAD, int THREADS = kSplitThreads>
 __device__ __forceinline__ int entry_of(int c0, int tid, int q) {
   if constexpr (QUAD) {
-    return c0 + 4 * (tid + kSplitThreads * (q >> 1)) + 2 * (q & 1);
+    return c0 + 4 * (tid + THREADS * (q >> 1)) + 2 * (q & 1);
   } else {
-    return c0 + 2 * (tid + kSplitThreads * q);
+    return c0 + 2 * (tid + THREADS * q);
   }
 }
 
@@ -261,24 +261,26 @@ __device__ __forceinline__ void max_bits(double a, uint32_t& mxh, uint32_t& mxl,
 // KIND 1: int8 digits, 3: bfloat16 holding the same integers, 4: E4M3 bytes.
 // BETA 7: truncated digits; BETA 5 and 8: nearest digits (four entries per thread).
 // S > 0: the slice count is the compile-time constant S (s is ignored), so the
-// per-digit slice test folds away.
-template <int KIND, int BETA, int S = 0>
+// per-digit slice test folds away. THREADS threads share the row (kPairs entry
+// pairs each per sweep of 2 kPairs THREADS entries).
+template <int KIND, int BETA, int S = 0, int THREADS = kSplitThreads>
 __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int64_t r, int64_t m, int k,
                                               int64_t lda, int s_arg, int32_t* __restrict__ exps,
                                               void* __restrict__ planes, int k_pad, int64_t plane_stride,
                                               int* flag) {
   constexpr bool kNearest = BETA != 7;
+  constexpr int kSweep = 2 * kPairs * THREADS;
   const int s = S > 0 ? S : s_arg;
   const int tid = threadIdx.x;
-  __shared__ uint32_t red_h[kSplitThreads / 32], red_l[kSplitThreads / 32];
-  __shared__ int red_bad[kSplitThreads / 32];
+  __shared__ uint32_t red_h[THREADS / 32], red_l[THREADS / 32];
+  __shared__ int red_bad[THREADS / 32];
   const bool live = r < m;
   const double* row = A + (live ? r * lda : 0);
   const bool vec = (reinterpret_cast<uintptr_t>(row) & 15) == 0;
 
   double2 v[kPairs];
 #pragma unroll
-  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<kNearest>(0, tid, q), k, live, vec);
+  for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<kNearest, THREADS>(0, tid, q), k, live, vec);
   uint32_t mxh = 0, mxl = 0;
   bool bad = false;
 #pragma unroll
@@ -287,7 +289,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
     max_bits(v[q].y, mxh, mxl, bad);
   }
   if (live) {
-    for (int j = kSweep + tid; j < k; j += kSplitThreads) max_bits(row[j], mxh, mxl, bad);
+    for (int j = kSweep + tid; j < k; j += THREADS) max_bits(row[j], mxh, mxl, bad);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -303,7 +305,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
   __syncthreads();
   int any_bad = 0;
 #pragma unroll
-  for (int w = 0; w < kSplitThreads / 32; ++w) {
+  for (int w = 0; w < THREADS / 32; ++w) {
     mxh = max(mxh, red_h[w]);
     mxl = max(mxl, red_l[w]);
     any_bad |= red_bad[w];
@@ -323,7 +325,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
   for (int c0 = 0;;) {
 #pragma unroll
     for (int q = 0; q < kPairs; q += (kNearest ? 2 : 1)) {
-      const int j = entry_of<kNearest>(c0, tid, q);
+      const int j = entry_of<kNearest, THREADS>(c0, tid, q);
       if (j < k_pad) {
         if constexpr (kNearest) {
           // entries j .. j + 3 (k_pad is a multiple of 4, so all four are inside)
@@ -345,7 +347,7 @@ __device__ __forceinline__ void split_one_row(const double* __restrict__ A, int6
     if (k_pad - c0 <= kSweep) break;
     c0 += kSweep;
 #pragma unroll
-    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<kNearest>(c0, tid, q), k, live, vec);
+    for (int q = 0; q < kPairs; ++q) v[q] = load_pair(row, entry_of<kNearest, THREADS>(c0, tid, q), k, live, vec);
   }
 }
 
@@ -385,8 +387,12 @@ void launch_split_any(dim3 grid, cudaStream_t st, const double* A, int64_t m, in
 
 // Grouped: CTA x covers row x - row_start[b] of matrix b (row_start ascending,
 // row_start[nmats] = total padded rows). Finished matrices are skipped.
+// Batch rows are short (a few thousand entries at most): 128 threads per row,
+// so that many rows are in flight per SM.
+constexpr int kGroupedSplitThreads = 128;
+
 template <int KIND, int BETA>
-__global__ void __launch_bounds__(kSplitThreads, 2)
+__global__ void __launch_bounds__(kGroupedSplitThreads, 8)
 split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restrict__ row_start, int nmats,
                      int which) {
   const int64_t x = blockIdx.x;
@@ -402,8 +408,8 @@ split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restric
   const int64_t lda = which == 0 ? M.ldp : M.n;
   int32_t* exps = which == 2 ? M.expsX : M.expsP;
   void* planes = which == 2 ? M.planesX : M.planesP;
-  split_one_row<KIND, BETA>(A, r, M.n, static_cast<int>(M.n), lda, M.s, exps, planes, static_cast<int>(M.k_pad),
-                            M.n_pad * M.k_pad, nullptr);
+  split_one_row<KIND, BETA, 0, kGroupedSplitThreads>(A, r, M.n, static_cast<int>(M.n), lda, M.s, exps, planes,
+                                                     static_cast<int>(M.k_pad), M.n_pad * M.k_pad, nullptr);
 }
 
 __global__ void transpose_kernel(const double* __restrict__ A, int64_t m, int64_t n, int64_t lda,
@@ -464,11 +470,11 @@ cudaError_t launch_split_grouped(const BatchMat* mats, const int64_t* row_start,
   ProfScope prof(DMP_PROF_SPLIT, st);  // batch rows are at most a few thousand long (k_pad << kMaxRow)
   const unsigned grid = static_cast<unsigned>(total_rows);
   if (beta == 7) {
-    split_grouped_kernel<3, 7><<<grid, kSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+    split_grouped_kernel<3, 7><<<grid, kGroupedSplitThreads, 0, st>>>(mats, row_start, nmats, which);
   } else if (beta == 8) {
-    split_grouped_kernel<3, 8><<<grid, kSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+    split_grouped_kernel<3, 8><<<grid, kGroupedSplitThreads, 0, st>>>(mats, row_start, nmats, which);
   } else if (beta == 5) {
-    split_grouped_kernel<4, 5><<<grid, kSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+    split_grouped_kernel<4, 5><<<grid, kGroupedSplitThreads, 0, st>>>(mats, row_start, nmats, which);
   } else {
     return cudaErrorInvalidValue;
   }
