@@ -408,15 +408,23 @@ def run_ours(args):
     dmp.purify_host(H_host, n_occ, out=P_host, ws=ws_host, mode=mode, slices=s, executor=args.executor,
                     refine=refine)
     torch.cuda.synchronize()
+    e2e_dev = []
     for _ in range(max(args.e2e_steps, 1)):
         barrier()
         torch.cuda.synchronize()
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        ea.record(stream)
         _, e2e_info = dmp.purify_host(H_host, n_occ, out=P_host, ws=ws_host, mode=mode, slices=s,
                                       executor=args.executor, refine=refine)
+        eb.record(stream)
         e2e_times.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        e2e_dev.append(ea.elapsed_time(eb) / 1e3)
     e2e = {"value": max_over_ranks(statistics.median(e2e_times), dev), "unit": UNIT,
            "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8, "runs_s": e2e_times,
+           "runs_device_s": e2e_dev,
            "call": "dm_purify_host (C ABI): pinned host H in, pinned host P out, one cudaMemcpy2DAsync each way "
                    "on the library's stream, synchronised before return; host clock around the call",
            "matches_device_call": bool(torch.equal(P_host, P.cpu()))}
