@@ -198,9 +198,15 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t par
       : "memory");
   return ok != 0;
 }
-// arrive on a barrier of either CTA of the pair (a shared::cluster address)
+// arrive on a barrier of either CTA of the pair (a shared::cluster address).
+// Used only to hand a TMEM buffer back to the MMA issuer: the loads from it
+// have completed (tcgen05.wait::ld) and are ordered before the arrive by
+// tcgen05.fence::before_thread_sync, and no memory this thread wrote is passed
+// on through the barrier. The arrive therefore keeps the default CTA-scope
+// release: a cluster-scope release adds a fence on every drained chunk that
+// waits for the thread's outstanding memory operations.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 // TMA load into this CTA's shared memory that signals `bar`, which may be the peer's
 __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int x, int y) {
