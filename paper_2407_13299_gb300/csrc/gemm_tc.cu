@@ -295,6 +295,48 @@ __device__ __forceinline__ void red_add_keep(void* p, long long v, uint64_t pol)
   asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol) : "memory");
 }
 
+// RN(h 2^sh + l) 2^e2 as a double, for integers |h|, |l| < 2^53, 0 <= sh < 64
+// and a normal result, by integer arithmetic alone: the exact sum is formed in
+// 128 bits, its leading 53 bits are rounded to nearest-even, and the exponent
+// and sign are set directly. This is the value float64 arithmetic gives for
+// double(h) 2^(sh + e2) + double(l) 2^e2 (both products exact, one rounding),
+// without the int64-to-double conversions and multiplies, which on this GPU
+// run on the narrow FP64 pipe.
+__device__ __forceinline__ double round_exact(long long h, int sh, long long l, int e2) {
+  // x = h 2^sh + l in two's complement (xh:xl)
+  const unsigned long long hl = static_cast<unsigned long long>(h) << sh;
+  unsigned long long xh = sh == 0 ? static_cast<unsigned long long>(h >> 63)
+                                  : static_cast<unsigned long long>(h >> (64 - sh));
+  const unsigned long long xl = hl + static_cast<unsigned long long>(l);
+  xh += static_cast<unsigned long long>(l >> 63) + (xl < hl ? 1ull : 0ull);
+  const bool neg = static_cast<long long>(xh) < 0;
+  // magnitude (mh:ml)
+  const unsigned long long ml = neg ? ~xl + 1ull : xl;
+  const unsigned long long mh = neg ? ~xh + (ml == 0 ? 1ull : 0ull) : xh;
+  if ((mh | ml) == 0) return 0.0;
+  int msb = mh != 0 ? 127 - __clzll(static_cast<long long>(mh)) : 63 - __clzll(static_cast<long long>(ml));
+  unsigned long long mant;
+  if (msb <= 52) {
+    mant = ml << (52 - msb);  // exact (mh is zero)
+  } else {
+    const int r = msb - 52;  // 1 .. 63: the dropped bits all lie in ml
+    mant = (ml >> r) | (r == 0 ? 0ull : mh << (64 - r));
+    const unsigned long long rem = ml & ((1ull << r) - 1ull);
+    const unsigned long long half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++msb;
+      }
+    }
+  }
+  const unsigned long long bits = (neg ? (1ull << 63) : 0ull) |
+                                  (static_cast<unsigned long long>(msb + e2 + 1023) << 52) |
+                                  (mant & ((1ull << 52) - 1ull));
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
 // x 2^e for a finite double: exponent arithmetic when the result stays normal,
 // ldexp otherwise (identical results: scaling by a power of two is exact).
 __device__ __forceinline__ double scale_pow2(double x, int e) {
@@ -919,7 +961,6 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       const double lscale = ldexp(1.0, -p.beta * (2 + (s - 1) % p.group));
       const bool has_d = s > p.group;
       const bool two_groups = has_d && s <= 2 * p.group;
-      const double g0scale = ldexp(1.0, -p.beta * (s + 1));
       const uint64_t pol = policy_evict_last();
       double* Cout = jb.epi.C;
       const int64_t ldc = jb.epi.ldc;
@@ -960,10 +1001,12 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           const int64_t col = col0 + t;
           if (col >= jb.n) break;
           if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
+          // one or two groups: the exact integer combination rounded once;
+          // three or more: the float64 sum D of the earlier groups plus the last
           const double acc =
-              two_groups ? static_cast<double>(ti[t]) * g0scale + static_cast<double>(td[t]) * lscale
+              two_groups ? round_exact(td[t], p.beta * p.group, ti[t], -p.beta * (s + 1))
                          : (has_d ? __longlong_as_double(td[t]) + static_cast<double>(ti[t]) * lscale
-                                  : static_cast<double>(ti[t]) * lscale);
+                                  : round_exact(0, 0, ti[t], -p.beta * (2 + (s - 1) % p.group)));
           double v = (er == kBadExp || ecv[t] == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
                                                           : scale_pow2(acc, er + ecv[t]);
           if (upd) v = wa * pv[t] + w2 * xv[t] + w3 * v;
