@@ -67,6 +67,9 @@ def parse_args():
                     help="purify: the n=8192 benchmark; batch64: the 64-matrix batched workload")
     ap.add_argument("--batch-mode", default="int8", choices=["int8", "bf16", "e4m3"],
                     help="slice mode of the batch64 workload")
+    ap.add_argument("--batch-stream", choices=("on", "off"), default="off",
+                    help="batch64 workload: run the batched iterations as plain stream launches "
+                         "(DMP_FLAG_BATCHED_STREAM) in the timed calls, so that a profiler sees every kernel")
     ap.add_argument("--batched", choices=("on", "off"), default="on",
                     help="also time the 64-matrix batched workload (dm_purify_batched) and report it as `batched`")
     ap.add_argument("--foe", choices=("on", "off"), default="on",
@@ -816,12 +819,14 @@ def run_ours(args):
     return 0
 
 
-def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True):
+def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True, stream=False):
     """The batched workload: 64 Hamiltonians, n = 32 U{4..48}, n_occ = n/4, gap
     0.2, through dm_purify_batched (one graph launch, slice count and tile width
-    from the library's autotuner), against 64 sequential dm_purify calls at the
-    same s. Returns a dict with both times, the slice-pair work and its rate
-    against the measured sustained bf16 peak (E4M3: twice that)."""
+    from the library's autotuner; `stream`: plain stream launches instead),
+    against 64 sequential dm_purify calls at the same s. Returns a dict with
+    both times, the slice-pair work and its rate against the measured sustained
+    bf16 peak (E4M3: twice that), and the per-phase device times of one more
+    call made with stream launches (the library's profiler sees no graph)."""
     import numpy as np
     import torch
 
@@ -835,20 +840,34 @@ def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True):
     opts.slices = 0
     ws = dmp.workspace(dmp.batched_workspace_bytes([h.n for h in hs], opts))
     Ps = [torch.empty_like(H) for H in Hs]
-    _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)  # tunes and builds the graph
+    _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws,
+                                     stream_launches=stream)  # tunes (and builds the graph)
     s = infos[0]["slices_used"]
     for _ in range(warmup):
-        dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)
+        dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, stream_launches=stream)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(steps):
-        _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws)
+        _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, stream_launches=stream)
     b.record()
     torch.cuda.synchronize()
     t_batch = a.elapsed_time(b) / 1e3 / steps
+    # per-phase device times: one more call as plain stream launches (same
+    # kernels and results), bracketed by the library's profiler
+    dmp.profile_enable(True)
+    dmp.profile_reset()
+    try:
+        dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, stream_launches=True)
+        torch.cuda.synchronize()
+        phases = {name: round(dmp.profile_read(k)[0], 3)
+                  for k, name in ((0, "products"), (1, "splits"), (2, "measures"), (3, "init"))}
+        launches = {name: dmp.profile_read(k)[1] for k, name in ((0, "products"), (1, "splits"), (2, "measures"))}
+    finally:
+        dmp.profile_enable(False)
     out = {"workload": "batch64: 64 H, n = 32 U{4..48}, n_occ = n/4, gap 0.2", "mode": f"ozaki-{mode}",
-           "slices": s, "value": t_batch, "unit": UNIT}
+           "slices": s, "value": t_batch, "unit": UNIT, "launch": "stream launches" if stream else "one graph launch",
+           "phases_ms_stream_launches": phases, "phase_launches": launches}
     # slice-pair work: per matrix 2 iters + 1 symmetric products of p n^2 (n + 1)
     p_s = s * (s + 1) // 2
     flops = sum((2 * i["iters"] + 1) * p_s * h.n * h.n * (h.n + 1) for i, h in zip(infos, hs))
@@ -883,7 +902,7 @@ def run_batch64(args):
     from paper_2407_13299_gb300 import dmp
 
     _build.build()
-    out = batched_leg(dmp, args.batch_mode, steps=args.steps, warmup=args.warmup)
+    out = batched_leg(dmp, args.batch_mode, steps=args.steps, warmup=args.warmup, stream=args.batch_stream == "on")
     out.update({"steps": args.steps, "warmup": args.warmup})
     print(json.dumps(out), flush=True)
     return 0

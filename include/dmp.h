@@ -97,7 +97,14 @@ enum {
  * precision of FP32 storage, not its memory saving). The refinement step
  * writes its result unrounded. Not offered with a tape, in the backward pass
  * or in the batched call (DMP_ERR_UNSUPPORTED). */
-enum { DMP_FLAG_BOUNDS_CONSTANT = 1, DMP_FLAG_FP32_STORAGE = 2 };
+/* DMP_FLAG_BATCHED_STREAM: dm_purify_batched runs its iterations as ordinary
+ * launches on the caller's stream, with a host read of the stopping rules
+ * after every two iterations, instead of one CUDA-graph WHILE launch. The
+ * kernels, their order and the results are the same; the host waits once per
+ * two iterations. For profilers that cannot look inside conditional graph
+ * nodes, and for per-phase times (dmp_profile_*), which are taken only outside
+ * graphs. Ignored by the other calls. */
+enum { DMP_FLAG_BOUNDS_CONSTANT = 1, DMP_FLAG_FP32_STORAGE = 2, DMP_FLAG_BATCHED_STREAM = 4 };
 
 /*
  * Purification method (dmp_opts.method).

@@ -44,7 +44,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Per-matrix partial measures (same quantities and order as the single path).
+// Per-matrix partial measures over the upper triangle (the quantities of the
+// single path's measure kernel). Batch rows are short (at most a few thousand
+// entries), so each warp takes whole rows: rows blockIdx.x 8 + w, + 8 kMeasBlk,
+// ... with the upper entries spread over the lanes, four independent
+// accumulator sets per lane, combined in a fixed order (reproducible sums).
 __global__ void __launch_bounds__(256)
 measure_grouped_kernel(const BatchMat* __restrict__ mats, int cur, double* __restrict__ part) {
   const BatchMat& M = mats[blockIdx.y];
@@ -55,13 +59,14 @@ measure_grouped_kernel(const BatchMat* __restrict__ mats, int cur, double* __res
   const double* X2 = M.X2;
   const double* H = M.H;
   const int64_t ldh = M.ldh;
-  double u_px = 0.0, u_id = 0.0, u_ph = 0.0;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double a_px[4] = {0.0, 0.0, 0.0, 0.0}, a_id[4] = {0.0, 0.0, 0.0, 0.0}, a_ph[4] = {0.0, 0.0, 0.0, 0.0};
   double d_p = 0.0, d_x = 0.0, d_px = 0.0, d_id = 0.0, d_ph = 0.0;
-  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * 8 + w; i < n; i += static_cast<int64_t>(gridDim.x) * 8) {
     const double* pr = P + i * ldp;
     const double* xr = X2 + i * n;
     const double* hr = H + i * ldh;
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       const double p = pr[i], x = xr[i], h = hr[i];
       d_p += p;
       d_x += x;
@@ -69,33 +74,53 @@ measure_grouped_kernel(const BatchMat* __restrict__ mats, int cur, double* __res
       d_id += (x - p) * (x - p);
       d_ph += p * h;
     }
-    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
+    int64_t j = i + 1 + lane;
+    for (; j + 96 < n; j += 128) {
+      double pv[4], xv[4], hv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        pv[u] = pr[j + 32 * u];
+        xv[u] = xr[j + 32 * u];
+        hv[u] = hr[j + 32 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a_px[u] += pv[u] * xv[u];
+        a_id[u] += (xv[u] - pv[u]) * (xv[u] - pv[u]);
+        a_ph[u] += pv[u] * hv[u];
+      }
+    }
+    for (; j < n; j += 32) {
       const double p = pr[j], x = xr[j], h = hr[j];
-      u_px += p * x;
-      u_id += (x - p) * (x - p);
-      u_ph += p * h;
+      a_px[0] += p * x;
+      a_id[0] += (x - p) * (x - p);
+      a_ph[0] += p * h;
     }
   }
+  const double u_px = (a_px[0] + a_px[1]) + (a_px[2] + a_px[3]);
+  const double u_id = (a_id[0] + a_id[1]) + (a_id[2] + a_id[3]);
+  const double u_ph = (a_ph[0] + a_ph[1]) + (a_ph[2] + a_ph[3]);
   __shared__ double red[8][8];
   double v[8] = {d_p, d_x, d_px, u_px, d_id, u_id, d_ph, u_ph};
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = warp_sum(v[q]);
-  if ((threadIdx.x & 31) == 0)
+  if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) red[threadIdx.x >> 5][q] = v[q];
+    for (int q = 0; q < 8; ++q) red[w][q] = v[q];
   __syncthreads();
   if (threadIdx.x < 8) {
     double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+    for (int ww = 0; ww < 8; ++ww) t += red[ww][threadIdx.x];
     part[(static_cast<int64_t>(blockIdx.y) * kMeasBlk + blockIdx.x) * 8 + threadIdx.x] = t;
   }
 }
 
 // One thread per matrix applies the stopping rules; the block then tells the
-// graph whether any matrix still runs.
+// graph (or, in stream mode, the host through *active) whether any matrix
+// still runs.
 __global__ void measure_grouped_final_kernel(const BatchMat* __restrict__ mats, int nmats,
                                              const double* __restrict__ part, cudaGraphConditionalHandle cond,
-                                             int set_cond) {
+                                             int set_cond, int* __restrict__ active) {
   __shared__ int any_active;
   if (threadIdx.x == 0) any_active = 0;
   __syncthreads();
@@ -114,6 +139,7 @@ __global__ void measure_grouped_final_kernel(const BatchMat* __restrict__ mats, 
   }
   __syncthreads();
   if (threadIdx.x == 0 && set_cond) cudaGraphSetConditional(cond, any_active ? 1u : 0u);
+  if (threadIdx.x == 0 && active != nullptr) *active = any_active;
 }
 
 // The result of a matrix that stopped after an odd number of updates sits in
@@ -131,7 +157,7 @@ __global__ void finish_grouped_kernel(const BatchMat* __restrict__ mats) {
 
 // ---------------------------------------------------------------- host side
 struct BatchLayout {
-  size_t mats, tiles, row_start, partials, err, counter, scratch, tune_ws, total;
+  size_t mats, tiles, row_start, partials, err, counter, active, scratch, tune_ws, total;
   std::vector<size_t> state, rowbuf, expsP, expsX, buf1, X2, planesP, planesX;
   std::vector<int64_t> n_pad, k_pad;
   int ntiles;
@@ -168,6 +194,7 @@ BatchLayout batch_layout(int batch, const int64_t* n, int s_max, int beta) {
   L.partials = c.take(sizeof(double) * 8 * kMeasBlk * batch);
   L.err = c.take(sizeof(int));
   L.counter = c.take(sizeof(int));
+  L.active = c.take(sizeof(int));
   L.scratch = c.take(tc_scratch_bytes());
   int64_t nmax = 2;
   for (int b = 0; b < batch; ++b) {
@@ -429,7 +456,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       build_tiles(cand, htiles);
       DMP_CUDA(cudaMemcpyAsync(dmats, hm.data(), sizeof(BatchMat) * batch, cudaMemcpyHostToDevice, st));
       DMP_CUDA(cudaMemcpyAsync(dtiles, htiles.data(), sizeof(int4) * htiles.size(), cudaMemcpyHostToDevice, st));
-      DMP_CUDA(launch_split_grouped(dmats, drow, batch, hrow[batch], 0, tbeta, st));
+      DMP_CUDA(launch_split_grouped(dmats, drow, batch, hrow[batch], 0, tbeta, s, st));
       cudaEvent_t e0, e1;
       DMP_CUDA(cudaEventCreate(&e0));
       DMP_CUDA(cudaEventCreate(&e1));
@@ -466,18 +493,19 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   }
   const int ntiles = static_cast<int>(htiles.size());
 
+  const bool stream_mode = (opts->flags & DMP_FLAG_BATCHED_STREAM) != 0;
   // graph: WHILE(any matrix running) { two iterations }, cached per argument set
   std::string gkey(reinterpret_cast<const char*>(hm.data()), sizeof(BatchMat) * batch);
   gkey.append(reinterpret_cast<const char*>(&ws), sizeof(ws));
   gkey.append(reinterpret_cast<const char*>(&cfg), sizeof(cfg));
   gkey.append(reinterpret_cast<const char*>(&tbeta), sizeof(tbeta));  // the digit rule picks the kernels
   cudaGraphExec_t exec = nullptr;
-  {
+  if (!stream_mode) {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto it = g_graphs.find(gkey);
     if (it != g_graphs.end()) exec = it->second.exec;
   }
-  if (exec == nullptr) {
+  if (!stream_mode && exec == nullptr) {
     GraphEntry ge;
     DMP_CUDA(cudaGraphCreate(&ge.graph, 0));
     cudaGraphConditionalHandle cond;
@@ -496,11 +524,11 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     cudaStream_t cs = capture_stream();
     DMP_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     for (int cur = 0; cur < 2; ++cur) {
-      launch_split_grouped(dmats, drow, batch, hrow[batch], cur, tbeta, cs);
+      launch_split_grouped(dmats, drow, batch, hrow[batch], cur, tbeta, s, cs);
       launch_ozaki_tc_grouped(dmats, dtiles, ntiles, cfg_bn(cfg), cfg_pair(cfg), tbeta, 0, cur, derr, scratch,
                               dcounter, cs);
-      launch_measure_grouped(dmats, batch, cur, dpart, cond, 1, cs);
-      launch_split_grouped(dmats, drow, batch, hrow[batch], 2, tbeta, cs);
+      launch_measure_grouped(dmats, batch, cur, dpart, cond, 1, nullptr, cs);
+      launch_split_grouped(dmats, drow, batch, hrow[batch], 2, tbeta, s, cs);
       launch_ozaki_tc_grouped(dmats, dtiles, ntiles, cfg_bn(cfg), cfg_pair(cfg), tbeta, 1, cur, derr, scratch,
                               dcounter, cs);
     }
@@ -512,8 +540,29 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     std::lock_guard<std::mutex> lk(g_graph_mu);
     g_graphs[gkey] = ge;
   }
-  DMP_CUDA(cudaGraphLaunch(exec, st));
-  count_launch();
+  if (stream_mode) {
+    // the graph body as plain launches; the host reads the stopping rules'
+    // verdict after every two iterations (the graph's condition check)
+    int* dactive = reinterpret_cast<int*>(at(ws, L.active));
+    for (int it = 0; it < max_iter; it += 2) {
+      for (int cur = 0; cur < 2; ++cur) {
+        DMP_CUDA(launch_split_grouped(dmats, drow, batch, hrow[batch], cur, tbeta, s, st));
+        DMP_CUDA(launch_ozaki_tc_grouped(dmats, dtiles, ntiles, cfg_bn(cfg), cfg_pair(cfg), tbeta, 0, cur, derr,
+                                         scratch, dcounter, st));
+        DMP_CUDA(launch_measure_grouped(dmats, batch, cur, dpart, cudaGraphConditionalHandle{}, 0, dactive, st));
+        DMP_CUDA(launch_split_grouped(dmats, drow, batch, hrow[batch], 2, tbeta, s, st));
+        DMP_CUDA(launch_ozaki_tc_grouped(dmats, dtiles, ntiles, cfg_bn(cfg), cfg_pair(cfg), tbeta, 1, cur, derr,
+                                         scratch, dcounter, st));
+      }
+      int active = 0;
+      DMP_CUDA(cudaMemcpyAsync(&active, dactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+      DMP_CUDA(cudaStreamSynchronize(st));
+      if (!active) break;
+    }
+  } else {
+    DMP_CUDA(cudaGraphLaunch(exec, st));
+    count_launch();
+  }
   DMP_CUDA(launch_finish_grouped(dmats, batch, st));
 
   std::vector<PurifyState> fin(batch);
@@ -554,10 +603,11 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
 namespace dmp {
 
 cudaError_t launch_measure_grouped(const BatchMat* mats, int nmats, int cur, double* partials,
-                                   cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st) {
+                                   cudaGraphConditionalHandle cond, int set_cond, int* active,
+                                   cudaStream_t st) {
   ProfScope prof(DMP_PROF_MEASURE, st);
   measure_grouped_kernel<<<dim3(kMeasBlk, nmats), 256, 0, st>>>(mats, cur, partials);
-  measure_grouped_final_kernel<<<1, 256, 0, st>>>(mats, nmats, partials, cond, set_cond);
+  measure_grouped_final_kernel<<<1, 256, 0, st>>>(mats, nmats, partials, cond, set_cond, active);
   count_launch(2);
   return cudaGetLastError();
 }

@@ -319,9 +319,10 @@ bool make_plane_map_ext(CUtensorMap* tm, const void* planes, int64_t k_pad, int6
 // Grouped kernels (every launch covers all matrices; finished ones are skipped).
 // `which`: 0 = buf[0], 1 = buf[1], 2 = X2.
 cudaError_t launch_split_grouped(const BatchMat* mats, const int64_t* row_start, int nmats, int64_t total_rows,
-                                 int which, int beta, cudaStream_t st);
+                                 int which, int beta, int s, cudaStream_t st);
 cudaError_t launch_measure_grouped(const BatchMat* mats, int nmats, int cur, double* partials,
-                                   cudaGraphConditionalHandle cond, int set_cond, cudaStream_t st);
+                                   cudaGraphConditionalHandle cond, int set_cond, int* active,
+                                   cudaStream_t st);
 cudaError_t launch_finish_grouped(const BatchMat* mats, int nmats, cudaStream_t st);
 // phase 0: X2 = P P from buf[cur]; phase 1: update buf[cur] -> buf[1 - cur].
 // `counter` (one int of device memory) is zeroed on the stream before a

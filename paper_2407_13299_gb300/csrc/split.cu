@@ -388,10 +388,12 @@ void launch_split_any(dim3 grid, cudaStream_t st, const double* A, int64_t m, in
 // Grouped: CTA x covers row x - row_start[b] of matrix b (row_start ascending,
 // row_start[nmats] = total padded rows). Finished matrices are skipped.
 // Batch rows are short (a few thousand entries at most): 128 threads per row,
-// so that many rows are in flight per SM.
+// so that many rows are in flight per SM. Every matrix of a batch has the
+// same slice count, a template argument where the launcher has an instance
+// for it (S = 0: taken from the descriptor).
 constexpr int kGroupedSplitThreads = 128;
 
-template <int KIND, int BETA>
+template <int KIND, int BETA, int S>
 __global__ void __launch_bounds__(kGroupedSplitThreads, 8)
 split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restrict__ row_start, int nmats,
                      int which) {
@@ -408,7 +410,7 @@ split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restric
   const int64_t lda = which == 0 ? M.ldp : M.n;
   int32_t* exps = which == 2 ? M.expsX : M.expsP;
   void* planes = which == 2 ? M.planesX : M.planesP;
-  split_one_row<KIND, BETA, 0, kGroupedSplitThreads>(A, r, M.n, static_cast<int>(M.n), lda, M.s, exps, planes,
+  split_one_row<KIND, BETA, S, kGroupedSplitThreads>(A, r, M.n, static_cast<int>(M.n), lda, M.s, exps, planes,
                                                      static_cast<int>(M.k_pad), M.n_pad * M.k_pad, nullptr);
 }
 
@@ -464,17 +466,31 @@ cudaError_t launch_transpose(const double* A, int64_t m, int64_t n, int64_t lda,
   return cudaGetLastError();
 }
 
+template <int KIND, int BETA, int S_LO, int S_HI>
+void launch_grouped_any(unsigned grid, cudaStream_t st, const BatchMat* mats, const int64_t* row_start, int nmats,
+                        int which, int s) {
+  if constexpr (S_LO <= S_HI) {
+    if (s == S_LO) {
+      split_grouped_kernel<KIND, BETA, S_LO><<<grid, kGroupedSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+      return;
+    }
+    launch_grouped_any<KIND, BETA, S_LO + 1, S_HI>(grid, st, mats, row_start, nmats, which, s);
+  } else {
+    split_grouped_kernel<KIND, BETA, 0><<<grid, kGroupedSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+  }
+}
+
 cudaError_t launch_split_grouped(const BatchMat* mats, const int64_t* row_start, int nmats, int64_t total_rows,
-                                 int which, int beta, cudaStream_t st) {
+                                 int which, int beta, int s, cudaStream_t st) {
   if (total_rows <= 0) return cudaSuccess;
   ProfScope prof(DMP_PROF_SPLIT, st);  // batch rows are at most a few thousand long (k_pad << kMaxRow)
   const unsigned grid = static_cast<unsigned>(total_rows);
   if (beta == 7) {
-    split_grouped_kernel<3, 7><<<grid, kGroupedSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+    launch_grouped_any<3, 7, 4, 9>(grid, st, mats, row_start, nmats, which, s);
   } else if (beta == 8) {
-    split_grouped_kernel<3, 8><<<grid, kGroupedSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+    launch_grouped_any<3, 8, 3, 7>(grid, st, mats, row_start, nmats, which, s);
   } else if (beta == 5) {
-    split_grouped_kernel<4, 5><<<grid, kGroupedSplitThreads, 0, st>>>(mats, row_start, nmats, which);
+    launch_grouped_any<4, 5, 5, 11>(grid, st, mats, row_start, nmats, which, s);
   } else {
     return cudaErrorInvalidValue;
   }

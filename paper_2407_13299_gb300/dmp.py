@@ -200,7 +200,7 @@ def _require_cuda(*ts):
             raise TypeError("expected a float64 CUDA tensor")
 
 
-FLAG_BOUNDS_CONSTANT, FLAG_FP32_STORAGE = 1, 2
+FLAG_BOUNDS_CONSTANT, FLAG_FP32_STORAGE, FLAG_BATCHED_STREAM = 1, 2, 4
 
 
 def make_opts(mode="int8", slices=7, executor="auto", tol=1e-10, energy_tol=0.0, max_iter=100,
@@ -465,15 +465,19 @@ def batched_workspace_bytes(ns, opts: Opts) -> int:
 
 
 def purify_batched(Hs, n_occs, mode="int8", slices=0, executor="tc", tol=1e-10, energy_tol=0.0, max_iter=100,
-                   Ps=None, ws=None, stream=None, raise_on_error=True):
+                   Ps=None, ws=None, stream=None, raise_on_error=True, stream_launches=False):
     """dm_purify_batched over a list of float64 CUDA tensors (each n x n,
-    contiguous). slices=0 lets the library's autotuner pick s. Returns
-    (list of P, list of info dicts, return code)."""
+    contiguous). slices=0 lets the library's autotuner pick s.
+    stream_launches=True runs the iterations as plain stream launches instead
+    of one graph launch (DMP_FLAG_BATCHED_STREAM: same results, visible to
+    profilers and to dmp_profile_*). Returns (list of P, list of info dicts,
+    return code)."""
     for H in Hs:
         _require_cuda(H)
     B = len(Hs)
     opts = make_opts(mode, slices if slices else 7, executor, tol, energy_tol, max_iter)
     opts.slices = int(slices)
+    opts.flags = FLAG_BATCHED_STREAM if stream_launches else 0
     ns = [int(H.shape[0]) for H in Hs]
     Hs = [H.contiguous() for H in Hs]
     if Ps is None:

@@ -71,3 +71,36 @@ def test_batch_member_errors_are_reported(dmp):
     assert infos[1]["status"] == dmp.ERR_NONFINITE
     assert infos[0]["status"] in (dmp.OK, dmp.C_OUT_OF_RANGE, dmp.STALLED)
     assert np.max(np.abs(Ps[0].cpu().numpy() - _proj(h1))) <= 1e-8
+
+
+@pytest.mark.parametrize("mode,s,max_iter", [("int8", 7, 100), ("e4m3", 10, 100), ("int8", 6, 3)])
+def test_stream_launches_match_the_graph(dmp, mode, s, max_iter):
+    """DMP_FLAG_BATCHED_STREAM runs the same kernels as plain launches with a
+    host check every two iterations: bit-identical P and the same reports, also
+    when the iteration cap (odd here) stops the loop; and the per-phase
+    profiler sees the launches."""
+    sizes = [(128, 32), (224, 56), (300, 75), (512, 128)]
+    hs = [make_hamiltonian(n, o, seed=900 + n) for n, o in sizes]
+    Hs = [torch.from_numpy(h.H).cuda() for h in hs]
+    occ = [o for _, o in sizes]
+    Pg, ig, rg = dmp.purify_batched(Hs, occ, mode=mode, slices=s, max_iter=max_iter, raise_on_error=False)
+    dmp.profile_enable(True)
+    dmp.profile_reset()
+    try:
+        Ps, is_, rs = dmp.purify_batched(Hs, occ, mode=mode, slices=s, max_iter=max_iter, raise_on_error=False,
+                                         stream_launches=True)
+        torch.cuda.synchronize()
+        prof = {k: dmp.profile_read(k) for k in (0, 1, 2)}
+    finally:
+        dmp.profile_enable(False)
+    assert rs == rg
+    assert all(torch.equal(a, b) for a, b in zip(Pg, Ps))
+    for a, b in zip(ig, is_):
+        assert a["iters"] == b["iters"] and a["status"] == b["status"] and a["energy"] == b["energy"]
+    iters = max(i["iters"] for i in is_)
+    assert iters <= max_iter
+    # two products, two splits and one measure per iteration, in bodies of two
+    # iterations, at least as many as the longest member ran
+    products, splits, measures = prof[0][1], prof[1][1], prof[2][1]
+    assert products == splits == 2 * measures and measures % 2 == 0 and measures >= iters
+    assert all(prof[k][0] > 0 for k in prof)
