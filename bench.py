@@ -70,6 +70,10 @@ def parse_args():
     ap.add_argument("--batch-stream", choices=("on", "off"), default="off",
                     help="batch64 workload: run the batched iterations as plain stream launches "
                          "(DMP_FLAG_BATCHED_STREAM) in the timed calls, so that a profiler sees every kernel")
+    ap.add_argument("--batch-tile", type=int, default=0, choices=(0, 128, 256, 512),
+                    help="batch64 workload: tile shape of the grouped product (0: the library's autotuner)")
+    ap.add_argument("--batch-sequential", choices=("on", "off"), default="on",
+                    help="batch64 workload: also time the 64 matrices as sequential dm_purify calls")
     ap.add_argument("--batched", choices=("on", "off"), default="on",
                     help="also time the 64-matrix batched workload (dm_purify_batched) and report it as `batched`")
     ap.add_argument("--foe", choices=("on", "off"), default="on",
@@ -902,7 +906,10 @@ def run_batch64(args):
     from paper_2407_13299_gb300 import dmp
 
     _build.build()
-    out = batched_leg(dmp, args.batch_mode, steps=args.steps, warmup=args.warmup, stream=args.batch_stream == "on")
+    dmp.set_batched_tile(args.batch_tile)
+    out = batched_leg(dmp, args.batch_mode, steps=args.steps, warmup=args.warmup, stream=args.batch_stream == "on",
+                      sequential=args.batch_sequential == "on")
+    out["tile_forced"] = args.batch_tile or None
     out.update({"steps": args.steps, "warmup": args.warmup})
     print(json.dumps(out), flush=True)
     return 0

@@ -513,6 +513,17 @@ int dmp_set_tc_pairing(int enable);
  * previous setting. A performance knob with no counterpart in the paper. */
 int dmp_set_tc_split_tiles(int enable);
 
+/* Tile shape of dm_purify_batched's grouped product: 0 (the default) lets the
+ * library's autotuner pick it by timing the batch's first product; 128 or 256
+ * force single-CTA tiles of 128 x 128 or 128 x 256, 512 forces CTA pairs on
+ * 256 x 256 tiles (E4M3 digits: 256 or 512 only). For reproducible runs and for
+ * profilers, whose replays would distort the tuner's timing. Process-wide, read
+ * at each call; returns the previous setting, or DMP_ERR_INVALID_ARG (setting
+ * unchanged) for another value. dm_purify_batched returns DMP_ERR_UNSUPPORTED
+ * when the forced shape is not available for its mode or on this GPU. A
+ * performance knob with no counterpart in the paper. */
+int dmp_set_batched_tile(int tile);
+
 /* Test hook for the bounded device waits (no counterpart in the paper). The
  * next tcgen05 product launch of the process (from any single-matrix entry
  * point, on any stream) is started with every wait bounded by wait_limit_us

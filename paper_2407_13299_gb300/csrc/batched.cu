@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -231,6 +232,7 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, std::pair<int, int>> g_tuned;  // -> (slices, tile shape cfg)
+std::atomic<int> g_forced_tile{0};                // dmp_set_batched_tile: 0 = tuner
 
 struct GraphEntry {
   cudaGraph_t graph = nullptr;
@@ -329,6 +331,9 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       tuned = true;
     }
   }
+  // a cached entry made while the tile shape was forced holds the slice count only
+  const bool tile_tuned = tuned && cfg != 0;
+  if (cfg == 0) cfg = 256;
   if (!tuned && s == 0) {
     const double target = opts->energy_tol > 0.0 ? opts->energy_tol : 1e-8;
     const int64_t nb = n[nmax_idx];
@@ -364,6 +369,11 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     // keep the caller's s
   }
   if (s > s_cap) return DMP_ERR_WORKSPACE;
+  const int forced = g_forced_tile.load();
+  if (forced != 0) {
+    if ((forced == 128 && f8) || (forced == 512 && !tc_pairs_available())) return DMP_ERR_UNSUPPORTED;
+    cfg = forced;
+  }
 
   // ---- descriptors
   std::vector<BatchMat> hm(batch);
@@ -441,7 +451,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   std::vector<int4> htiles;
   DMP_CUDA(cudaMemcpyAsync(drow, hrow.data(), sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, st));
 
-  if (!tuned) {
+  if (!tile_tuned && forced == 0) {
     // tile shape: time the P^2 product of the batch's initial guesses with each
     // (128 x 128 and 128 x 256 single CTAs, 256 x 256 CTA pairs; E4M3 digits run
     // on 256-column tiles only)
@@ -476,9 +486,9 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     }
     cfg = best_cfg;
   }
-  {
+  if (!tuned || (!tile_tuned && forced == 0)) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = std::make_pair(s, cfg);
+    g_tuned[key] = std::make_pair(s, forced != 0 ? 0 : cfg);  // 0: tile shape not tuned yet
   }
 
   // ---- the real run
@@ -620,3 +630,8 @@ cudaError_t launch_finish_grouped(const BatchMat* mats, int nmats, cudaStream_t 
 }
 
 }  // namespace dmp
+
+extern "C" int dmp_set_batched_tile(int tile) {
+  if (tile != 0 && tile != 128 && tile != 256 && tile != 512) return DMP_ERR_INVALID_ARG;
+  return dmp::g_forced_tile.exchange(tile);
+}

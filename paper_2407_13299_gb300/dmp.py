@@ -113,6 +113,7 @@ SIGNATURES = {
     "dmp_set_tc_pairing": (ctypes.c_int, [ctypes.c_int]),
     "dmp_test_stall_next_product": (ctypes.c_int, [_i32]),
     "dmp_set_tc_split_tiles": (ctypes.c_int, [ctypes.c_int]),
+    "dmp_set_batched_tile": (ctypes.c_int, [ctypes.c_int]),
 }
 
 
@@ -154,6 +155,14 @@ def set_tc_split_tiles(enable: bool) -> bool:
     shared by every CTA (dmp_set_tc_split_tiles; on by default). Returns the
     previous setting."""
     return bool(lib().dmp_set_tc_split_tiles(1 if enable else 0))
+
+
+def set_batched_tile(tile: int) -> int:
+    """Force the tile shape of dm_purify_batched's grouped product (128, 256:
+    single-CTA tiles of 128 x tile; 512: CTA pairs on 256 x 256 tiles) or let
+    the autotuner pick it (0, the default). Returns the previous setting
+    (dmp_set_batched_tile)."""
+    return _check(int(lib().dmp_set_batched_tile(int(tile))), "dmp_set_batched_tile", allow_status=True)
 
 
 def test_stall_next_product(wait_limit_us: int) -> None:

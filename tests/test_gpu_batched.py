@@ -104,3 +104,28 @@ def test_stream_launches_match_the_graph(dmp, mode, s, max_iter):
     products, splits, measures = prof[0][1], prof[1][1], prof[2][1]
     assert products == splits == 2 * measures and measures % 2 == 0 and measures >= iters
     assert all(prof[k][0] > 0 for k in prof)
+
+
+@pytest.mark.parametrize("mode,tiles", [("int8", (128, 256, 512)), ("e4m3", (256, 512))])
+def test_forced_tile_shapes_give_the_tuned_result(dmp, mode, tiles):
+    """dmp_set_batched_tile: every tile shape gives bit-for-bit the autotuned
+    call's P (the level sums are exact whatever the tiling); a shape the mode
+    cannot use is refused, and 0 hands the choice back to the tuner."""
+    sizes = [(160, 40), (256, 64), (416, 104)]
+    hs = [make_hamiltonian(n, o, seed=950 + n) for n, o in sizes]
+    Hs = [torch.from_numpy(h.H).cuda() for h in hs]
+    occ = [o for _, o in sizes]
+    s = 7 if mode == "int8" else 10
+    want, _, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=s)
+    try:
+        for t in tiles:
+            dmp.set_batched_tile(t)
+            got, _, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=s)
+            assert all(torch.equal(a, b) for a, b in zip(want, got)), t
+        if mode == "e4m3":
+            dmp.set_batched_tile(128)
+            _, _, rc = dmp.purify_batched(Hs, occ, mode=mode, slices=s, raise_on_error=False)
+            assert rc == dmp.ERR_UNSUPPORTED
+    finally:
+        assert dmp.set_batched_tile(0) in tiles + (128,)
+    assert dmp.lib().dmp_set_batched_tile(384) == dmp.ERR_INVALID_ARG
