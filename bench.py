@@ -72,6 +72,8 @@ def parse_args():
                          "(DMP_FLAG_BATCHED_STREAM) in the timed calls, so that a profiler sees every kernel")
     ap.add_argument("--batch-tile", type=int, default=0, choices=(0, 128, 256, 512),
                     help="batch64 workload: tile shape of the grouped product (0: the library's autotuner)")
+    ap.add_argument("--batch-refine", type=int, default=0,
+                    help="batch64 workload: refinement step with this many slices (0: none)")
     ap.add_argument("--batch-sequential", choices=("on", "off"), default="on",
                     help="batch64 workload: also time the 64 matrices as sequential dm_purify calls")
     ap.add_argument("--batched", choices=("on", "off"), default="on",
@@ -697,6 +699,12 @@ def run_ours(args):
     batched = None
     if args.batched == "on" and not args.slices:
         batched = batched_leg(dmp, "int8")
+        # the same workload with the refinement step (7-slice products; the
+        # tuner then compares refined energies): reported beside it
+        ref = batched_leg(dmp, "int8", steps=3, warmup=1, sequential=False, refine=7)
+        batched["with_refinement"] = {k: ref[k] for k in ("value", "unit", "slices", "refinement", "frac",
+                                                          "iters_max", "max_rel_energy_error",
+                                                          "phases_ms_stream_launches")}
 
     # ---- FP64 purification on the same GPU (once)
     fp64 = None
@@ -823,7 +831,7 @@ def run_ours(args):
     return 0
 
 
-def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True, stream=False):
+def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True, stream=False, refine=0):
     """The batched workload: 64 Hamiltonians, n = 32 U{4..48}, n_occ = n/4, gap
     0.2, through dm_purify_batched (one graph launch, slice count and tile width
     from the library's autotuner; `stream`: plain stream launches instead),
@@ -842,18 +850,20 @@ def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True, stream=Fal
     occ = [o for _, o, _ in sizes]
     opts = dmp.make_opts(mode, 7, "tc")
     opts.slices = 0
-    ws = dmp.workspace(dmp.batched_workspace_bytes([h.n for h in hs], opts))
     Ps = [torch.empty_like(H) for H in Hs]
-    _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws,
+    opts.refine_slices = refine
+    ws = dmp.workspace(dmp.batched_workspace_bytes([h.n for h in hs], opts))
+    _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, refine=refine,
                                      stream_launches=stream)  # tunes (and builds the graph)
     s = infos[0]["slices_used"]
     for _ in range(warmup):
-        dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, stream_launches=stream)
+        dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, refine=refine, stream_launches=stream)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(steps):
-        _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, stream_launches=stream)
+        _, infos, _ = dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, refine=refine,
+                                         stream_launches=stream)
     b.record()
     torch.cuda.synchronize()
     t_batch = a.elapsed_time(b) / 1e3 / steps
@@ -862,7 +872,7 @@ def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True, stream=Fal
     dmp.profile_enable(True)
     dmp.profile_reset()
     try:
-        dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, stream_launches=True)
+        dmp.purify_batched(Hs, occ, mode=mode, slices=0, Ps=Ps, ws=ws, refine=refine, stream_launches=True)
         torch.cuda.synchronize()
         phases = {name: round(dmp.profile_read(k)[0], 3)
                   for k, name in ((0, "products"), (1, "splits"), (2, "measures"), (3, "init"))}
@@ -870,11 +880,15 @@ def batched_leg(dmp, mode="int8", steps=3, warmup=1, sequential=True, stream=Fal
     finally:
         dmp.profile_enable(False)
     out = {"workload": "batch64: 64 H, n = 32 U{4..48}, n_occ = n/4, gap 0.2", "mode": f"ozaki-{mode}",
-           "slices": s, "value": t_batch, "unit": UNIT, "launch": "stream launches" if stream else "one graph launch",
+           "slices": s, "refinement": f"{refine}-slice products" if refine else None, "value": t_batch, "unit": UNIT,
+           "launch": "stream launches" if stream else "one graph launch",
            "phases_ms_stream_launches": phases, "phase_launches": launches}
-    # slice-pair work: per matrix 2 iters + 1 symmetric products of p n^2 (n + 1)
+    # slice-pair work: per matrix 2 iters + 1 symmetric products of p n^2 (n + 1),
+    # and the refinement step's two products of p(r) pairs
     p_s = s * (s + 1) // 2
-    flops = sum((2 * i["iters"] + 1) * p_s * h.n * h.n * (h.n + 1) for i, h in zip(infos, hs))
+    p_r = refine * (refine + 1) // 2
+    flops = sum(((2 * i["iters"] + 1) * p_s + (2 * p_r if i["refined"] else 0)) * h.n * h.n * (h.n + 1)
+                for i, h in zip(infos, hs))
     peaks, _ = load_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])) * \
         (2.0 if mode == "e4m3" else 1.0)
@@ -908,7 +922,7 @@ def run_batch64(args):
     _build.build()
     dmp.set_batched_tile(args.batch_tile)
     out = batched_leg(dmp, args.batch_mode, steps=args.steps, warmup=args.warmup, stream=args.batch_stream == "on",
-                      sequential=args.batch_sequential == "on")
+                      sequential=args.batch_sequential == "on", refine=args.batch_refine)
     out["tile_forced"] = args.batch_tile or None
     out.update({"steps": args.steps, "warmup": args.warmup})
     print(json.dumps(out), flush=True)

@@ -342,6 +342,13 @@ int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* 
  * matrix. Each matrix stops on its own rule; the call returns DMP_OK when all
  * converged, else the largest status seen. Modes DMP_OZAKI_INT8, DMP_OZAKI_BF16
  * and DMP_OZAKI_E4M3 (DMP_FP64 gives DMP_ERR_UNSUPPORTED).
+ * opts->refine_slices = r > 0 adds the refinement step of dm_purify (one
+ * McWeeny step P' = 3 P^2 - 2 P^3 with r-slice products, Sec. "Precision
+ * Requirements Sweep") to every member that ended without an error, after the
+ * whole batch has stopped; its report then holds the refined energy
+ * (refined = 1). FP64 refinement products (r < 0), FP32 storage and the
+ * late-slice schedule are not offered here (DMP_ERR_UNSUPPORTED). With
+ * opts->slices = 0 the slice-count tuner compares refined energies.
  */
 int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n,
                       const int64_t* n_occ, double* const* P, const dmp_opts* opts,

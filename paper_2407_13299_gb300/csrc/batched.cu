@@ -156,6 +156,49 @@ __global__ void finish_grouped_kernel(const BatchMat* __restrict__ mats) {
   }
 }
 
+// The refinement step (one McWeeny step P' = 3 P^2 - 2 P^3 with r-slice
+// products after the loop, Sec. "Precision Requirements Sweep"): matrices that
+// ended without an error run again (done cleared) with the McWeeny weights.
+__global__ void refine_begin_kernel(const BatchMat* __restrict__ mats, int nmats) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nmats; b += gridDim.x * blockDim.x) {
+    PurifyState* st = mats[b].state;
+    if (st->status < 0) continue;
+    st->alpha = 0.0;
+    st->b2 = 3.0;
+    st->b3 = -2.0;
+    st->done = 0;
+  }
+}
+
+// The refined P (in buf[1]) goes to the caller's buffer.
+__global__ void refine_copy_kernel(const BatchMat* __restrict__ mats) {
+  const BatchMat& M = mats[blockIdx.y];
+  if (M.state->done) return;
+  const int64_t n = M.n;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n * n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    M.buf[0][i * M.ldp + j] = M.buf[1][e];
+  }
+}
+
+// tr(P' H) of each refined matrix from the grouped measures' partial sums
+// (diagonal and upper P H, the same fixed order as the stopping rules'), and
+// the matrix done again.
+__global__ void refine_end_kernel(const BatchMat* __restrict__ mats, int nmats, const double* __restrict__ part) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nmats; b += gridDim.x * blockDim.x) {
+    PurifyState* st = mats[b].state;
+    if (st->done) continue;
+    double d = 0.0, u = 0.0;
+    for (int k = 0; k < kMeasBlk; ++k) {
+      d += part[(static_cast<int64_t>(b) * kMeasBlk + k) * 8 + 6];
+      u += part[(static_cast<int64_t>(b) * kMeasBlk + k) * 8 + 7];
+    }
+    st->energy_refined = d + 2.0 * u;
+    st->done = 1;
+  }
+}
+
 // ---------------------------------------------------------------- host side
 struct BatchLayout {
   size_t mats, tiles, row_start, partials, err, counter, active, scratch, tune_ws, total;
@@ -274,7 +317,8 @@ int dmp_batched_workspace_size(int32_t batch, const int64_t* n, const dmp_opts* 
     if (n[b] < 2) return DMP_ERR_INVALID_ARG;
   if (!batch_mode(opts->mode)) return DMP_ERR_UNSUPPORTED;
   const int beta = beta_of(opts->mode);
-  const int s_max = opts->slices > 0 ? opts->slices : max_slices(opts->mode);
+  const int s_max =
+      std::max(opts->slices > 0 ? opts->slices : max_slices(opts->mode), std::max(opts->refine_slices, 0));
   *bytes = batch_layout(batch, n, s_max, beta).total;
   return DMP_OK;
 }
@@ -287,7 +331,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     return DMP_ERR_INVALID_ARG;
   if (!batch_mode(opts->mode)) return DMP_ERR_UNSUPPORTED;
   if (opts->executor != DMP_EXEC_AUTO && opts->executor != DMP_EXEC_TC) return DMP_ERR_UNSUPPORTED;
-  if (opts->refine_slices != 0) return DMP_ERR_UNSUPPORTED;  // no batched refinement step
+  if (opts->refine_slices < 0) return DMP_ERR_UNSUPPORTED;  // the refinement step runs Ozaki products only
   if (opts->flags & DMP_FLAG_FP32_STORAGE) return DMP_ERR_UNSUPPORTED;
   if (opts->late_slices != 0) return DMP_ERR_UNSUPPORTED;  // one slice count per batched launch
   if (opts->method != DMP_METHOD_PM) return DMP_ERR_UNSUPPORTED;  // canonical purification only
@@ -295,6 +339,8 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   const int smax_mode = max_slices(opts->mode);
   const bool f8 = beta == 5;
   if (opts->slices < 0 || opts->slices > smax_mode) return DMP_ERR_INVALID_ARG;
+  const int refine = opts->refine_slices;  // 0: none
+  if (refine > smax_mode) return DMP_ERR_INVALID_ARG;
   for (int b = 0; b < batch; ++b) {
     if (H[b] == nullptr || P[b] == nullptr || n[b] < 2 || n_occ[b] <= 0 || n_occ[b] >= n[b])
       return DMP_ERR_INVALID_ARG;
@@ -302,7 +348,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     const double dmax = digit_max(opts->mode);
     if (static_cast<double>(smax_mode) * n[b] * dmax * dmax >= 2147483648.0) return DMP_ERR_UNSUPPORTED;
   }
-  const int s_cap = opts->slices > 0 ? opts->slices : smax_mode;
+  const int s_cap = std::max(opts->slices > 0 ? opts->slices : smax_mode, refine);
   const BatchLayout L = batch_layout(batch, n, s_cap, beta);
   if (ws_bytes < L.total) return DMP_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -319,7 +365,8 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
   const int64_t nmax_idx = std::max_element(n, n + batch) - n;
 
   // ---- autotune: slice count (accuracy) and tile width (speed), cached per shape
-  TuneKey key{std::vector<int64_t>(n, n + batch), opts->mode * 16 + opts->slices + (tc_pairs_available() ? 1024 : 0)};
+  TuneKey key{std::vector<int64_t>(n, n + batch),
+              opts->mode * 16 + opts->slices + (tc_pairs_available() ? 1024 : 0) + 2048 * refine};
   int s = opts->slices, cfg = 256;
   bool tuned = false;
   {
@@ -343,6 +390,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       dmp_opts t{};
       t.mode = opts->mode;
       t.slices = sc;
+      t.refine_slices = refine;  // compared after the refinement step when the call has one
       t.executor = DMP_EXEC_TC;
       t.max_iter = max_iter;
       t.tol = tol;
@@ -408,7 +456,7 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     const int box_b = cfg_pair(cfg) ? cfg_bn(cfg) / 2 : cfg_bn(cfg);
     for (int b = 0; b < batch; ++b) {
       BatchMat& M = hm[b];
-      const int64_t rows = static_cast<int64_t>(s) * M.n_pad;
+      const int64_t rows = static_cast<int64_t>(M.s) * M.n_pad;
       if (!make_map(&M.tmPa, M.planesP, M.k_pad, rows, 128, f8)) return false;
       if (!make_map(&M.tmPb, M.planesP, M.k_pad, rows, box_b, f8)) return false;
       if (!make_map(&M.tmXb, M.planesX, M.k_pad, rows, box_b, f8)) return false;
@@ -573,7 +621,43 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
     DMP_CUDA(cudaGraphLaunch(exec, st));
     count_launch();
   }
-  DMP_CUDA(launch_finish_grouped(dmats, batch, st));
+  DMP_CUDA(launch_finish_grouped(dmats, batch, st));  // every iterate in the caller's P
+
+  if (refine > 0) {
+    // ---- refinement step: X^2 = P P and P' = 3 X^2 - 2 P X^2 with r-slice
+    // products over the same tiles, for every matrix that ended without an
+    // error (the others stay done and are skipped), then tr(P' H)
+    for (int b = 0; b < batch; ++b) hm[b].s = refine;
+    if (!build_maps(cfg)) return DMP_ERR_CUDA;
+    DMP_CUDA(cudaMemcpyAsync(dmats, hm.data(), sizeof(BatchMat) * batch, cudaMemcpyHostToDevice, st));
+    {
+      ProfScope prof(DMP_PROF_OTHER, st);
+      refine_begin_kernel<<<1, 256, 0, st>>>(dmats, batch);
+      count_launch();
+      DMP_CUDA(cudaGetLastError());
+    }
+    DMP_CUDA(launch_split_grouped(dmats, drow, batch, hrow[batch], 0, tbeta, refine, st));
+    DMP_CUDA(launch_ozaki_tc_grouped(dmats, dtiles, ntiles, cfg_bn(cfg), cfg_pair(cfg), tbeta, 0, 0, derr, scratch,
+                                     dcounter, st));
+    DMP_CUDA(launch_split_grouped(dmats, drow, batch, hrow[batch], 2, tbeta, refine, st));
+    DMP_CUDA(launch_ozaki_tc_grouped(dmats, dtiles, ntiles, cfg_bn(cfg), cfg_pair(cfg), tbeta, 1, 0, derr, scratch,
+                                     dcounter, st));
+    {
+      // the grouped measures' partial sums of P' (buf[1]) give its P H sums
+      // (no stopping rules: those would take P' for another iterate)
+      ProfScope prof(DMP_PROF_MEASURE, st);
+      measure_grouped_kernel<<<dim3(kMeasBlk, batch), 256, 0, st>>>(dmats, 1, dpart);
+      count_launch();
+      DMP_CUDA(cudaGetLastError());
+    }
+    {
+      ProfScope prof(DMP_PROF_OTHER, st);
+      refine_copy_kernel<<<dim3(64, batch), 256, 0, st>>>(dmats);
+      refine_end_kernel<<<1, 256, 0, st>>>(dmats, batch, dpart);
+      count_launch(2);
+      DMP_CUDA(cudaGetLastError());
+    }
+  }
 
   std::vector<PurifyState> fin(batch);
   for (int b = 0; b < batch; ++b)
@@ -589,17 +673,18 @@ int dm_purify_batched(int32_t batch, const double* const* H, const int64_t* n, c
       dmp_info& I = infos[b];
       I.status = f.status;
       I.iters = f.iter;
+      const bool refined = refine > 0 && f.status >= 0;
       I.slices_used = s;
       I.executor_used = DMP_EXEC_TC;
-      I.energy = f.energy;
-      I.band_energy = 2.0 * f.energy;
+      I.energy = refined ? f.energy_refined : f.energy;
+      I.band_energy = 2.0 * I.energy;
       I.idem = std::sqrt(f.idem2);
       I.trace = f.t1;
       I.c_last = f.c;
       I.h_min = f.h_min;
       I.h_max = f.h_max;
       I.energy_unrefined = f.energy;
-      I.refined = 0;
+      I.refined = refined ? 1 : 0;
     }
     worst = std::max(worst, f.status);
   }

@@ -474,9 +474,10 @@ def batched_workspace_bytes(ns, opts: Opts) -> int:
 
 
 def purify_batched(Hs, n_occs, mode="int8", slices=0, executor="tc", tol=1e-10, energy_tol=0.0, max_iter=100,
-                   Ps=None, ws=None, stream=None, raise_on_error=True, stream_launches=False):
+                   Ps=None, ws=None, stream=None, raise_on_error=True, stream_launches=False, refine=0):
     """dm_purify_batched over a list of float64 CUDA tensors (each n x n,
-    contiguous). slices=0 lets the library's autotuner pick s.
+    contiguous). slices=0 lets the library's autotuner pick s. refine=r > 0
+    adds the r-slice refinement step to every member (opts.refine_slices).
     stream_launches=True runs the iterations as plain stream launches instead
     of one graph launch (DMP_FLAG_BATCHED_STREAM: same results, visible to
     profilers and to dmp_profile_*). Returns (list of P, list of info dicts,
@@ -487,6 +488,7 @@ def purify_batched(Hs, n_occs, mode="int8", slices=0, executor="tc", tol=1e-10, 
     opts = make_opts(mode, slices if slices else 7, executor, tol, energy_tol, max_iter)
     opts.slices = int(slices)
     opts.flags = FLAG_BATCHED_STREAM if stream_launches else 0
+    opts.refine_slices = int(refine)
     ns = [int(H.shape[0]) for H in Hs]
     Hs = [H.contiguous() for H in Hs]
     if Ps is None:

@@ -129,3 +129,54 @@ def test_forced_tile_shapes_give_the_tuned_result(dmp, mode, tiles):
     finally:
         assert dmp.set_batched_tile(0) in tiles + (128,)
     assert dmp.lib().dmp_set_batched_tile(384) == dmp.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mode,s,r", [("int8", 5, 8), ("e4m3", 7, 10), ("bf16", 5, 7)])
+def test_batched_refinement_matches_single_and_oracle(dmp, mode, s, r):
+    """opts.refine_slices in the batched call: every member gets dm_purify's
+    refinement step (one McWeeny step with r-slice products after the loop), so
+    it matches its own refined dm_purify call; one member against the oracle's
+    refinement in the same digit rule."""
+    sizes = [(128, 32), (200, 50), (320, 80), (448, 112)]
+    hs = [make_hamiltonian(n, o, seed=970 + n) for n, o in sizes]
+    Hs = [torch.from_numpy(h.H).cuda() for h in hs]
+    Ps, infos, rc = dmp.purify_batched(Hs, [o for _, o in sizes], mode=mode, slices=s, refine=r)
+    assert rc in (dmp.OK, dmp.C_OUT_OF_RANGE, dmp.STALLED)
+    beta = {"int8": 7, "bf16": 8, "e4m3": 5}[mode]
+    # the batched and single loops sum their traces in different orders, and at
+    # these small slice counts a last-bit difference of an iterate moves
+    # truncated digits: agreement to a few dozen units of the slices' resolution
+    tol = 50.0 * 2.0 ** (-beta * s)
+    for h, H, P, info in zip(hs, Hs, Ps, infos):
+        assert info["refined"] == 1
+        assert info["band_energy"] == 2.0 * info["energy"]
+        P1, i1 = dmp.purify(H, h.n_occ, mode=mode, slices=s, executor="tc", refine=r)
+        Pn = P.cpu().numpy()
+        assert np.max(np.abs(Pn - P1.cpu().numpy())) <= tol, h.n
+        assert abs(info["energy"] - i1["energy"]) <= tol * abs(i1["energy"]), h.n
+        assert np.array_equal(Pn, Pn.T)
+        # the refinement beats the loop's own energy error
+        E = float(np.sum(h.e[: h.n_occ]))
+        assert abs(info["energy"] - E) <= abs(info["energy_unrefined"] - E) + 1e-14 * abs(E)
+    h = hs[2]
+    beta, rounding = {"int8": (7, "trunc"), "bf16": (8, "nearest"), "e4m3": (5, "nearest")}[mode]
+    ref = pu.purify(h.H, h.n_occ, tol=1e-10, product=partial(oz.ozaki_gemm, s=s, beta=beta, rounding=rounding),
+                    refine_product=partial(oz.ozaki_gemm, s=r, beta=beta, rounding=rounding))
+    assert np.max(np.abs(Ps[2].cpu().numpy() - ref["P"])) <= 1e-8
+    assert abs(infos[2]["energy"] - ref["energy"]) <= 1e-10 * abs(ref["energy"])
+
+
+def test_batched_refinement_with_tuned_slices_on_the_64_workload(dmp):
+    """The 64-matrix workload with the refinement step and the slice count left
+    to the tuner (which then compares refined energies): every member within
+    1e-8 of its exact band energy."""
+    sizes = batch_sizes()
+    hs = [make_hamiltonian(n, o, occ=(-2.0, -0.1), virt=(0.1, 2.0), seed=sd) for n, o, sd in sizes]
+    Hs = [torch.from_numpy(h.H).cuda() for h in hs]
+    Ps, infos, rc = dmp.purify_batched(Hs, [o for _, o, _ in sizes], mode="int8", slices=0, refine=8)
+    assert rc >= 0
+    assert 4 <= infos[0]["slices_used"] <= 10
+    for h, info in zip(hs, infos):
+        E = float(np.sum(h.e[: h.n_occ]))
+        assert info["refined"] == 1
+        assert abs(info["energy"] - E) <= 1e-8 * abs(E), (h.n, info)
