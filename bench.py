@@ -431,12 +431,38 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t0)
         torch.cuda.synchronize()
         e2e_dev.append(ea.elapsed_time(eb) / 1e3)
+    matches = bool(torch.equal(P_host, P.cpu()))
+    # the two copies alone, timed the same way (events on the stream)
+    Hd_probe = torch.empty_like(H)
+    ea = torch.cuda.Event(enable_timing=True)
+    eb = torch.cuda.Event(enable_timing=True)
+    ec = torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    Hd_probe.copy_(H_host, non_blocking=True)
+    eb.record(stream)
+    P_host.copy_(Hd_probe, non_blocking=True)
+    ec.record(stream)
+    torch.cuda.synchronize()
+    dev_check = {"h2d_copy_s": ea.elapsed_time(eb) / 1e3, "d2h_copy_s": eb.elapsed_time(ec) / 1e3}
+    del Hd_probe
+    # the same purification as a device call, once on the host call's own
+    # device workspace (past its H and P) and once on the timed region's: how
+    # much of the gap between e2e and value is placement of the workspace
+    front = 2 * ((n * n * 8 + 255) // 256 * 256)
+    for name, w_ in (("device_call_on_host_workspace_s", ws_host[front:]), ("device_call_s", ws)):
+        ea = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        dmp.purify(H, n_occ, mode=mode, slices=s, executor=args.executor, refine=refine, P=P, ws=w_)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        dev_check[name] = ea.elapsed_time(eb) / 1e3
     e2e = {"value": max_over_ranks(statistics.median(e2e_times), dev), "unit": UNIT,
            "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8, "runs_s": e2e_times,
            "runs_device_s": e2e_dev,
            "call": "dm_purify_host (C ABI): pinned host H in, pinned host P out, one cudaMemcpy2DAsync each way "
                    "on the library's stream, synchronised before return; host clock around the call",
-           "matches_device_call": bool(torch.equal(P_host, P.cpu()))}
+           "matches_device_call": matches, **dev_check}
     del ws_host
 
     # ---- timed region: K full purifications, H resident in HBM (512 MiB > L2)
