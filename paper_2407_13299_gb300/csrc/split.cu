@@ -387,14 +387,14 @@ void launch_split_any(dim3 grid, cudaStream_t st, const double* A, int64_t m, in
 
 // Grouped: CTA x covers row x - row_start[b] of matrix b (row_start ascending,
 // row_start[nmats] = total padded rows). Finished matrices are skipped.
-// Batch rows are short (a few thousand entries at most): 128 threads per row,
-// so that many rows are in flight per SM. Every matrix of a batch has the
+// Batch rows are short (at most about 1500 entries): 64 threads per row, so
+// that many rows are in flight per SM (sixteen CTAs). Every matrix of a batch has the
 // same slice count, a template argument where the launcher has an instance
 // for it (S = 0: taken from the descriptor).
-constexpr int kGroupedSplitThreads = 128;
+constexpr int kGroupedSplitThreads = 64;
 
 template <int KIND, int BETA, int S>
-__global__ void __launch_bounds__(kGroupedSplitThreads, 8)
+__global__ void __launch_bounds__(kGroupedSplitThreads, 16)
 split_grouped_kernel(const BatchMat* __restrict__ mats, const int64_t* __restrict__ row_start, int nmats,
                      int which) {
   const int64_t x = blockIdx.x;
