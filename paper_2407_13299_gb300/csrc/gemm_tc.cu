@@ -337,6 +337,18 @@ __device__ __forceinline__ double round_exact(long long h, int sh, long long l, 
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// RN(h 2^sh + l) as a double (unscaled), for integers |h|, |l| < 2^53 and
+// 0 <= sh < 64: when the exact sum fits in 63 bits (|h| < 2^(62 - sh), always
+// so for a last group of one level) it is formed in int64 and converted with
+// one correctly rounded conversion; otherwise round_exact forms it in 128 bits.
+// Either way the value is that of the float64 expression.
+__device__ __forceinline__ double round_sum(long long h, int sh, long long l) {
+  const long long lim = 1ll << (62 - sh);
+  if (h > -lim && h < lim)
+    return __ll2double_rn(static_cast<long long>(static_cast<unsigned long long>(h) << sh) + l);
+  return round_exact(h, sh, l, 0);
+}
+
 // x 2^e for a finite double: exponent arithmetic when the result stays normal,
 // ldexp otherwise (identical results: scaling by a power of two is exact).
 __device__ __forceinline__ double scale_pow2(double x, int e) {
@@ -961,6 +973,9 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       const double lscale = ldexp(1.0, -p.beta * (2 + (s - 1) % p.group));
       const bool has_d = s > p.group;
       const bool two_groups = has_d && s <= 2 * p.group;
+      // weight of the rounded sum: 2^(-beta (s+1)) for two groups, 2^(-beta L_a)
+      // for one, none with D (already scaled)
+      const int e_acc = two_groups ? -p.beta * (s + 1) : (has_d ? 0 : -p.beta * (2 + (s - 1) % p.group));
       const uint64_t pol = policy_evict_last();
       double* Cout = jb.epi.C;
       const int64_t ldc = jb.epi.ldc;
@@ -1001,14 +1016,14 @@ ozaki_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           const int64_t col = col0 + t;
           if (col >= jb.n) break;
           if (jb.sym && r > col) continue;  // the (col, r) element's mirror covers it
-          // one or two groups: the exact integer combination rounded once;
-          // three or more: the float64 sum D of the earlier groups plus the last
-          const double acc =
-              two_groups ? round_exact(td[t], p.beta * p.group, ti[t], -p.beta * (s + 1))
-                         : (has_d ? __longlong_as_double(td[t]) + static_cast<double>(ti[t]) * lscale
-                                  : round_exact(0, 0, ti[t], -p.beta * (2 + (s - 1) % p.group)));
+          // one or two groups: the exact integer combination rounded once and
+          // scaled by 2^e_acc (exact); three or more: the float64 sum D of the
+          // earlier groups plus the last
+          const double acc = two_groups ? round_sum(td[t], p.beta * p.group, ti[t])
+                                        : (has_d ? __longlong_as_double(td[t]) + static_cast<double>(ti[t]) * lscale
+                                                 : static_cast<double>(ti[t]));
           double v = (er == kBadExp || ecv[t] == kBadExp) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                          : scale_pow2(acc, er + ecv[t]);
+                                                          : scale_pow2(acc, er + ecv[t] + e_acc);
           if (upd) v = wa * pv[t] + w2 * xv[t] + w3 * v;
           v = stored_value(v, jb.epi.round32 != 0);
           Cout[r * ldc + col] = v;
